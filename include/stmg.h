@@ -1,0 +1,164 @@
+/*
+ * stmg -- space-time multigrid for the heat equation on one GPU.
+ *
+ * Method: Gander & Neumueller, "Analysis of a new space-time parallel
+ * multigrid algorithm for parabolic problems" (arXiv:1411.0519).
+ *
+ * Problem (Section 1, eq. (chap4_modelproblem)): du/dt - Laplace u = f on
+ * (0,1)^d x (0,T), d = 1, 2, 3, u = 0 on the boundary, u(.,0) = u0.  Space:
+ * P1 (d = 1) / Q1 (d = 2, 3) finite elements on a uniform grid with n = 2^k - 1
+ * interior nodes per axis, h = 1/(n+1).  Time: N = 2^m uniform slabs,
+ * tau = T/N, discontinuous Galerkin of degree p_t in the Legendre basis
+ * psi_k(t) = P_k(2 (t - t_{n-1}) / tau - 1), q = p_t + 1 dofs per slab.
+ * The discrete system (chap4_generalLinearSystem) is block lower-bidiagonal:
+ *
+ *     A u_1 = f_1,  B u_{n-1} + A u_n = f_n,
+ *     A = K_tau (x) M_h + M_tau (x) K_h,   B = -N_tau (x) M_h.
+ *
+ * Vector layout (every pointer below that holds a space-time vector):
+ * contiguous FP64, index ((s * q + l) * n^d + j) for time step s = 0..N-1,
+ * time dof l = 0..q-1, spatial node j = (z * n + y) * n + x (x fastest).
+ * A spatial field (u0_ic, grad_u0) is n^d contiguous FP64 in the same node
+ * order.  All vector pointers are DEVICE pointers owned by the caller and
+ * must not alias each other unless stated.  Calls are asynchronous on the
+ * stream given to st_setup except where a host result is returned (norms,
+ * iteration counts), which synchronises that stream.
+ *
+ * Levels are numbered as in the paper (Section 2): L = 0 is the coarsest
+ * (one time step by default), L = st_num_levels() - 1 the finest.
+ *
+ * Errors: every int-returning call returns ST_OK (0) or one of the ST_E*
+ * codes; nothing throws across this interface.  st_last_error() returns a
+ * message for the last failure on that handle.  ST_ECUDA leaves the handle
+ * usable only for st_destroy.
+ */
+#ifndef STMG_H
+#define STMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ST_OK        0
+#define ST_EINVAL    1   /* bad argument: n != 2^k-1, N not a power of 2, p_t out of range, T <= 0, null pointer */
+#define ST_ENOMEM    2   /* device allocation failed or exceeds st_options.max_workspace_bytes */
+#define ST_ENOTCONV  3   /* maxit reached before rtol, or the residual grew by 1e6 */
+#define ST_ENAN      4   /* a residual norm was NaN or Inf */
+#define ST_ECUDA     5   /* a CUDA runtime call failed */
+
+#define ST_FP64      0   /* every kernel in FP64 */
+#define ST_MIXED     1   /* FP64 outer residual / update / coarsest solve, FP32 V-cycle */
+
+#define ST_AUTO      0   /* the paper's rule (Section 4): full iff mu_L >= mu*_{p_t} */
+#define ST_SEMI      1   /* always semi-coarsen in time */
+#define ST_FULL      2   /* full space-time coarsening whenever n_L >= 3 */
+
+#define ST_INIT_GIVEN 1  /* st_solve flag: u holds the initial iterate (else u^0 = 0) */
+
+#define ST_MAX_PT    3   /* largest supported DG degree p_t (q <= 4) */
+
+typedef struct st_mesh {
+  int dim;  /* 1, 2 or 3 */
+  int n;    /* interior nodes per axis, 2^k - 1, k >= 1 */
+} st_mesh;
+
+typedef struct st_options {
+  int nu1, nu2;          /* pre-/post-smoothing steps (Section 2), default 2, 2 */
+  double omega;          /* block-Jacobi damping omega_t (eq. chap4_smoother), default 1/2 (Lemma 21) */
+  double rtol;           /* stop when ||r_k|| <= rtol ||r_0|| (Section 2), default 1e-8 */
+  int maxit;             /* maximum V-cycles / refinement steps, default 50 */
+  int precision;         /* ST_FP64 or ST_MIXED */
+  int coarsening;        /* ST_AUTO, ST_SEMI or ST_FULL */
+  int coarsest_steps;    /* time steps on the coarsest level, power of 2, default 1 (Section 2) */
+  int inner_cycles;      /* ST_MIXED: FP32 V-cycles per FP64 refinement step, default 1 */
+  size_t max_workspace_bytes;  /* 0 = unlimited; setup fails with ST_ENOMEM above it */
+} st_options;
+
+typedef struct st_handle st_handle;
+
+/* Fill *opt with the defaults listed above. */
+void st_default_options(st_options* opt);
+
+/* Build the space-time hierarchy for the problem of Section 1 and allocate
+ * its device workspace.  Coarsening follows Section 4 (mu_L = tau_L / h_L^2
+ * against mu* of Remark chap4_remarkCriticalDiscretizationParameter) until
+ * N_L = coarsest_steps.  cuda_stream: a cudaStream_t (NULL = default stream)
+ * used by every later call on this handle.  On success *out owns the handle.
+ * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
+int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt,
+             void* cuda_stream, st_handle** out);
+
+/* Free the handle and its device workspace (NULL is ignored). */
+void st_destroy(st_handle* h);
+
+/* Message of the last error on this handle ("" if none; static text for NULL). */
+const char* st_last_error(const st_handle* h);
+
+/* Number of unknowns N q n^d of the finest level. */
+size_t st_ndof(const st_handle* h);
+
+int st_num_levels(const st_handle* h);
+
+/* Level L (0 = coarsest): time steps, nodes per axis, mu_L = tau_L/h_L^2 and
+ * whether level L was obtained from L+1 by full coarsening (1), semi (0), or
+ * is the finest (-1).  Any output pointer may be NULL.  Errors: ST_EINVAL. */
+int st_level_info(const st_handle* h, int L, int* N_L, int* n_L, double* mu_L, int* full);
+
+/* r = f + IC - L u on the finest level (system chap4_generalLinearSystem),
+ * where IC adds psi_k(t_0^+) (M_h u0_ic) to block 1 (the n = 0 term of eq.
+ * (equation1)); u0_ic may be NULL (zero initial value).  r may not alias u. */
+int st_residual(st_handle* h, const double* f, const double* u0_ic, const double* u, double* r);
+
+/* One V-cycle (gamma = 1, Section 2) on L u = f + IC for the finest level, in
+ * place on u.  With ST_MIXED this is one refinement step: FP64 residual,
+ * inner_cycles FP32 V-cycles on the scaled residual, FP64 update. */
+int st_vcycle(st_handle* h, double* u, const double* f, const double* u0_ic);
+
+/* Solve L u = f + IC to ||r|| <= rtol ||r_0|| by repeated V-cycles (Section 2).
+ * flags: ST_INIT_GIVEN to start from the given u, else u^0 = 0.  *iters gets
+ * the number of cycles, *relres ||r|| / ||r_0|| (either may be NULL).
+ * Returns ST_ENOTCONV / ST_ENAN (u then holds the last iterate). */
+int st_solve(st_handle* h, const double* f, const double* u0_ic, double* u, int flags,
+             int* iters, double* relres);
+
+/* Adjoint solve L^T lambda = g (transposed, backward-in-time system) with the
+ * same hierarchy and transfers.  grad_u0 (may be NULL) receives
+ * M_h sum_k psi_k(t_0^+) lambda_{1,k}, the derivative of a loss with
+ * dJ/du = g with respect to u0_ic; lambda itself is dJ/df. */
+int st_adjoint_solve(st_handle* h, const double* g, double* lambda, double* grad_u0,
+                     int* iters, double* relres);
+
+/* ---- step-level entry points (one step of the cycle on one level) ----
+ * adjoint != 0 selects the transposed operator.  Vectors have the level's
+ * layout (N_L, q, n_L^d). */
+
+/* r = f - L_L u (no IC term) or f - L_L^T u. */
+int st_level_residual(st_handle* h, int L, int adjoint, const double* f, const double* u, double* r);
+
+/* d = D_L^{-1} r (exact block inverse of diag{A}, Section 3.1), in FP64. */
+int st_level_block_solve(st_handle* h, int L, int adjoint, const double* r, double* d);
+
+/* nu damped block-Jacobi steps u <- u + omega D^{-1}(f - L u) (eq. chap4_smoother). */
+int st_level_smooth(st_handle* h, int L, int adjoint, int nu, const double* f, double* u);
+
+/* f_c = R r: level L (L >= 1) to level L-1, eqs. (chap4_restrictionTime),
+ * (chap4_spaceRestrictionProlongation); semi or full as the hierarchy says. */
+int st_level_restrict(st_handle* h, int L, const double* r_fine, double* f_coarse);
+
+/* u_fine += P e_c, P = R^T, level L-1 to level L. */
+int st_level_prolong(st_handle* h, int L, const double* e_coarse, double* u_fine);
+
+/* Exact solve on the coarsest level (Section 2): one step via the block
+ * inverse, several by forward (adjoint: backward) substitution. */
+int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u);
+
+/* ||x||_2 of n FP64 values (deterministic order); synchronises. */
+int st_norm2(st_handle* h, const double* x, size_t n, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STMG_H */

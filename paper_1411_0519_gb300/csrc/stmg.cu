@@ -1,0 +1,819 @@
+// Host side of the space-time multigrid library: handle, level hierarchy,
+// V-cycle driver, solve loops and the C ABI declared in include/stmg.h.
+//
+// Method: Gander & Neumueller, arXiv:1411.0519.  Section 2 (V-cycle, damped
+// block Jacobi, P = R^T, exact coarsest solve), Section 3 (exact block inverse,
+// transfers), Section 4 (coarsening rule mu_L >= mu*).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "stmg.h"
+#include "stmg_kernels.cuh"
+
+using stmg::TimeCoef;
+
+namespace {
+
+constexpr int kQmax = ST_MAX_PT + 1;
+
+// ---------------------------------------------------------------------------
+// Host-side time data in the Legendre basis (Section 1 definitions evaluated
+// in closed form for P_k on the reference slab):
+//   K_tau[k][l] = 1 - 2 [l < k and k - l odd]    (from int P_l P_k' = 2 there)
+//   M_tau[k][k] = tau / (2k + 1),  psi_k(start) = (-1)^k,  psi_k(end) = 1.
+// R1^T, R2^T (eq. chap4_restrictionTime) are the Legendre coefficients of the
+// coarse P_l restricted to each fine half, by Gauss-Legendre quadrature.
+// ---------------------------------------------------------------------------
+double legendre_P(int k, double s) {
+  double p0 = 1.0, p1 = s;
+  if (k == 0) return p0;
+  for (int m = 1; m < k; ++m) {
+    double p2 = ((2.0 * m + 1.0) * s * p1 - m * p0) / (m + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+void gauss_legendre(int npts, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(npts, 0.0);
+  w.assign(npts, 0.0);
+  for (int i = 0; i < npts; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (npts + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p = legendre_P(npts, z), pm = legendre_P(npts - 1, z);
+      double dp = npts * (z * p - pm) / (z * z - 1.0);
+      double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p = legendre_P(npts, z), pm = legendre_P(npts - 1, z);
+    double dp = npts * (z * p - pm) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+struct HostTime {
+  int q;
+  double K[kQmax * kQmax], Mh[kQmax], st[kQmax], en[kQmax], R1[kQmax * kQmax], R2[kQmax * kQmax];
+};
+
+HostTime make_time(int p_t) {
+  HostTime t{};
+  const int q = p_t + 1;
+  t.q = q;
+  for (int k = 0; k < q; ++k) {
+    for (int l = 0; l < q; ++l) t.K[k * q + l] = (l < k && ((k - l) & 1)) ? -1.0 : 1.0;
+    t.Mh[k] = 1.0 / (2.0 * k + 1.0);
+    t.st[k] = (k & 1) ? -1.0 : 1.0;
+    t.en[k] = 1.0;
+  }
+  std::vector<double> gx, gw;
+  gauss_legendre(q + 2, gx, gw);
+  // RsT[k][l] = (2k+1)/2 int_{-1}^{1} P_l(c(s)) P_k(s) ds, c(s) = (s -+ 1)/2;
+  // R_s[k][l] = RsT[l][k] (coarse k <- fine l).
+  for (int k = 0; k < q; ++k) {
+    for (int l = 0; l < q; ++l) {
+      double a1 = 0.0, a2 = 0.0;
+      for (size_t g = 0; g < gx.size(); ++g) {
+        a1 += gw[g] * legendre_P(l, 0.5 * (gx[g] - 1.0)) * legendre_P(k, gx[g]);
+        a2 += gw[g] * legendre_P(l, 0.5 * (gx[g] + 1.0)) * legendre_P(k, gx[g]);
+      }
+      const double c = 0.5 * (2.0 * k + 1.0);
+      t.R1[l * q + k] = c * a1;   // transpose: row = coarse l, column = fine k
+      t.R2[l * q + k] = c * a2;
+    }
+  }
+  return t;
+}
+
+template <typename T, int Q>
+TimeCoef<T, Q> to_coef(const HostTime& t) {
+  TimeCoef<T, Q> c{};
+  for (int i = 0; i < Q * Q; ++i) {
+    c.K[i] = (T)t.K[i];
+    c.R1[i] = (T)t.R1[i];
+    c.R2[i] = (T)t.R2[i];
+  }
+  for (int i = 0; i < Q; ++i) {
+    c.Mh[i] = (T)t.Mh[i];
+    c.st[i] = (T)t.st[i];
+    c.en[i] = (T)t.en[i];
+  }
+  return c;
+}
+
+// (p, p+1) subdiagonal Pade approximation of exp(z) (textbook closed form);
+// mu* solves R(-3 mu) = sqrt(2) - 1 (Remark on the critical parameter).
+double pade(int p, double z) {
+  const int m = p, k = p + 1;
+  auto fact = [](int a) { double r = 1.0; for (int i = 2; i <= a; ++i) r *= i; return r; };
+  double num = 0.0, den = 0.0;
+  for (int j = 0; j <= m; ++j)
+    num += fact(m + k - j) * fact(m) / (fact(m + k) * fact(j) * fact(m - j)) * std::pow(z, j);
+  for (int j = 0; j <= k; ++j)
+    den += fact(m + k - j) * fact(k) / (fact(m + k) * fact(j) * fact(k - j)) * std::pow(-z, j);
+  return num / den;
+}
+
+double mu_star(int p) {
+  const double target = std::sqrt(2.0) - 1.0;
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (pade(p, -3.0 * mid) > target) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+template <typename T>
+struct Tables {
+  T* mval = nullptr;  // m_k = h/3 (2 + cos(k pi / Nf)), k = 1..n
+  T* kval = nullptr;  // kappa_k = 2/h (1 - cos(k pi / Nf))
+  T* sinp = nullptr;  // sin(j pi / Nf), j = 0..Nf-1
+  T* twc = nullptr;   // cos(2 pi k / Nf), k = 0..Nf-1
+  T* tws = nullptr;   // sin(2 pi k / Nf)
+};
+
+template <typename T>
+struct Vecs {
+  T* u = nullptr;
+  T* f = nullptr;
+  T* r = nullptr;
+};
+
+struct Level {
+  int N = 0, n = 0;
+  double tau = 0, h = 0, mu = 0;
+  int coarsen_full = 0;   // how this level is restricted to level L-1 (L >= 1)
+  int64_t Nx = 0, ndof = 0;
+  Vecs<double> v64;
+  Vecs<float> v32;
+  Tables<double> t64;
+  Tables<float> t32;
+};
+
+}  // namespace
+
+struct st_handle {
+  int d = 0, p_t = 0, q = 0, N = 0;
+  double T = 0;
+  st_options opt{};
+  cudaStream_t stream = nullptr;
+  std::vector<Level> levels;   // 0 = coarsest
+  HostTime tm{};
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double* partial = nullptr;   // norm partial sums
+  double* dnorm = nullptr;     // device result of a norm
+  double* hnorm = nullptr;     // pinned host copy
+  double* coarse64_u = nullptr;  // mixed precision: FP64 copies for the coarsest solve
+  double* coarse64_f = nullptr;
+  double* coarse64_r = nullptr;
+  double* r64 = nullptr;         // mixed precision: finest FP64 residual
+  std::string err;
+};
+
+namespace {
+
+constexpr int kNormBlocks = 1024;
+constexpr int kThreads = 256;
+
+struct Fail {
+  int code;
+};
+
+void check(st_handle* h, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    h->err = std::string(what) + ": " + cudaGetErrorString(e);
+    throw Fail{ST_ECUDA};
+  }
+}
+
+void fail(st_handle* h, int code, const std::string& msg) {
+  h->err = msg;
+  throw Fail{code};
+}
+
+template <typename T>
+T* dalloc(st_handle* h, size_t count) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  if (h->opt.max_workspace_bytes && h->bytes + bytes > h->opt.max_workspace_bytes)
+    fail(h, ST_ENOMEM, "device workspace would exceed max_workspace_bytes");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(h, ST_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(p);
+  h->bytes += bytes;
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+void upload(st_handle* h, T* dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  check(h, cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice), "upload table");
+}
+
+template <typename T>
+void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
+  const int n = lv.n, Nf = n + 1;
+  std::vector<double> mv(n), kv(n), sp(Nf), tc(Nf), ts(Nf);
+  for (int k = 1; k <= n; ++k) {
+    double c = std::cos(k * M_PI / Nf);
+    mv[k - 1] = lv.h / 3.0 * (2.0 + c);
+    kv[k - 1] = 2.0 / lv.h * (1.0 - c);
+  }
+  for (int j = 0; j < Nf; ++j) {
+    sp[j] = std::sin(j * M_PI / Nf);
+    tc[j] = std::cos(2.0 * M_PI * j / Nf);
+    ts[j] = std::sin(2.0 * M_PI * j / Nf);
+  }
+  tb.mval = dalloc<T>(h, n);
+  tb.kval = dalloc<T>(h, n);
+  tb.sinp = dalloc<T>(h, Nf);
+  tb.twc = dalloc<T>(h, Nf);
+  tb.tws = dalloc<T>(h, Nf);
+  upload(h, tb.mval, mv);
+  upload(h, tb.kval, kv);
+  upload(h, tb.sinp, sp);
+  upload(h, tb.twc, tc);
+  upload(h, tb.tws, ts);
+}
+
+template <typename T> Vecs<T>& vecs(Level& lv);
+template <> Vecs<double>& vecs<double>(Level& lv) { return lv.v64; }
+template <> Vecs<float>& vecs<float>(Level& lv) { return lv.v32; }
+template <typename T> Tables<T>& tables(Level& lv);
+template <> Tables<double>& tables<double>(Level& lv) { return lv.t64; }
+template <> Tables<float>& tables<float>(Level& lv) { return lv.t32; }
+
+inline unsigned blocks_for(int64_t n, int threads = kThreads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+// ------------------------------------------------------------------ dispatch
+template <typename T, int D, int Q>
+void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r,
+                       int s0, int ns) {
+  auto tc = to_coef<T, Q>(h->tm);
+  dim3 grid(blocks_for(lv.Nx), 1);
+  for (int c = 0; c < ns; c += 65535) {
+    grid.y = std::min(65535, ns - c);
+    if (adj)
+      stmg::k_residual<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c,
+                                                                         (T)lv.tau, (T)lv.h, tc);
+    else
+      stmg::k_residual<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c,
+                                                                          (T)lv.tau, (T)lv.h, tc);
+  }
+}
+
+template <typename T, int D, int Q>
+void launch_mode_solve_t(st_handle* h, Level& lv, bool adj, const T* in, T* out, int ns, T scale) {
+  auto tc = to_coef<T, Q>(h->tm);
+  Tables<T>& tb = tables<T>(lv);
+  dim3 grid(blocks_for(lv.Nx), 1);
+  for (int c = 0; c < ns; c += 65535) {
+    grid.y = std::min(65535, ns - c);
+    const int64_t off = (int64_t)c * Q * lv.Nx;
+    if (adj)
+      stmg::k_mode_solve<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(in + off, out + off, lv.n, grid.y, tb.mval,
+                                                                          tb.kval, (T)lv.tau, scale, tc);
+    else
+      stmg::k_mode_solve<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(in + off, out + off, lv.n, grid.y,
+                                                                           tb.mval, tb.kval, (T)lv.tau, scale, tc);
+  }
+}
+
+template <typename T, int D, int Q>
+void launch_restrict_t(st_handle* h, const Level& fine, const Level& coarse, const T* r, T* fc) {
+  auto tc = to_coef<T, Q>(h->tm);
+  dim3 grid(blocks_for(coarse.Nx), coarse.N);
+  if (fine.coarsen_full)
+    stmg::k_restrict<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
+  else
+    stmg::k_restrict<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
+}
+
+template <typename T, int D, int Q>
+void launch_prolong_t(st_handle* h, const Level& fine, const Level& coarse, const T* ec, T* uf) {
+  auto tc = to_coef<T, Q>(h->tm);
+  dim3 grid(blocks_for(fine.Nx), fine.N);
+  if (fine.coarsen_full)
+    stmg::k_prolong<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
+  else
+    stmg::k_prolong<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
+}
+
+template <typename T, int D, int Q>
+void launch_ic_grad_t(st_handle* h, const Level& lv, const T* lam, T* g) {
+  auto tc = to_coef<T, Q>(h->tm);
+  stmg::k_ic_gradient<T, D, Q><<<blocks_for(lv.Nx), kThreads, 0, h->stream>>>(lam, g, lv.n, (T)lv.h, tc);
+}
+
+#define STMG_DISPATCH(FN, ...)                                                   \
+  do {                                                                           \
+    switch (h->d * 10 + h->q) {                                                  \
+      case 11: FN<T, 1, 1>(__VA_ARGS__); break;                                  \
+      case 12: FN<T, 1, 2>(__VA_ARGS__); break;                                  \
+      case 13: FN<T, 1, 3>(__VA_ARGS__); break;                                  \
+      case 14: FN<T, 1, 4>(__VA_ARGS__); break;                                  \
+      case 21: FN<T, 2, 1>(__VA_ARGS__); break;                                  \
+      case 22: FN<T, 2, 2>(__VA_ARGS__); break;                                  \
+      case 23: FN<T, 2, 3>(__VA_ARGS__); break;                                  \
+      case 24: FN<T, 2, 4>(__VA_ARGS__); break;                                  \
+      case 31: FN<T, 3, 1>(__VA_ARGS__); break;                                  \
+      case 32: FN<T, 3, 2>(__VA_ARGS__); break;                                  \
+      case 33: FN<T, 3, 3>(__VA_ARGS__); break;                                  \
+      case 34: FN<T, 3, 4>(__VA_ARGS__); break;                                  \
+      default: fail(h, ST_EINVAL, "unsupported (dim, q)");                       \
+    }                                                                            \
+  } while (0)
+
+template <typename T>
+void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0 = 0,
+              int ns = -1) {
+  if (ns < 0) ns = lv.N;
+  STMG_DISPATCH(launch_residual_t, h, lv, adj, f, u, u0, r, s0, ns);
+}
+
+template <typename T>
+void mode_solve(st_handle* h, Level& lv, bool adj, const T* in, T* out, int ns, T scale) {
+  STMG_DISPATCH(launch_mode_solve_t, h, lv, adj, in, out, ns, scale);
+}
+
+template <typename T>
+void restrict_to(st_handle* h, int L, const T* r, T* fc) {
+  Level& fine = h->levels[L];
+  Level& coarse = h->levels[L - 1];
+  STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
+}
+
+template <typename T>
+void prolong_add(st_handle* h, int L, const T* ec, T* uf) {
+  Level& fine = h->levels[L];
+  Level& coarse = h->levels[L - 1];
+  STMG_DISPATCH(launch_prolong_t, h, fine, coarse, ec, uf);
+}
+
+// DST-I along every axis of `ns` time steps of data (in place).
+template <typename T>
+void dst_all_axes(st_handle* h, Level& lv, T* data, int ns, T scale_last) {
+  const int n = lv.n, Nf = n + 1, D = h->d;
+  int logh = 0;
+  while ((1 << (logh + 1)) <= Nf / 2) ++logh;
+  const int W = (Nf >= 512 && sizeof(T) == 8) ? 16 : 32;
+  const int nwarps = 8;
+  const size_t smem = (size_t)(W + nwarps) * Nf * sizeof(T);
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    check(h, cudaFuncSetAttribute(stmg::k_dst_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+          "cudaFuncSetAttribute");
+    attr_set[sizeof(T) == 8] = true;
+  }
+  Tables<T>& tb = tables<T>(lv);
+  stmg::DstTables<T> dt{tb.sinp, tb.twc, tb.tws};
+  const int64_t slabs = (int64_t)ns * h->q;
+  int64_t inner = 1;
+  for (int a = 0; a < D; ++a) {
+    const int64_t nlines = slabs * lv.Nx / n;
+    const int64_t stride = (a == 0) ? 1 : inner;
+    const unsigned grid = (unsigned)((nlines + W - 1) / W);
+    const T scale = (a == D - 1) ? scale_last : T(1);
+    stmg::k_dst_axis<T><<<grid, nwarps * 32, smem, h->stream>>>(data, n, nlines, (a == 0) ? 1 : inner, stride, W,
+                                                                 scale, dt, logh);
+    inner *= n;
+  }
+}
+
+// d = D^{-1} r on time steps [s0, s0 + ns) (exact block inverse: DST, per-mode
+// solve, inverse DST).  r and d may be the same buffer.
+template <typename T>
+void block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d, int s0, int ns) {
+  const int64_t off = (int64_t)s0 * h->q * lv.Nx;
+  const int64_t cnt = (int64_t)ns * h->q * lv.Nx;
+  if (r != d) check(h, cudaMemcpyAsync(d + off, r + off, cnt * sizeof(T), cudaMemcpyDeviceToDevice, h->stream), "copy");
+  dst_all_axes<T>(h, lv, d + off, ns, T(1));
+  const T scale = (T)std::pow(2.0 / (lv.n + 1), h->d);
+  mode_solve<T>(h, lv, adj, d + off, d + off, ns, scale);
+  dst_all_axes<T>(h, lv, d + off, ns, T(1));
+}
+
+template <typename T>
+void axpy(st_handle* h, T* y, const T* x, T a, int64_t n) {
+  stmg::k_axpy<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, n);
+}
+
+// One damped block-Jacobi step (eq. chap4_smoother).
+template <typename T>
+void smooth_step(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
+  residual<T>(h, lv, adj, f, u, u0, work);
+  block_solve<T>(h, lv, adj, work, work, 0, lv.N);
+  axpy<T>(h, u, work, (T)h->opt.omega, lv.ndof);
+}
+
+// Exact coarsest solve (Section 2): one step via the block inverse, several by
+// forward (adjoint: backward) substitution, in the vector's own precision.
+template <typename T>
+void coarsest_solve_t(st_handle* h, bool adj, T* u, const T* f, T* work) {
+  Level& lv = h->levels[0];
+  if (lv.N == 1) {
+    block_solve<T>(h, lv, adj, f, u, 0, 1);
+    return;
+  }
+  check(h, cudaMemsetAsync(u, 0, lv.ndof * sizeof(T), h->stream), "memset");
+  for (int i = 0; i < lv.N; ++i) {
+    const int s = adj ? lv.N - 1 - i : i;
+    residual<T>(h, lv, adj, f, u, (const T*)nullptr, work, s, 1);
+    block_solve<T>(h, lv, adj, work, u, s, 1);
+  }
+}
+
+void coarsest_solve_mixed(st_handle* h, bool adj, float* u, const float* f, float* work) {
+  (void)work;
+  Level& lv = h->levels[0];
+  const int64_t n = lv.ndof;
+  stmg::k_cast_up<<<blocks_for(n), kThreads, 0, h->stream>>>(h->coarse64_f, f, n);
+  coarsest_solve_t<double>(h, adj, h->coarse64_u, h->coarse64_f, h->coarse64_r);
+  stmg::k_cast_down<<<blocks_for(n), kThreads, 0, h->stream>>>(u, h->coarse64_u, 1.0, n);
+}
+
+template <typename T>
+void coarsest_solve(st_handle* h, bool adj, T* u, const T* f, T* work);
+template <>
+void coarsest_solve<double>(st_handle* h, bool adj, double* u, const double* f, double* work) {
+  coarsest_solve_t<double>(h, adj, u, f, work);
+}
+template <>
+void coarsest_solve<float>(st_handle* h, bool adj, float* u, const float* f, float* work) {
+  coarsest_solve_mixed(h, adj, u, f, work);
+}
+
+// V-cycle (gamma = 1) on level L for L u = f (+ the initial-value term u0 on
+// the finest level), Section 2.
+template <typename T>
+void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0) {
+  Level& lv = h->levels[L];
+  T* work = vecs<T>(lv).r;
+  if (L == 0) {
+    coarsest_solve<T>(h, adj, u, f, work);
+    return;
+  }
+  for (int i = 0; i < h->opt.nu1; ++i) smooth_step<T>(h, lv, adj, u, f, u0, work);
+  residual<T>(h, lv, adj, f, u, u0, work);
+  Level& cl = h->levels[L - 1];
+  Vecs<T>& cv = vecs<T>(cl);
+  restrict_to<T>(h, L, work, cv.f);
+  check(h, cudaMemsetAsync(cv.u, 0, cl.ndof * sizeof(T), h->stream), "memset");
+  vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr);
+  prolong_add<T>(h, L, cv.u, u);
+  for (int i = 0; i < h->opt.nu2; ++i) smooth_step<T>(h, lv, adj, u, f, u0, work);
+}
+
+template <typename T>
+double norm2(st_handle* h, const T* x, int64_t n) {
+  stmg::k_sumsq_partial<T><<<kNormBlocks, kThreads, 0, h->stream>>>(x, n, h->partial);
+  stmg::k_sum_final<<<1, 1024, 0, h->stream>>>(h->partial, kNormBlocks, h->dnorm);
+  check(h, cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm copy");
+  check(h, cudaStreamSynchronize(h->stream), "norm sync");
+  return std::sqrt(*h->hnorm);
+}
+
+Level& finest(st_handle* h) { return h->levels.back(); }
+
+// One FP64 refinement step of the mixed-precision form: given the FP64 residual
+// r (norm s), solve L e = r / s approximately with FP32 V-cycles and update
+// u += s e in FP64.
+void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
+  Level& lv = finest(h);
+  const int L = (int)h->levels.size() - 1;
+  Vecs<float>& v = lv.v32;
+  stmg::k_cast_down<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(v.f, r, 1.0 / s,
+                                                                                                   lv.ndof);
+  check(h, cudaMemsetAsync(v.u, 0, lv.ndof * sizeof(float), h->stream), "memset");
+  for (int c = 0; c < std::max(1, h->opt.inner_cycles); ++c) vcycle<float>(h, L, adj, v.u, v.f, (const float*)nullptr);
+  stmg::k_axpy_up<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(u, v.u, s, lv.ndof);
+}
+
+int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double* u, int flags, int* iters,
+               double* relres) {
+  Level& lv = finest(h);
+  const int L = (int)h->levels.size() - 1;
+  if (!(flags & ST_INIT_GIVEN)) check(h, cudaMemsetAsync(u, 0, lv.ndof * sizeof(double), h->stream), "memset");
+  double* r = (h->opt.precision == ST_MIXED) ? h->r64 : lv.v64.r;
+  residual<double>(h, lv, adj, f, u, u0, r);
+  const double r0 = norm2<double>(h, r, lv.ndof);
+  double rn = r0;
+  int it = 0;
+  int status = ST_OK;
+  if (!std::isfinite(r0)) status = ST_ENAN;
+  while (status == ST_OK && r0 > 0.0 && rn > h->opt.rtol * r0) {
+    if (it >= h->opt.maxit) { status = ST_ENOTCONV; h->err = "maxit reached"; break; }
+    if (h->opt.precision == ST_MIXED) {
+      mixed_step(h, adj, u, r, rn);
+    } else {
+      vcycle<double>(h, L, adj, u, f, u0);
+    }
+    ++it;
+    residual<double>(h, lv, adj, f, u, u0, r);
+    rn = norm2<double>(h, r, lv.ndof);
+    if (!std::isfinite(rn)) { status = ST_ENAN; h->err = "residual norm is not finite"; break; }
+    if (rn > 1e6 * r0) { status = ST_ENOTCONV; h->err = "residual grew by 1e6"; break; }
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
+  return status;
+}
+
+bool is_pow2m1(int n) { return n >= 1 && ((n + 1) & n) == 0; }
+bool is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+template <typename F>
+int guarded(st_handle* h, F&& fn) {
+  if (!h) return ST_EINVAL;
+  try {
+    h->err.clear();
+    return fn();
+  } catch (const Fail& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ST_ENOMEM;
+  } catch (...) {
+    h->err = "unexpected error";
+    return ST_ECUDA;
+  }
+}
+
+void after_launch(st_handle* h) { check(h, cudaGetLastError(), "kernel launch"); }
+
+int level_index(st_handle* h, int L) {
+  if (L < 0 || L >= (int)h->levels.size()) fail(h, ST_EINVAL, "level out of range");
+  return L;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+void st_default_options(st_options* o) {
+  if (!o) return;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega = 0.5;
+  o->rtol = 1e-8;
+  o->maxit = 50;
+  o->precision = ST_FP64;
+  o->coarsening = ST_AUTO;
+  o->coarsest_steps = 1;
+  o->inner_cycles = 1;
+  o->max_workspace_bytes = 0;
+}
+
+int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt, void* cuda_stream,
+             st_handle** out) {
+  if (!out) return ST_EINVAL;
+  *out = nullptr;
+  st_handle* h = new (std::nothrow) st_handle();
+  if (!h) return ST_ENOMEM;
+  int rc = guarded(h, [&]() -> int {
+    if (!mesh || mesh->dim < 1 || mesh->dim > 3 || !is_pow2m1(mesh->n)) fail(h, ST_EINVAL, "mesh: dim 1..3, n = 2^k-1");
+    if (p_t < 0 || p_t > ST_MAX_PT) fail(h, ST_EINVAL, "p_t out of range");
+    if (!is_pow2(N)) fail(h, ST_EINVAL, "N must be a power of 2");
+    if (!(T > 0.0) || !std::isfinite(T)) fail(h, ST_EINVAL, "T must be positive");
+    if (opt) h->opt = *opt; else st_default_options(&h->opt);
+    if (h->opt.nu1 < 0 || h->opt.nu2 < 0 || !(h->opt.omega > 0.0) || h->opt.maxit < 0 || !(h->opt.rtol >= 0.0))
+      fail(h, ST_EINVAL, "bad options");
+    if (h->opt.precision != ST_FP64 && h->opt.precision != ST_MIXED) fail(h, ST_EINVAL, "bad precision");
+    if (h->opt.coarsening < ST_AUTO || h->opt.coarsening > ST_FULL) fail(h, ST_EINVAL, "bad coarsening");
+    if (h->opt.coarsest_steps < 1) h->opt.coarsest_steps = 1;
+    if (!is_pow2(h->opt.coarsest_steps) || h->opt.coarsest_steps > N) fail(h, ST_EINVAL, "bad coarsest_steps");
+    h->d = mesh->dim;
+    h->p_t = p_t;
+    h->q = p_t + 1;
+    h->N = N;
+    h->T = T;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->tm = make_time(p_t);
+    // hierarchy, finest first, then reversed to the paper's numbering (0 = coarsest)
+    const double ms = mu_star(p_t);
+    std::vector<Level> lv;
+    int Nl = N, nl = mesh->n;
+    double tau = T / N;
+    while (true) {
+      Level L;
+      L.N = Nl;
+      L.n = nl;
+      L.tau = tau;
+      L.h = 1.0 / (nl + 1);
+      L.mu = tau / (L.h * L.h);
+      L.Nx = 1;
+      for (int a = 0; a < h->d; ++a) L.Nx *= nl;
+      L.ndof = (int64_t)Nl * h->q * L.Nx;
+      if (Nl <= h->opt.coarsest_steps) {
+        lv.push_back(L);
+        break;
+      }
+      bool full;
+      if (h->opt.coarsening == ST_SEMI) full = false;
+      else if (h->opt.coarsening == ST_FULL) full = nl >= 3;
+      else full = (L.mu >= ms * (1.0 - 1e-12)) && nl >= 3;
+      L.coarsen_full = full ? 1 : 0;
+      lv.push_back(L);
+      Nl /= 2;
+      tau *= 2.0;
+      if (full) nl = (nl - 1) / 2;
+    }
+    std::reverse(lv.begin(), lv.end());
+    h->levels = lv;
+    const int nlev = (int)h->levels.size();
+    const bool mixed = h->opt.precision == ST_MIXED;
+    for (int L = 0; L < nlev; ++L) {
+      Level& l = h->levels[L];
+      if (L < nlev - 1) {
+        l.v64.u = dalloc<double>(h, l.ndof);
+        l.v64.f = dalloc<double>(h, l.ndof);
+      }
+      l.v64.r = dalloc<double>(h, l.ndof);
+      make_tables<double>(h, l, l.t64);
+      if (mixed) {
+        l.v32.u = dalloc<float>(h, l.ndof);
+        l.v32.f = dalloc<float>(h, l.ndof);
+        l.v32.r = dalloc<float>(h, l.ndof);
+        make_tables<float>(h, l, l.t32);
+      }
+    }
+    if (mixed) {
+      Level& c = h->levels[0];
+      h->coarse64_u = dalloc<double>(h, c.ndof);
+      h->coarse64_f = dalloc<double>(h, c.ndof);
+      h->coarse64_r = dalloc<double>(h, c.ndof);
+      h->r64 = finest(h).v64.r;
+    }
+    h->partial = dalloc<double>(h, kNormBlocks);
+    h->dnorm = dalloc<double>(h, 1);
+    check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");
+    check(h, cudaDeviceSynchronize(), "setup sync");
+    return ST_OK;
+  });
+  if (rc != ST_OK) {
+    // keep the message readable through a temporary handle is not possible; print once
+    std::fprintf(stderr, "st_setup: %s\n", h->err.c_str());
+    st_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return ST_OK;
+}
+
+void st_destroy(st_handle* h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->hnorm) cudaFreeHost(h->hnorm);
+  delete h;
+}
+
+const char* st_last_error(const st_handle* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+size_t st_ndof(const st_handle* h) { return h ? (size_t)h->levels.back().ndof : 0; }
+
+int st_num_levels(const st_handle* h) { return h ? (int)h->levels.size() : 0; }
+
+int st_level_info(const st_handle* h, int L, int* N_L, int* n_L, double* mu_L, int* full) {
+  if (!h || L < 0 || L >= (int)h->levels.size()) return ST_EINVAL;
+  const Level& l = h->levels[L];
+  if (N_L) *N_L = l.N;
+  if (n_L) *n_L = l.n;
+  if (mu_L) *mu_L = l.mu;
+  if (full) *full = (L == (int)h->levels.size() - 1) ? -1 : h->levels[L + 1].coarsen_full;
+  return ST_OK;
+}
+
+int st_residual(st_handle* h, const double* f, const double* u0_ic, const double* u, double* r) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
+    residual<double>(h, finest(h), false, f, u, u0_ic, r);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_vcycle(st_handle* h, double* u, const double* f, const double* u0_ic) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u) fail(h, ST_EINVAL, "null pointer");
+    const int L = (int)h->levels.size() - 1;
+    if (h->opt.precision == ST_MIXED) {
+      Level& lv = finest(h);
+      residual<double>(h, lv, false, f, u, u0_ic, h->r64);
+      const double s = norm2<double>(h, h->r64, lv.ndof);
+      if (!std::isfinite(s)) fail(h, ST_ENAN, "residual norm is not finite");
+      if (s > 0.0) mixed_step(h, false, u, h->r64, s);
+    } else {
+      vcycle<double>(h, L, false, u, f, u0_ic);
+    }
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_solve(st_handle* h, const double* f, const double* u0_ic, double* u, int flags, int* iters, double* relres) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u) fail(h, ST_EINVAL, "null pointer");
+    int rc = solve_impl(h, false, f, u0_ic, u, flags, iters, relres);
+    after_launch(h);
+    return rc;
+  });
+}
+
+int st_adjoint_solve(st_handle* h, const double* g, double* lambda, double* grad_u0, int* iters, double* relres) {
+  return guarded(h, [&]() -> int {
+    if (!g || !lambda) fail(h, ST_EINVAL, "null pointer");
+    int rc = solve_impl(h, true, g, nullptr, lambda, 0, iters, relres);
+    if (grad_u0) {
+      using T = double;
+      STMG_DISPATCH(launch_ic_grad_t, h, finest(h), lambda, grad_u0);
+    }
+    after_launch(h);
+    return rc;
+  });
+}
+
+int st_level_residual(st_handle* h, int L, int adjoint, const double* f, const double* u, double* r) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
+    residual<double>(h, h->levels[level_index(h, L)], adjoint != 0, f, u, (const double*)nullptr, r);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_level_block_solve(st_handle* h, int L, int adjoint, const double* r, double* d) {
+  return guarded(h, [&]() -> int {
+    if (!r || !d) fail(h, ST_EINVAL, "null pointer");
+    Level& lv = h->levels[level_index(h, L)];
+    block_solve<double>(h, lv, adjoint != 0, r, d, 0, lv.N);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_level_smooth(st_handle* h, int L, int adjoint, int nu, const double* f, double* u) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u || nu < 0) fail(h, ST_EINVAL, "bad argument");
+    Level& lv = h->levels[level_index(h, L)];
+    for (int i = 0; i < nu; ++i) smooth_step<double>(h, lv, adjoint != 0, u, f, (const double*)nullptr, lv.v64.r);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_level_restrict(st_handle* h, int L, const double* r_fine, double* f_coarse) {
+  return guarded(h, [&]() -> int {
+    if (!r_fine || !f_coarse || level_index(h, L) < 1) fail(h, ST_EINVAL, "bad argument");
+    restrict_to<double>(h, L, r_fine, f_coarse);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_level_prolong(st_handle* h, int L, const double* e_coarse, double* u_fine) {
+  return guarded(h, [&]() -> int {
+    if (!e_coarse || !u_fine || level_index(h, L) < 1) fail(h, ST_EINVAL, "bad argument");
+    prolong_add<double>(h, L, e_coarse, u_fine);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u) fail(h, ST_EINVAL, "null pointer");
+    coarsest_solve_t<double>(h, adjoint != 0, u, f, h->levels[0].v64.r);
+    after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_norm2(st_handle* h, const double* x, size_t n, double* out) {
+  return guarded(h, [&]() -> int {
+    if (!x || !out) fail(h, ST_EINVAL, "null pointer");
+    *out = norm2<double>(h, x, (int64_t)n);
+    return ST_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,626 @@
+// Device kernels of the space-time multigrid V-cycle (FP64 and FP32).
+//
+// Vector layout: index ((s * Q + l) * Nx + j), time step s, time dof l,
+// spatial node j = (z * n + y) * n + x with x fastest, Nx = n^D.
+//
+// Time matrices (Section 1) in the Legendre basis are passed by value in
+// TimeCoef: K = K_tau (dimensionless), Mh = diag(M_tau) / tau, st = psi_k at
+// the slab start, en = psi_k at the slab end (so N_tau = st en^T), and the
+// time restriction blocks R1, R2 of eq. (chap4_restrictionTime).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace stmg {
+
+template <typename T, int Q>
+struct TimeCoef {
+  T K[Q * Q];    // K_tau[k][l] row-major, k = test (row), l = trial
+  T Mh[Q];       // M_tau[k][k] / tau
+  T st[Q];       // psi_k(t_{n-1}^+)
+  T en[Q];       // psi_k(t_n^-)
+  T R1[Q * Q];   // coarse k <- fine l (first fine slab)
+  T R2[Q * Q];   // coarse k <- fine l (second fine slab)
+};
+
+// ---------------------------------------------------------------------------
+// Spatial stencils of M_h and K_h for Q1 (P1 in 1D), Section 1 / Section 3:
+// M_1 = h/6 [1 4 1], K_1 = 1/h [-1 2 -1], M_h = (x)_a M_1,
+// K_h = sum_a K_1 (axis a) (x)_{b != a} M_1.  Nodes outside [0, n) are zero
+// (homogeneous Dirichlet).
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+struct Stencil {
+  // weights for offset o in {-1,0,1}: index o + 1
+  T m1[3], k1[3];
+  __device__ __forceinline__ Stencil(T h) {
+    m1[0] = h / T(6); m1[1] = T(4) * h / T(6); m1[2] = h / T(6);
+    k1[0] = T(-1) / h; k1[1] = T(2) / h; k1[2] = T(-1) / h;
+  }
+};
+
+// Apply M_h and K_h at node (ix, iy, iz) to a field given by an accessor
+// get(j) -> T (flat spatial index j).  Out-of-range neighbours contribute 0.
+template <typename T, int D, typename Get>
+__device__ __forceinline__ void apply_mk(const Stencil<T, D>& S, int n, int ix, int iy, int iz,
+                                         Get get, T& mu, T& ku) {
+  mu = T(0);
+  ku = T(0);
+  if (D == 1) {
+#pragma unroll
+    for (int ox = -1; ox <= 1; ++ox) {
+      int x = ix + ox;
+      if (x < 0 || x >= n) continue;
+      T v = get(x);
+      mu += S.m1[ox + 1] * v;
+      ku += S.k1[ox + 1] * v;
+    }
+  } else if (D == 2) {
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy) {
+      int y = iy + oy;
+      if (y < 0 || y >= n) continue;
+      // row pass: a = M_1 u, b = K_1 u along x
+      T a = T(0), b = T(0);
+#pragma unroll
+      for (int ox = -1; ox <= 1; ++ox) {
+        int x = ix + ox;
+        if (x < 0 || x >= n) continue;
+        T v = get(y * n + x);
+        a += S.m1[ox + 1] * v;
+        b += S.k1[ox + 1] * v;
+      }
+      mu += S.m1[oy + 1] * a;
+      ku += S.k1[oy + 1] * a + S.m1[oy + 1] * b;
+    }
+  } else {
+#pragma unroll
+    for (int oz = -1; oz <= 1; ++oz) {
+      int z = iz + oz;
+      if (z < 0 || z >= n) continue;
+      T am = T(0), ak = T(0);   // M_1(y) M_1(x) u, and the K part of the (x,y) plane
+#pragma unroll
+      for (int oy = -1; oy <= 1; ++oy) {
+        int y = iy + oy;
+        if (y < 0 || y >= n) continue;
+        T a = T(0), b = T(0);
+#pragma unroll
+        for (int ox = -1; ox <= 1; ++ox) {
+          int x = ix + ox;
+          if (x < 0 || x >= n) continue;
+          T v = get(((int64_t)z * n + y) * n + x);
+          a += S.m1[ox + 1] * v;
+          b += S.k1[ox + 1] * v;
+        }
+        am += S.m1[oy + 1] * a;
+        ak += S.k1[oy + 1] * a + S.m1[oy + 1] * b;
+      }
+      mu += S.m1[oz + 1] * am;
+      ku += S.k1[oz + 1] * am + S.m1[oz + 1] * ak;
+    }
+  }
+}
+
+// Only M_h (for the time-coupling trace term and the initial value).
+template <typename T, int D, typename Get>
+__device__ __forceinline__ T apply_m(const Stencil<T, D>& S, int n, int ix, int iy, int iz, Get get) {
+  T mu, ku;
+  apply_mk<T, D>(S, n, ix, iy, iz, get, mu, ku);
+  return mu;
+}
+
+__device__ __forceinline__ void node_coords(int64_t j, int n, int D, int& ix, int& iy, int& iz) {
+  ix = (int)(j % n);
+  iy = D >= 2 ? (int)((j / n) % n) : 0;
+  iz = D >= 3 ? (int)(j / ((int64_t)n * n)) : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = f - L u (system chap4_generalLinearSystem) or f - L^T u.
+// Forward:  r_{s,k} = f_{s,k} - sum_l K[k,l] (M_h u_{s,l}) - tau Mh[k] (K_h u_{s,k})
+//                     + st[k] M_h (sum_l en[l] u_{s-1,l})      (B = -N_tau (x) M_h)
+//           for s = 0 the previous trace is the initial value u0 (may be null).
+// Adjoint:  r_{s,k} = f_{s,k} - sum_l K[l,k] (M_h u_{s,l}) - tau Mh[k] (K_h u_{s,k})
+//                     + en[k] M_h (sum_l st[l] u_{s+1,l}).
+// One thread per (spatial node, time step); grid.y indexes the time step
+// within [s0, s0 + gridDim.y).
+// ---------------------------------------------------------------------------
+template <typename T, int D, int Q, bool ADJ>
+__global__ void k_residual(const T* __restrict__ f, const T* __restrict__ u,
+                           const T* __restrict__ u0, T* __restrict__ r,
+                           int n, int N, int s0, T tau, T h, TimeCoef<T, Q> tc) {
+  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N) return;
+  int ix, iy, iz;
+  node_coords(j, n, D, ix, iy, iz);
+  Stencil<T, D> S(h);
+  T mu[Q], ku[Q];
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const T* ul = u + ((int64_t)s * Q + l) * Nx;
+    apply_mk<T, D>(S, n, ix, iy, iz, [&](int64_t q) { return ul[q]; }, mu[l], ku[l]);
+  }
+  T mt = T(0);
+  if (!ADJ) {
+    if (s > 0) {
+      const T* up = u + (int64_t)(s - 1) * Q * Nx;
+      mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) {
+        T t = T(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) t += tc.en[l] * up[(int64_t)l * Nx + q];
+        return t;
+      });
+    } else if (u0 != nullptr) {
+      mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) { return u0[q]; });
+    }
+  } else {
+    if (s < N - 1) {
+      const T* un = u + (int64_t)(s + 1) * Q * Nx;
+      mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) {
+        T t = T(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) t += tc.st[l] * un[(int64_t)l * Nx + q];
+        return t;
+      });
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    T acc = f[idx];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc -= (ADJ ? tc.K[l * Q + k] : tc.K[k * Q + l]) * mu[l];
+    acc -= tau * tc.Mh[k] * ku[k];
+    acc += (ADJ ? tc.en[k] : tc.st[k]) * mt;
+    r[idx] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched DST-I along one spatial axis, X_j = sum_{m=1}^{n} x_m sin(pi j m / Nf),
+// Nf = n + 1 a power of two.  Exact block inverse of Section 3.1 (the
+// eigenvectors of M_1 and K_1 are the sine vectors).
+//
+// Fast algorithm (O(n log n)): with x_0 = 0,
+//   y_j = sin(j pi / Nf) (x_j + x_{Nf-j}) + (x_j - x_{Nf-j}) / 2,  j = 1..Nf-1, y_0 = 0;
+//   the real DFT of y gives R_k = sum y_j cos(2 pi j k / Nf), I_k = sum y_j sin(2 pi j k / Nf);
+//   then X_{2k} = I_k and X_{2k+1} = X_{2k-1} + R_k with X_1 = R_0 / 2.
+// The real DFT of length Nf uses a complex radix-2 FFT of length Nf/2 on
+// z_m = y_{2m} + i y_{2m+1} followed by the even/odd split.
+//
+// One warp transforms one line held in shared memory.  Each CTA stages W lines:
+// line w of the tile starts at gbase(w) and has element stride `stride`.
+// tables: sinp[j] = sin(j pi / Nf) (j < Nf), twc/tws[k] = cos/sin(2 pi k / Nf) (k < Nf).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DstTables {
+  const T* sinp;
+  const T* twc;
+  const T* tws;
+};
+
+// Transform one line in place: x[0..Nf-1] (x[0] unused on input, x[j] = x_j),
+// zr/zi scratch of length Nf/2.  Output X_j in x[j], j = 1..Nf-1.
+template <typename T>
+__device__ void dst1_warp(T* x, T* zr, T* zi, int Nf, int logh, DstTables<T> tb, int lane) {
+  const int half = Nf >> 1;
+  // 1. pre-processing and packing into bit-reversed order
+  for (int m = lane; m < half; m += 32) {
+    T y0 = T(0), y1;
+    int j0 = 2 * m, j1 = 2 * m + 1;
+    if (j0 > 0) y0 = tb.sinp[j0] * (x[j0] + x[Nf - j0]) + T(0.5) * (x[j0] - x[Nf - j0]);
+    y1 = tb.sinp[j1] * (x[j1] + x[Nf - j1]) + T(0.5) * (x[j1] - x[Nf - j1]);
+    int br = logh > 0 ? (int)(__brev((unsigned)m) >> (32 - logh)) : 0;
+    zr[br] = y0;
+    zi[br] = y1;
+  }
+  __syncwarp();
+  // 2. radix-2 decimation-in-time FFT, e^{-2 pi i jk / half}
+  for (int len = 2; len <= half; len <<= 1) {
+    const int hl = len >> 1;
+    const int tstride = Nf / len;
+    for (int b = lane; b < (half >> 1); b += 32) {
+      int grp = b / hl, jj = b - grp * hl;
+      int i0 = grp * len + jj, i1 = i0 + hl;
+      T wc = tb.twc[tstride * jj], ws = -tb.tws[tstride * jj];   // w = e^{-2 pi i jj / len}
+      T ar = zr[i1], ai = zi[i1];
+      T tr = wc * ar - ws * ai, ti = wc * ai + ws * ar;
+      T br0 = zr[i0], bi0 = zi[i0];
+      zr[i1] = br0 - tr; zi[i1] = bi0 - ti;
+      zr[i0] = br0 + tr; zi[i0] = bi0 + ti;
+    }
+    __syncwarp();
+  }
+  // 3. even/odd split: Y_k = E_k + W^k O_k, W = e^{-2 pi i / Nf};
+  //    R_k -> x[2k+1], I_k = -Im Y_k -> x[2k]
+  for (int k = lane; k < half; k += 32) {
+    int kc = (half - k) & (half - 1);
+    T zkr = zr[k], zki = zi[k];
+    T zcr = zr[kc], zci = -zi[kc];            // conj(Z_{half-k})
+    T er = T(0.5) * (zkr + zcr), ei = T(0.5) * (zki + zci);
+    // O = (Zk - Zc) / (2i) = (dI / 2) - i (dR / 2)
+    T dr = zkr - zcr, di = zki - zci;
+    T orr = T(0.5) * di, oi = T(-0.5) * dr;
+    T wc = tb.twc[k], ws = -tb.tws[k];
+    T yr = er + (wc * orr - ws * oi);
+    T yi = ei + (wc * oi + ws * orr);
+    x[2 * k + 1] = yr;
+    x[2 * k] = -yi;
+  }
+  __syncwarp();
+  // 4. X_{2k+1} = sum_{k' <= k} R_k' - R_0 / 2  (warp prefix scan over half values)
+  const T R0 = x[1];
+  __syncwarp();
+  const int per = half >= 32 ? (half >> 5) : 1;
+  const int k0 = lane * per;
+  T loc = T(0);
+  if (k0 < half) {
+    for (int c = 0; c < per; ++c) {
+      loc += x[2 * (k0 + c) + 1];
+      x[2 * (k0 + c) + 1] = loc;     // chunk-local inclusive prefix
+    }
+  }
+  T incl = loc;                      // inclusive scan of chunk totals across lanes
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    T v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const T shift = (incl - loc) - T(0.5) * R0;
+  if (k0 < half) {
+    for (int c = 0; c < per; ++c) x[2 * (k0 + c) + 1] += shift;
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void k_dst_axis(T* __restrict__ data, int n, int64_t nlines, int64_t inner,
+                           int64_t stride, int W, T scale, DstTables<T> tb, int logh) {
+  // Line id g -> (outer, in) with in < inner; base = outer * inner * n + in (axis
+  // stride = inner); for the x axis inner = 1 and stride = 1.
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int Nf = n + 1;
+  const int half = Nf >> 1;
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* xs = sm;                                   // W lines x Nf
+  T* zs = sm + (int64_t)W * Nf;                 // per warp: zr[half], zi[half]
+  T* zr = zs + (int64_t)warp * Nf;
+  T* zi = zr + half;
+  const int64_t g0 = (int64_t)blockIdx.x * W;   // first line of this tile
+  const int wcount = (int)((nlines - g0) < W ? (nlines - g0) : W);
+  // load
+  if (stride == 1) {
+    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
+      int w = idx / n, jj = idx - w * n;
+      int64_t g = g0 + w;
+      xs[w * Nf + 1 + jj] = data[g * n + jj];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
+      int jj = idx / wcount, w = idx - jj * wcount;
+      int64_t g = g0 + w;
+      int64_t outer = g / inner, in = g - outer * inner;
+      xs[w * Nf + 1 + jj] = data[outer * inner * n + in + (int64_t)jj * stride];
+    }
+  }
+  __syncthreads();
+  for (int w = warp; w < wcount; w += nwarps) {
+    dst1_warp<T>(xs + w * Nf, zr, zi, Nf, logh, tb, lane);
+  }
+  __syncthreads();
+  if (stride == 1) {
+    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
+      int w = idx / n, jj = idx - w * n;
+      int64_t g = g0 + w;
+      data[g * n + jj] = scale * xs[w * Nf + 1 + jj];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
+      int jj = idx / wcount, w = idx - jj * wcount;
+      int64_t g = g0 + w;
+      int64_t outer = g / inner, in = g - outer * inner;
+      data[outer * inner * n + in + (int64_t)jj * stride] = scale * xs[w * Nf + 1 + jj];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-mode q x q solve in the sine basis (Section 3.1 with the eigenvalues of
+// Lemma 17): (lamM K + lamK tau Mh) d = r (adjoint: K^T), where
+// lamM = prod_a m_{k_a}, lamK = sum_a kappa_{k_a} prod_{b != a} m_{k_b},
+// m_k = h/3 (2 + cos(k pi / Nf)), kappa_k = 2/h (1 - cos(k pi / Nf)).
+// The result is multiplied by `scale` (the inverse-DST normalisation).
+// Gaussian elimination with partial pivoting in registers.
+// ---------------------------------------------------------------------------
+template <typename T, int Q>
+__device__ __forceinline__ void small_solve(T A[Q][Q], T b[Q]) {
+#pragma unroll
+  for (int c = 0; c < Q; ++c) {
+    int p = c;
+    T best = fabs(A[c][c]);
+#pragma unroll
+    for (int r2 = c + 1; r2 < Q; ++r2) {
+      T v = fabs(A[r2][c]);
+      if (v > best) { best = v; p = r2; }
+    }
+    if (p != c) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) { T t = A[c][k]; A[c][k] = A[p][k]; A[p][k] = t; }
+      T t = b[c]; b[c] = b[p]; b[p] = t;
+    }
+    T inv = T(1) / A[c][c];
+#pragma unroll
+    for (int r2 = c + 1; r2 < Q; ++r2) {
+      T fct = A[r2][c] * inv;
+#pragma unroll
+      for (int k = c; k < Q; ++k) A[r2][k] -= fct * A[c][k];
+      b[r2] -= fct * b[c];
+    }
+  }
+#pragma unroll
+  for (int c = Q - 1; c >= 0; --c) {
+    T acc = b[c];
+#pragma unroll
+    for (int k = c + 1; k < Q; ++k) acc -= A[c][k] * b[k];
+    b[c] = acc / A[c][c];
+  }
+}
+
+template <typename T, int D, int Q, bool ADJ>
+__global__ void k_mode_solve(const T* __restrict__ in, T* __restrict__ out, int n, int nsteps,
+                             const T* __restrict__ mval, const T* __restrict__ kval,
+                             T tau, T scale, TimeCoef<T, Q> tc) {
+  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= Nx || s >= nsteps) return;
+  int ix, iy, iz;
+  node_coords(j, n, D, ix, iy, iz);
+  T lamM, lamK;
+  if (D == 1) {
+    lamM = mval[ix];
+    lamK = kval[ix];
+  } else if (D == 2) {
+    lamM = mval[ix] * mval[iy];
+    lamK = kval[ix] * mval[iy] + mval[ix] * kval[iy];
+  } else {
+    lamM = mval[ix] * mval[iy] * mval[iz];
+    lamK = kval[ix] * mval[iy] * mval[iz] + mval[ix] * kval[iy] * mval[iz] + mval[ix] * mval[iy] * kval[iz];
+  }
+  T A[Q][Q], b[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) A[k][l] = lamM * (ADJ ? tc.K[l * Q + k] : tc.K[k * Q + l]);
+    A[k][k] += lamK * tau * tc.Mh[k];
+    b[k] = in[((int64_t)s * Q + k) * Nx + j];
+  }
+  small_solve<T, Q>(A, b);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) out[((int64_t)s * Q + k) * Nx + j] = scale * b[k];
+}
+
+// ---------------------------------------------------------------------------
+// Restriction (eqs. chap4_restrictionTime, chap4_spaceRestrictionProlongation):
+// fc[m, k, J] = sum_l R1[k,l] (Rx r)[2m, l, J] + R2[k,l] (Rx r)[2m+1, l, J],
+// Rx = identity (semi) or (x)_a (1/2)[1 2 1] at fine nodes 2J, 2J+1, 2J+2 (0-based,
+// full).  One thread per coarse (node, step).
+// ---------------------------------------------------------------------------
+template <typename T, int D, int Q, bool FULL>
+__global__ void k_restrict(const T* __restrict__ r, T* __restrict__ fc, int nf, int nc, int Nc,
+                           TimeCoef<T, Q> tc) {
+  const int64_t Nxc = (D == 1) ? nc : (D == 2) ? (int64_t)nc * nc : (int64_t)nc * nc * nc;
+  const int64_t Nxf = (D == 1) ? nf : (D == 2) ? (int64_t)nf * nf : (int64_t)nf * nf * nf;
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (J >= Nxc || m >= Nc) return;
+  int jx, jy, jz;
+  node_coords(J, nc, D, jx, jy, jz);
+  T a[2][Q];
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const T* rl = r + ((int64_t)(2 * m + sl) * Q + l) * Nxf;
+      T acc = T(0);
+      if (!FULL) {
+        acc = rl[J];
+      } else {
+        const T w[3] = {T(0.5), T(1), T(0.5)};
+        if (D == 1) {
+#pragma unroll
+          for (int ox = 0; ox < 3; ++ox) acc += w[ox] * rl[2 * jx + ox];
+        } else if (D == 2) {
+#pragma unroll
+          for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox)
+              acc += w[oy] * w[ox] * rl[(int64_t)(2 * jy + oy) * nf + 2 * jx + ox];
+        } else {
+#pragma unroll
+          for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+            for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+              for (int ox = 0; ox < 3; ++ox)
+                acc += w[oz] * w[oy] * w[ox] *
+                       rl[((int64_t)(2 * jz + oz) * nf + 2 * jy + oy) * nf + 2 * jx + ox];
+        }
+      }
+      a[sl][l] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    T acc = T(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc += tc.R1[k * Q + l] * a[0][l] + tc.R2[k * Q + l] * a[1][l];
+    fc[((int64_t)m * Q + k) * Nxc + J] = acc;
+  }
+}
+
+// Prolongation and correction u_f += P e_c, P = R^T: fine step 2m+sl, dof l gets
+// sum_k R_sl[k,l] (Px e)[m, k, I]; Px = Rx^T is linear interpolation (fine node
+// 2J+1 <- coarse J with weight 1, fine node 2J <- coarse J-1, J with weight 1/2).
+template <typename T, int D, int Q, bool FULL>
+__global__ void k_prolong(const T* __restrict__ ec, T* __restrict__ uf, int nf, int nc, int Nf_steps,
+                          TimeCoef<T, Q> tc) {
+  const int64_t Nxc = (D == 1) ? nc : (D == 2) ? (int64_t)nc * nc : (int64_t)nc * nc * nc;
+  const int64_t Nxf = (D == 1) ? nf : (D == 2) ? (int64_t)nf * nf : (int64_t)nf * nf * nf;
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (I >= Nxf || s >= Nf_steps) return;
+  const int m = s >> 1, sl = s & 1;
+  int ix, iy, iz;
+  node_coords(I, nf, D, ix, iy, iz);
+  T e[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const T* ek = ec + ((int64_t)m * Q + k) * Nxc;
+    T acc;
+    if (!FULL) {
+      acc = ek[I];
+    } else {
+      // per axis: list of (coarse index, weight)
+      int ci[3][2];
+      T cw[3][2];
+      int cnt[3];
+      int coord[3] = {ix, iy, iz};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        int i = coord[a];
+        if (i & 1) { ci[a][0] = (i - 1) >> 1; cw[a][0] = T(1); cnt[a] = 1; }
+        else {
+          int c = 0;
+          int jl = (i >> 1) - 1, jr = i >> 1;
+          if (jl >= 0) { ci[a][c] = jl; cw[a][c] = T(0.5); ++c; }
+          if (jr < nc) { ci[a][c] = jr; cw[a][c] = T(0.5); ++c; }
+          cnt[a] = c;
+        }
+      }
+      acc = T(0);
+      if (D == 1) {
+        for (int p = 0; p < cnt[0]; ++p) acc += cw[0][p] * ek[ci[0][p]];
+      } else if (D == 2) {
+        for (int py = 0; py < cnt[1]; ++py)
+          for (int px = 0; px < cnt[0]; ++px)
+            acc += cw[1][py] * cw[0][px] * ek[(int64_t)ci[1][py] * nc + ci[0][px]];
+      } else {
+        for (int pz = 0; pz < cnt[2]; ++pz)
+          for (int py = 0; py < cnt[1]; ++py)
+            for (int px = 0; px < cnt[0]; ++px)
+              acc += cw[2][pz] * cw[1][py] * cw[0][px] *
+                     ek[((int64_t)ci[2][pz] * nc + ci[1][py]) * nc + ci[0][px]];
+      }
+    }
+    e[k] = acc;
+  }
+  const T* Rb = sl ? tc.R2 : tc.R1;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) acc += Rb[k * Q + l] * e[k];
+    uf[((int64_t)s * Q + l) * Nxf + I] += acc;
+  }
+}
+
+// M_h applied to sum_k c[k] v_{0,k} (block 0 of a space-time vector): gradient of
+// the initial-value term, grad_u0 = M_h sum_k psi_k(t_0^+) lambda_{1,k}.
+template <typename T, int D, int Q>
+__global__ void k_ic_gradient(const T* __restrict__ lam, T* __restrict__ g, int n, T h, TimeCoef<T, Q> tc) {
+  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Nx) return;
+  int ix, iy, iz;
+  node_coords(j, n, D, ix, iy, iz);
+  Stencil<T, D> S(h);
+  g[j] = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) {
+    T t = T(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) t += tc.st[k] * lam[(int64_t)k * Nx + q];
+    return t;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, T a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+template <typename T>
+__global__ void k_scale_copy(T* __restrict__ y, const T* __restrict__ x, T a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// y32 = (float)(a * x64)
+__global__ void k_cast_down(float* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(a * x[i]);
+}
+
+// y64 += a * (double)x32
+__global__ void k_axpy_up(double* __restrict__ y, const float* __restrict__ x, double a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * (double)x[i];
+}
+
+// y64 = (double)x32
+__global__ void k_cast_up(double* __restrict__ y, const float* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic two-stage sum of squares: stage 1 writes one partial per block
+// (fixed grid, fixed per-thread ranges, fixed tree), stage 2 reduces the
+// partials in one block.  Accumulation in FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sumsq_partial(const T* __restrict__ x, int64_t n, double* __restrict__ partial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)x[i];
+    acc += v * v;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) partial[blockIdx.x] = acc;
+  }
+}
+
+__global__ void k_sum_final(const double* __restrict__ partial, int np, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) out[0] = acc;
+  }
+}
+
+}  // namespace stmg

@@ -1,0 +1,284 @@
+"""Python binding of the stmg C ABI (include/stmg.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+libstmg.so.  PyTorch provides device memory and the stream.  If the library
+has not been built, importing this module raises; there is no CPU fallback.
+
+Space-time vectors are torch.float64 CUDA tensors of shape (N, q, n, ..., n)
+(or any contiguous tensor with N q n^d elements) in the layout of the header:
+time step, time dof (Legendre degree), then space with x fastest.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_PKG, "libstmg.so")
+
+ST_OK, ST_EINVAL, ST_ENOMEM, ST_ENOTCONV, ST_ENAN, ST_ECUDA = range(6)
+ST_FP64, ST_MIXED = 0, 1
+ST_AUTO, ST_SEMI, ST_FULL = 0, 1, 2
+ST_INIT_GIVEN = 1
+ST_MAX_PT = 3
+
+EXPORTS = [
+    "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
+    "st_level_info", "st_residual", "st_vcycle", "st_solve", "st_adjoint_solve", "st_level_residual",
+    "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
+    "st_coarsest_solve", "st_norm2",
+]
+
+
+class StMesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int)]
+
+
+class StOptions(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
+                ("coarsening", ctypes.c_int), ("coarsest_steps", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("max_workspace_bytes", ctypes.c_size_t)]
+
+
+class StmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"stmg error {code}: {msg}")
+        self.code = code
+
+
+def library_path():
+    return _LIBPATH
+
+
+def load_library(path=None):
+    """Load libstmg.so and declare the C signatures; raises if it is missing."""
+    path = path or _LIBPATH
+    if not os.path.exists(path):
+        raise ImportError(f"stmg CUDA library not built ({path}); run "
+                          "`python -m paper_1411_0519_gb300.build` or __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    H = ctypes.c_void_p
+    sig = {
+        "st_default_options": (None, [ctypes.POINTER(StOptions)]),
+        "st_setup": (I, [ctypes.POINTER(StMesh), I, I, D, ctypes.POINTER(StOptions), P, ctypes.POINTER(H)]),
+        "st_destroy": (None, [H]),
+        "st_last_error": (ctypes.c_char_p, [H]),
+        "st_ndof": (ctypes.c_size_t, [H]),
+        "st_num_levels": (I, [H]),
+        "st_level_info": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "st_residual": (I, [H, P, P, P, P]),
+        "st_vcycle": (I, [H, P, P, P]),
+        "st_solve": (I, [H, P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "st_adjoint_solve": (I, [H, P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "st_level_residual": (I, [H, I, I, P, P, P]),
+        "st_level_block_solve": (I, [H, I, I, P, P]),
+        "st_level_smooth": (I, [H, I, I, I, P, P]),
+        "st_level_restrict": (I, [H, I, P, P]),
+        "st_level_prolong": (I, [H, I, P, P]),
+        "st_coarsest_solve": (I, [H, I, P, P]),
+        "st_norm2": (I, [H, P, ctypes.c_size_t, ctypes.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _ptr(t, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous torch.float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_PRECISION = {"fp64": ST_FP64, "mixed": ST_MIXED}
+_COARSEN = {"auto": ST_AUTO, "semi": ST_SEMI, "full": ST_FULL}
+
+
+class Solver:
+    """A space-time hierarchy (st_setup) bound to the current CUDA stream."""
+
+    def __init__(self, dim, n, p_t, N, T, *, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50,
+                 precision="fp64", coarsening="auto", coarsest_steps=1, inner_cycles=1,
+                 max_workspace_bytes=0, stream=None, device=None):
+        L = lib()
+        self._lib = L
+        self.dim, self.n, self.p_t, self.N, self.T = dim, n, p_t, N, float(T)
+        self.q = p_t + 1
+        opt = StOptions()
+        L.st_default_options(ctypes.byref(opt))
+        opt.nu1, opt.nu2, opt.omega, opt.rtol, opt.maxit = nu1, nu2, omega, rtol, maxit
+        opt.precision = _PRECISION[precision]
+        opt.coarsening = _COARSEN[coarsening]
+        opt.coarsest_steps = coarsest_steps
+        opt.inner_cycles = inner_cycles
+        opt.max_workspace_bytes = max_workspace_bytes
+        self.options = opt
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        mesh = StMesh(dim, n)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = L.st_setup(ctypes.byref(mesh), p_t, N, float(T), ctypes.byref(opt),
+                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != ST_OK:
+            raise StmgError(rc, "st_setup failed (see stderr)")
+        self._h = h
+        self.ndof = int(L.st_ndof(h))
+        self.shape = (N, self.q) + (n,) * dim
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.st_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != ST_OK and rc not in allow:
+            raise StmgError(rc, self._lib.st_last_error(self._h).decode())
+        return rc
+
+    # ------------------------------------------------------------ hierarchy
+    @property
+    def num_levels(self):
+        return int(self._lib.st_num_levels(self._h))
+
+    def level_info(self, L):
+        Nl, nl, mu, full = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        self._check(self._lib.st_level_info(self._h, L, ctypes.byref(Nl), ctypes.byref(nl),
+                                            ctypes.byref(mu), ctypes.byref(full)))
+        return {"N": Nl.value, "n": nl.value, "mu": mu.value, "full": full.value}
+
+    def level_shape(self, L):
+        i = self.level_info(L)
+        return (i["N"], self.q) + (i["n"],) * self.dim
+
+    def level_ndof(self, L):
+        i = self.level_info(L)
+        return i["N"] * self.q * i["n"] ** self.dim
+
+    def empty(self, L=None):
+        shp = self.shape if L is None else self.level_shape(L)
+        return torch.empty(shp, dtype=torch.float64, device=self.device)
+
+    # ------------------------------------------------------------ full solver
+    def residual(self, f, u, u0=None, out=None):
+        out = self.empty() if out is None else out
+        nx = self.n ** self.dim
+        self._check(self._lib.st_residual(self._h, _ptr(f, self.ndof, "f"), _ptr(u0, nx, "u0"),
+                                          _ptr(u, self.ndof, "u"), _ptr(out, self.ndof, "r")))
+        return out
+
+    def vcycle(self, u, f, u0=None):
+        nx = self.n ** self.dim
+        self._check(self._lib.st_vcycle(self._h, _ptr(u, self.ndof, "u"), _ptr(f, self.ndof, "f"),
+                                        _ptr(u0, nx, "u0")))
+        return u
+
+    def solve(self, f, u0=None, u=None, raise_on_failure=True):
+        """Solve L u = f + IC(u0).  Returns (u, iterations, relative residual)."""
+        init = u is not None
+        u = self.empty() if u is None else u
+        nx = self.n ** self.dim
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        rc = self._lib.st_solve(self._h, _ptr(f, self.ndof, "f"), _ptr(u0, nx, "u0"), _ptr(u, self.ndof, "u"),
+                                ST_INIT_GIVEN if init else 0, ctypes.byref(it), ctypes.byref(rr))
+        self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
+        self.last_status = rc
+        return u, it.value, rr.value
+
+    def adjoint_solve(self, g, lam=None, raise_on_failure=True):
+        """Solve L^T lam = g.  Returns (lam, grad_u0, iterations, relative residual)."""
+        lam = self.empty() if lam is None else lam
+        gu0 = torch.empty((self.n,) * self.dim, dtype=torch.float64, device=self.device)
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        rc = self._lib.st_adjoint_solve(self._h, _ptr(g, self.ndof, "g"), _ptr(lam, self.ndof, "lambda"),
+                                        _ptr(gu0, gu0.numel(), "grad_u0"), ctypes.byref(it), ctypes.byref(rr))
+        self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
+        self.last_status = rc
+        return lam, gu0, it.value, rr.value
+
+    def norm2(self, x):
+        out = ctypes.c_double()
+        self._check(self._lib.st_norm2(self._h, _ptr(x, None, "x"), x.numel(), ctypes.byref(out)))
+        return out.value
+
+    # ------------------------------------------------------------ step level
+    def level_residual(self, L, f, u, adjoint=False, out=None):
+        m = self.level_ndof(L)
+        out = self.empty(L) if out is None else out
+        self._check(self._lib.st_level_residual(self._h, L, int(adjoint), _ptr(f, m, "f"), _ptr(u, m, "u"),
+                                                _ptr(out, m, "r")))
+        return out
+
+    def level_block_solve(self, L, r, adjoint=False, out=None):
+        m = self.level_ndof(L)
+        out = self.empty(L) if out is None else out
+        self._check(self._lib.st_level_block_solve(self._h, L, int(adjoint), _ptr(r, m, "r"), _ptr(out, m, "d")))
+        return out
+
+    def level_smooth(self, L, f, u, nu=1, adjoint=False):
+        m = self.level_ndof(L)
+        self._check(self._lib.st_level_smooth(self._h, L, int(adjoint), nu, _ptr(f, m, "f"), _ptr(u, m, "u")))
+        return u
+
+    def level_restrict(self, L, r, out=None):
+        out = self.empty(L - 1) if out is None else out
+        self._check(self._lib.st_level_restrict(self._h, L, _ptr(r, self.level_ndof(L), "r"),
+                                                _ptr(out, self.level_ndof(L - 1), "f_coarse")))
+        return out
+
+    def level_prolong(self, L, e, u):
+        self._check(self._lib.st_level_prolong(self._h, L, _ptr(e, self.level_ndof(L - 1), "e"),
+                                               _ptr(u, self.level_ndof(L), "u")))
+        return u
+
+    def coarsest_solve(self, f, adjoint=False, out=None):
+        out = self.empty(0) if out is None else out
+        m = self.level_ndof(0)
+        self._check(self._lib.st_coarsest_solve(self._h, int(adjoint), _ptr(f, m, "f"), _ptr(out, m, "u")))
+        return out
+
+
+class SpaceTimeSolve(torch.autograd.Function):
+    """u = L^{-1}(f + IC(u0)) with gradients from the adjoint solve:
+    dJ/df = lambda, dJ/du0 = M_h sum_k psi_k(t_0^+) lambda_{1,k}, L^T lambda = dJ/du."""
+
+    @staticmethod
+    def forward(ctx, f, u0, solver):
+        ctx.solver = solver
+        u, it, rr = solver.solve(f.contiguous(), u0.contiguous())
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        lam, gu0, it, rr = ctx.solver.adjoint_solve(grad_u.contiguous())
+        return lam, gu0, None
+
+
+def solve(f, u0, solver):
+    """Differentiable solve of the heat equation's space-time system."""
+    return SpaceTimeSolve.apply(f, u0, solver)
