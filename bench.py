@@ -1,0 +1,364 @@
+"""Benchmark: space-time DoF/s of the heat-equation space-time multigrid solve
+to a 1e-8 relative residual on one GB300 (or N independent problems on N GPUs).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl stmg|reference]
+
+A step is one full solve (st_solve) of the 2D workload heat2d_255: Q1 on the
+unit square with 255^2 interior nodes, DG degree p_t = 1, N = 1024 time steps,
+T = 1 (133,171,200 unknowns, 1.07 GB per FP64 vector, far above the 129 MB
+L2, so no flush is needed between steps); f ~ U[-1,1] (seed 0 + rank),
+u0 = sin(pi x) sin(pi y).  The headline value is the plain FP64 solve; the
+mixed-precision form (FP32 V-cycles inside FP64 refinement) of the same solve
+is reported under "mixed".  Device time comes from CUDA events on the
+solver's stream; "e2e" repeats the solve through the same C ABI call with the
+inputs copied from pinned host memory and the solution copied back inside the
+timed region.  Kernel time per class comes from the library's event timing
+(st_profile_start/stop) over the timed region.
+
+Under torchrun every rank solves its own problem (no data-path collective,
+"scaling": "weak"); rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (oracle/, SciPy sparse LU) on a bounded
+sample of the same workload: the first 8 of the 1024 time steps (same tau and
+mesh) solved to the same tolerance; DoF/s = sampled DoF / solve time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "heat2d_255"
+METRIC = "space-time DoF/s to 1e-8 rel. residual (FP64 vs mixed); V-cycle HBM GB/s"
+CPU_SAMPLE_STEPS = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="stmg", choices=["stmg", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--inner-cycles", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# FP64 vector-ALU peak of a GB300: 1.25 TFLOP/s (the published per-GPU FP64
+# figure); an FMA-chain probe on this part reached 1.196 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+# FP32 vector-ALU peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def inputs(w, rank):
+    from paper_1411_0519_gb300 import workloads
+    f = workloads.uniform_load(w["d"], w["n"], w["p_t"], w["N"], seed=rank)
+    u0 = workloads.sine_ic(w["d"], w["n"])
+    return f, u0
+
+
+def time_solves(torch, solver, f, u0, u, steps, warmup, barrier):
+    """Warm-up, then `steps` solves timed with CUDA events on the solver's stream."""
+    u = solver.empty() if u is None else u
+    for _ in range(warmup):
+        solver.solve(f, u0, u=u, initial_guess=False)
+    stream = solver.stream
+    iters = []
+    barrier()
+    torch.cuda.synchronize()
+    solver.profile_start(400000)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    relres = None
+    for _ in range(steps):
+        _, it, relres = solver.solve(f, u0, u=u, initial_guess=False)
+        iters.append(it)
+    e1.record(stream)
+    e1.synchronize()
+    prof = solver.profile_stop()
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1), iters, relres, prof
+
+
+def roofline(prof, fp32, pk):
+    """Dominant kernel class in the timed region and its achieved fraction."""
+    classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["ms"] > 0}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    v = classes[dom]
+    sec = v["ms"] / 1e3
+    gbs = v["bytes"] / sec / 1e9
+    tfl = v["flops"] / sec / 1e12
+    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    f_hbm = gbs / pk["hbm_gbs"]
+    f_alu = tfl / alu_peak
+    total_ms = sum(c["ms"] for c in classes.values())
+    share = v["ms"] / total_ms
+    if f_alu >= f_hbm:
+        rf = {"bound": "alu", "achieved": round(tfl, 4), "peak": alu_peak, "unit": "TFLOP/s",
+              "frac": round(f_alu, 4), "peak_src": "FP32 lanes x clock" if fp32 else
+              "published FP64 rate (probe: 1.196 TFLOP/s)"}
+    else:
+        rf = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+              "frac": round(f_hbm, 4), "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)"}
+    rf.update({"kernel": dom, "launches": v["launches"], "avg_launch_ms": round(v["ms"] / max(1, v["launches"]), 4),
+               "share": round(share, 3), "traffic": None,
+               "alg_bytes_per_launch": v["bytes"] / max(1, v["launches"]),
+               "alg_flops_per_launch": v["flops"] / max(1, v["launches"])})
+    return rf
+
+
+def breakdown(prof):
+    return {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+            for k, v in prof.items() if not k.startswith("_") and v["launches"] > 0}
+
+
+def cpu_baseline(w, rank, repeats=1):
+    """The oracle, as it stands, on a bounded sample (first CPU_SAMPLE_STEPS time
+    steps); returns one entry per timed solve (setup excluded)."""
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(1)
+    except Exception:
+        limiter = None
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import multigrid, spacetime
+    from paper_1411_0519_gb300 import workloads
+    Ns = CPU_SAMPLE_STEPS
+    tau = w["T"] / w["N"]
+    H = multigrid.Hierarchy(w["d"], w["n"], w["p_t"], Ns, tau * Ns)
+    disc = H.finest.disc
+    f = workloads.uniform_load(w["d"], w["n"], w["p_t"], w["N"], seed=rank)[:Ns].reshape(disc.shape())
+    g = spacetime.add_ic(disc, f, workloads.sine_ic(w["d"], w["n"]))
+    out = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        _, it, hist = multigrid.solve(H, g, rtol=w["rtol"], maxit=60)
+        dt = time.perf_counter() - t0
+        out.append({"value": disc.ndof / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                    "sample": f"oracle solve of the first {Ns} of {w['N']} time steps (same mesh and tau, "
+                              f"{disc.ndof} DoF) to {w['rtol']:g}: {it} V-cycles in {dt:.1f} s; setup excluded",
+                    "seconds": dt, "iters": it, "dof": disc.ndof})
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    from paper_1411_0519_gb300 import workloads
+    w = workloads.WORKLOADS[args.workload]
+    if rank != 0:
+        return 0
+    # each step: one oracle solve of the bounded sample; warm-up solves untimed
+    samples = cpu_baseline(w, 0, repeats=args.warmup + args.steps)[args.warmup:]
+    sec = sum(s["seconds"] for s in samples)
+    value = samples[0]["dof"] * len(samples) / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(samples),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "d": w["d"], "n": w["n"], "p_t": w["p_t"], "N": w["N"],
+                       "T": w["T"], "rtol": w["rtol"], "sampled_time_steps": CPU_SAMPLE_STEPS},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1411_0519_gb300 import stmg, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = workloads.WORKLOADS[args.workload]
+    d, n, p, N, T, rtol = w["d"], w["n"], w["p_t"], w["N"], w["T"], w["rtol"]
+    f_np, u0_np = inputs(w, rank)
+    f = torch.from_numpy(f_np).cuda()
+    u0 = torch.from_numpy(u0_np).cuda()
+    pk = peaks()
+
+    # ---------------------------------------------------------------- FP64 (headline)
+    s64 = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="fp64")
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms64, it64, rr64, prof64 = time_solves(torch, s64, f, u0, None, args.steps, args.warmup, barrier)
+    ck = clocks.stop()
+    ms64 = max_over_ranks(ms64)
+    per_step = ms64 / args.steps
+    value = world * s64.ndof / (per_step / 1e3)
+    launches = sum(v["launches"] for k, v in prof64.items() if not k.startswith("_"))
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(f_np).pin_memory()
+        u0h = torch.from_numpy(u0_np).pin_memory()
+        uh = torch.empty(s64.shape, dtype=torch.float64).pin_memory()
+        fd = torch.empty_like(f)
+        u0d = torch.empty_like(u0)
+        ud = s64.empty()
+        stream = s64.stream
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                fd.copy_(fh, non_blocking=True)
+                u0d.copy_(u0h, non_blocking=True)
+            s64.solve(fd, u0d, u=ud, initial_guess=False)
+            with torch.cuda.stream(stream):
+                uh.copy_(ud, non_blocking=True)
+            stream.synchronize()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * s64.ndof * args.steps / dt, "unit": "DoF/s",
+               "h2d_bytes_per_step": fh.numel() * 8 + u0h.numel() * 8, "d2h_bytes_per_step": uh.numel() * 8,
+               "ms_per_step": 1e3 * dt / args.steps}
+        del fh, u0h, uh, fd, u0d, ud
+    rf64 = roofline(prof64, False, pk)
+    s64.close()
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- mixed precision
+    mixed = None
+    if not args.no_mixed:
+        smx = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="mixed", inner_cycles=args.inner_cycles)
+        msm, itm, rrm, profm = time_solves(torch, smx, f, u0, None, args.steps, max(1, args.warmup), barrier)
+        msm = max_over_ranks(msm)
+        mixed = {"value": world * smx.ndof / (msm / args.steps / 1e3), "unit": "DoF/s",
+                 "ms_per_step": msm / args.steps, "iters": itm[-1], "relres": rrm,
+                 "inner_cycles": args.inner_cycles, "dtype": "f32 V-cycle in f64 refinement",
+                 "roofline": roofline(profm, True, pk), "kernels": breakdown(profm),
+                 "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_"))}
+        smx.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(w, 0)[0]
+        for k in ("seconds", "iters", "dof"):
+            cpu.pop(k, None)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "d": d, "n": n, "p_t": p, "N": N, "T": T, "rtol": rtol,
+                   "dof_per_gpu": s64.ndof, "nu1": 2, "nu2": 2, "omega": 0.5, "precision": "fp64",
+                   "l2": "inputs larger than L2 (1.07 GB per vector), no flush"},
+        "iters": it64[-1], "relres": rr64,
+        "gpu_launches": launches,
+        "roofline": rf64,
+        "kernels": breakdown(prof64),
+        "mixed": mixed,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

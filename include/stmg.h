@@ -157,6 +157,31 @@ int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u);
 /* ||x||_2 of n FP64 values (deterministic order); synchronises. */
 int st_norm2(st_handle* h, const double* x, size_t n, double* out);
 
+/* ---- kernel timing (CUDA events on the handle's stream) ----
+ * Kernel classes for st_profile_stop: */
+#define ST_K_RESIDUAL   0   /* residual (forward / transposed) */
+#define ST_K_DST        1   /* batched sine transform along one axis */
+#define ST_K_MODESOLVE  2   /* per-mode q x q solve */
+#define ST_K_RESTRICT   3
+#define ST_K_PROLONG    4
+#define ST_K_NORM       5   /* both reduction stages */
+#define ST_K_VECTOR     6   /* axpy, casts, copies, memsets */
+#define ST_K_SMOOTH     7   /* fused smoothing kernels */
+#define ST_K_COUNT      8
+
+/* Record a CUDA event pair around every kernel launched by this handle, for up
+ * to max_launches launches (events are created here, not per launch).  Adds a
+ * few microseconds of host time per launch.  Errors: ST_EINVAL, ST_ECUDA. */
+int st_profile_start(st_handle* h, int max_launches);
+
+/* Synchronise the stream, stop recording and return per class (arrays of
+ * ST_K_COUNT entries, any may be NULL) the number of launches, their summed
+ * device time in milliseconds, and their algorithmic HBM bytes and
+ * floating-point operations (the minimum the computation needs: each input
+ * read once, each output written once; formulas in the library source).
+ * Launches beyond max_launches are counted but not timed (*dropped). */
+int st_profile_stop(st_handle* h, int* launches, double* ms, double* bytes, double* flops, int* dropped);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,8 +26,14 @@ class Level:
         self.full = lv["full"]
         self.mu = lv["mu"]
         self.lu = spla.splu(self.disc.A.tocsc())
-        self.luT = spla.splu(self.disc.A.T.tocsc())
+        self._luT = None       # LU of A^T, built on first adjoint use
         self.R = None          # restriction to the next coarser level
+
+    @property
+    def luT(self):
+        if self._luT is None:
+            self._luT = spla.splu(self.disc.A.T.tocsc())
+        return self._luT
 
     def block_solve(self, r, adjoint=False):
         """D^{-1} r: A^{-1} (or A^{-T}) applied to every time block of r."""

@@ -178,6 +178,14 @@ struct st_handle {
   double* coarse64_r = nullptr;
   double* r64 = nullptr;         // mixed precision: finest FP64 residual
   std::string err;
+  // kernel timing
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;          // pool, 2 per timed launch
+  std::vector<int> ev_class;            // class of each recorded pair
+  int prof_launches[ST_K_COUNT] = {0};
+  double prof_bytes[ST_K_COUNT] = {0};   // algorithmic HBM bytes of the counted launches
+  double prof_flops[ST_K_COUNT] = {0};   // algorithmic floating-point operations
+  int prof_dropped = 0;
 };
 
 namespace {
@@ -200,6 +208,27 @@ void fail(st_handle* h, int code, const std::string& msg) {
   h->err = msg;
   throw Fail{code};
 }
+
+// Records an event pair around the launches made during its lifetime when the
+// handle's kernel timing is on.
+struct Prof {
+  st_handle* h;
+  int slot = -1;
+  Prof(st_handle* hh, int cls, double bytes = 0.0, double flops = 0.0, int kernels = 1) : h(hh) {
+    if (!h->prof) return;
+    h->prof_launches[cls] += kernels;
+    h->prof_bytes[cls] += bytes;
+    h->prof_flops[cls] += flops;
+    const int pair = (int)h->ev_class.size();
+    if (2 * pair + 1 >= (int)h->ev.size()) { h->prof_dropped++; return; }
+    slot = pair;
+    h->ev_class.push_back(cls);
+    cudaEventRecord(h->ev[2 * pair], h->stream);
+  }
+  ~Prof() {
+    if (slot >= 0) cudaEventRecord(h->ev[2 * slot + 1], h->stream);
+  }
+};
 
 template <typename T>
 T* dalloc(st_handle* h, size_t count) {
@@ -344,11 +373,21 @@ template <typename T>
 void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0 = 0,
               int ns = -1) {
   if (ns < 0) ns = lv.N;
+  const int D = h->d, Q = h->q;
+  const double nodes = (double)ns * lv.Nx;
+  // per node: Q fields x (9D-3) FMA for M_h, K_h (tensor-product passes), trace Q + 3D,
+  // time mixing Q^2 + 2Q; bytes: read u, f, write r (+ u0)
+  const double fma = Q * (9.0 * D - 3.0) + Q + 3.0 * D + Q * Q + 2.0 * Q;
+  Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)), 2.0 * fma * nodes);
   STMG_DISPATCH(launch_residual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
 template <typename T>
 void mode_solve(st_handle* h, Level& lv, bool adj, const T* in, T* out, int ns, T scale) {
+  const double nodes = (double)ns * lv.Nx;
+  const double Q = h->q;
+  Prof pr(h, ST_K_MODESOLVE, sizeof(T) * 2.0 * nodes * Q,
+          nodes * (2.0 * Q * Q * Q / 3.0 + 2.0 * Q * Q + 3.0 * Q + 3.0 * h->d));
   STMG_DISPATCH(launch_mode_solve_t, h, lv, adj, in, out, ns, scale);
 }
 
@@ -356,6 +395,9 @@ template <typename T>
 void restrict_to(st_handle* h, int L, const T* r, T* fc) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
+  const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
+  Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_),
+          2.0 * cn * (2.0 * (fine.coarsen_full ? std::pow(3.0, h->d) : 1.0) + 2.0 * h->q));
   STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
 }
 
@@ -363,7 +405,22 @@ template <typename T>
 void prolong_add(st_handle* h, int L, const T* ec, T* uf) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
+  const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
+  Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_),
+          2.0 * fn_ * ((fine.coarsen_full ? std::pow(2.0, h->d) : 1.0) + h->q));
   STMG_DISPATCH(launch_prolong_t, h, fine, coarse, ec, uf);
+}
+
+template <typename T>
+void zero(st_handle* h, T* y, int64_t n) {
+  Prof pr(h, ST_K_VECTOR, sizeof(T) * (double)n, 0.0);
+  stmg::k_fill<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, T(0), n);
+}
+
+template <typename T>
+void copy(st_handle* h, T* y, const T* x, int64_t n) {
+  Prof pr(h, ST_K_VECTOR, 2.0 * sizeof(T) * (double)n, 0.0);
+  stmg::k_scale_copy<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, T(1), n);
 }
 
 // DST-I along every axis of `ns` time steps of data (in place).
@@ -390,6 +447,11 @@ void dst_all_axes(st_handle* h, Level& lv, T* data, int ns, T scale_last) {
     const int64_t stride = (a == 0) ? 1 : inner;
     const unsigned grid = (unsigned)((nlines + W - 1) / W);
     const T scale = (a == D - 1) ? scale_last : T(1);
+    // per line: pre-processing 5 Nf, complex FFT of Nf/2 points 5 (Nf/2) log2(Nf/2),
+    // even/odd split 12 (Nf/2), prefix scan Nf, scaling n
+    const double hf = Nf / 2.0;
+    const double line_flops = 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
+    Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines);
     stmg::k_dst_axis<T><<<grid, nwarps * 32, smem, h->stream>>>(data, n, nlines, (a == 0) ? 1 : inner, stride, W,
                                                                  scale, dt, logh);
     inner *= n;
@@ -402,7 +464,7 @@ template <typename T>
 void block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d, int s0, int ns) {
   const int64_t off = (int64_t)s0 * h->q * lv.Nx;
   const int64_t cnt = (int64_t)ns * h->q * lv.Nx;
-  if (r != d) check(h, cudaMemcpyAsync(d + off, r + off, cnt * sizeof(T), cudaMemcpyDeviceToDevice, h->stream), "copy");
+  if (r != d) copy<T>(h, d + off, r + off, cnt);
   dst_all_axes<T>(h, lv, d + off, ns, T(1));
   const T scale = (T)std::pow(2.0 / (lv.n + 1), h->d);
   mode_solve<T>(h, lv, adj, d + off, d + off, ns, scale);
@@ -411,6 +473,7 @@ void block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d, int s0, in
 
 template <typename T>
 void axpy(st_handle* h, T* y, const T* x, T a, int64_t n) {
+  Prof pr(h, ST_K_VECTOR, 3.0 * sizeof(T) * (double)n, 2.0 * (double)n);
   stmg::k_axpy<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, n);
 }
 
@@ -431,7 +494,7 @@ void coarsest_solve_t(st_handle* h, bool adj, T* u, const T* f, T* work) {
     block_solve<T>(h, lv, adj, f, u, 0, 1);
     return;
   }
-  check(h, cudaMemsetAsync(u, 0, lv.ndof * sizeof(T), h->stream), "memset");
+  zero<T>(h, u, lv.ndof);
   for (int i = 0; i < lv.N; ++i) {
     const int s = adj ? lv.N - 1 - i : i;
     residual<T>(h, lv, adj, f, u, (const T*)nullptr, work, s, 1);
@@ -443,8 +506,12 @@ void coarsest_solve_mixed(st_handle* h, bool adj, float* u, const float* f, floa
   (void)work;
   Level& lv = h->levels[0];
   const int64_t n = lv.ndof;
-  stmg::k_cast_up<<<blocks_for(n), kThreads, 0, h->stream>>>(h->coarse64_f, f, n);
+  {
+    Prof pr(h, ST_K_VECTOR, 12.0 * (double)n, 0.0);
+    stmg::k_cast_up<<<blocks_for(n), kThreads, 0, h->stream>>>(h->coarse64_f, f, n);
+  }
   coarsest_solve_t<double>(h, adj, h->coarse64_u, h->coarse64_f, h->coarse64_r);
+  Prof pr(h, ST_K_VECTOR, 12.0 * (double)n, 0.0);
   stmg::k_cast_down<<<blocks_for(n), kThreads, 0, h->stream>>>(u, h->coarse64_u, 1.0, n);
 }
 
@@ -474,7 +541,7 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0) {
   Level& cl = h->levels[L - 1];
   Vecs<T>& cv = vecs<T>(cl);
   restrict_to<T>(h, L, work, cv.f);
-  check(h, cudaMemsetAsync(cv.u, 0, cl.ndof * sizeof(T), h->stream), "memset");
+  zero<T>(h, cv.u, cl.ndof);
   vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr);
   prolong_add<T>(h, L, cv.u, u);
   for (int i = 0; i < h->opt.nu2; ++i) smooth_step<T>(h, lv, adj, u, f, u0, work);
@@ -482,8 +549,11 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0) {
 
 template <typename T>
 double norm2(st_handle* h, const T* x, int64_t n) {
-  stmg::k_sumsq_partial<T><<<kNormBlocks, kThreads, 0, h->stream>>>(x, n, h->partial);
-  stmg::k_sum_final<<<1, 1024, 0, h->stream>>>(h->partial, kNormBlocks, h->dnorm);
+  {
+    Prof pr(h, ST_K_NORM, sizeof(T) * (double)n, 2.0 * (double)n, 2);
+    stmg::k_sumsq_partial<T><<<kNormBlocks, kThreads, 0, h->stream>>>(x, n, h->partial);
+    stmg::k_sum_final<<<1, 1024, 0, h->stream>>>(h->partial, kNormBlocks, h->dnorm);
+  }
   check(h, cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm copy");
   check(h, cudaStreamSynchronize(h->stream), "norm sync");
   return std::sqrt(*h->hnorm);
@@ -498,10 +568,14 @@ void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
   Vecs<float>& v = lv.v32;
-  stmg::k_cast_down<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(v.f, r, 1.0 / s,
-                                                                                                   lv.ndof);
-  check(h, cudaMemsetAsync(v.u, 0, lv.ndof * sizeof(float), h->stream), "memset");
+  {
+    Prof pr(h, ST_K_VECTOR, 12.0 * (double)lv.ndof, (double)lv.ndof);
+    stmg::k_cast_down<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(
+        v.f, r, 1.0 / s, lv.ndof);
+  }
+  zero<float>(h, v.u, lv.ndof);
   for (int c = 0; c < std::max(1, h->opt.inner_cycles); ++c) vcycle<float>(h, L, adj, v.u, v.f, (const float*)nullptr);
+  Prof pr(h, ST_K_VECTOR, 20.0 * (double)lv.ndof, 2.0 * (double)lv.ndof);
   stmg::k_axpy_up<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(u, v.u, s, lv.ndof);
 }
 
@@ -509,7 +583,7 @@ int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double
                double* relres) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
-  if (!(flags & ST_INIT_GIVEN)) check(h, cudaMemsetAsync(u, 0, lv.ndof * sizeof(double), h->stream), "memset");
+  if (!(flags & ST_INIT_GIVEN)) zero<double>(h, u, lv.ndof);
   double* r = (h->opt.precision == ST_MIXED) ? h->r64 : lv.v64.r;
   residual<double>(h, lv, adj, f, u, u0, r);
   const double r0 = norm2<double>(h, r, lv.ndof);
@@ -681,6 +755,7 @@ void st_destroy(st_handle* h) {
   if (!h) return;
   for (void* p : h->allocs) cudaFree(p);
   if (h->hnorm) cudaFreeHost(h->hnorm);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
 }
 
@@ -804,6 +879,50 @@ int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u) {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
     coarsest_solve_t<double>(h, adjoint != 0, u, f, h->levels[0].v64.r);
     after_launch(h);
+    return ST_OK;
+  });
+}
+
+int st_profile_start(st_handle* h, int max_launches) {
+  return guarded(h, [&]() -> int {
+    if (max_launches < 1) fail(h, ST_EINVAL, "max_launches must be positive");
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+    h->ev_class.clear();
+    h->ev.resize(2 * (size_t)max_launches);
+    for (auto& e : h->ev) check(h, cudaEventCreate(&e), "cudaEventCreate");
+    for (int c = 0; c < ST_K_COUNT; ++c) {
+      h->prof_launches[c] = 0;
+      h->prof_bytes[c] = 0.0;
+      h->prof_flops[c] = 0.0;
+    }
+    h->prof_dropped = 0;
+    h->prof = true;
+    return ST_OK;
+  });
+}
+
+int st_profile_stop(st_handle* h, int* launches, double* ms, double* bytes, double* flops, int* dropped) {
+  return guarded(h, [&]() -> int {
+    if (!h->prof) fail(h, ST_EINVAL, "kernel timing was not started");
+    h->prof = false;
+    check(h, cudaStreamSynchronize(h->stream), "profile sync");
+    double tot[ST_K_COUNT] = {0};
+    for (size_t i = 0; i < h->ev_class.size(); ++i) {
+      float t = 0.f;
+      check(h, cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]), "cudaEventElapsedTime");
+      tot[h->ev_class[i]] += t;
+    }
+    for (int c = 0; c < ST_K_COUNT; ++c) {
+      if (launches) launches[c] = h->prof_launches[c];
+      if (ms) ms[c] = tot[c];
+      if (bytes) bytes[c] = h->prof_bytes[c];
+      if (flops) flops[c] = h->prof_flops[c];
+    }
+    if (dropped) *dropped = h->prof_dropped;
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+    h->ev_class.clear();
     return ST_OK;
   });
 }

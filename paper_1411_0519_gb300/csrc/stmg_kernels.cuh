@@ -557,6 +557,12 @@ __global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, T a, int64_t 
 }
 
 template <typename T>
+__global__ void k_fill(T* __restrict__ y, T v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = v;
+}
+
+template <typename T>
 __global__ void k_scale_copy(T* __restrict__ y, const T* __restrict__ x, T a, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i];

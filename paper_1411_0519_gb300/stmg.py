@@ -26,8 +26,10 @@ EXPORTS = [
     "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
     "st_level_info", "st_residual", "st_vcycle", "st_solve", "st_adjoint_solve", "st_level_residual",
     "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
-    "st_coarsest_solve", "st_norm2",
+    "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop",
 ]
+
+KERNEL_CLASSES = ["residual", "dst", "mode_solve", "restrict", "prolong", "norm", "vector", "smooth"]
 
 
 class StMesh(ctypes.Structure):
@@ -81,6 +83,9 @@ def load_library(path=None):
         "st_level_prolong": (I, [H, I, P, P]),
         "st_coarsest_solve": (I, [H, I, P, P]),
         "st_norm2": (I, [H, P, ctypes.c_size_t, ctypes.POINTER(D)]),
+        "st_profile_start": (I, [H, I]),
+        "st_profile_stop": (I, [H, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                                ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -198,9 +203,11 @@ class Solver:
                                         _ptr(u0, nx, "u0")))
         return u
 
-    def solve(self, f, u0=None, u=None, raise_on_failure=True):
-        """Solve L u = f + IC(u0).  Returns (u, iterations, relative residual)."""
-        init = u is not None
+    def solve(self, f, u0=None, u=None, initial_guess=None, raise_on_failure=True):
+        """Solve L u = f + IC(u0).  ``u`` is the output buffer (allocated if None);
+        it is used as the initial iterate when ``initial_guess`` is true (default:
+        true exactly when ``u`` is given).  Returns (u, iterations, relative residual)."""
+        init = (u is not None) if initial_guess is None else bool(initial_guess)
         u = self.empty() if u is None else u
         nx = self.n ** self.dim
         it, rr = ctypes.c_int(), ctypes.c_double()
@@ -225,6 +232,25 @@ class Solver:
         out = ctypes.c_double()
         self._check(self._lib.st_norm2(self._h, _ptr(x, None, "x"), x.numel(), ctypes.byref(out)))
         return out.value
+
+    # ------------------------------------------------------------ kernel timing
+    def profile_start(self, max_launches=100000):
+        self._check(self._lib.st_profile_start(self._h, max_launches))
+
+    def profile_stop(self):
+        """{class: dict(launches, ms, bytes, flops)} from CUDA events on the
+        solver's stream; bytes / flops are the algorithmic work of those launches."""
+        n = len(KERNEL_CLASSES)
+        launches = (ctypes.c_int * n)()
+        ms = (ctypes.c_double * n)()
+        by = (ctypes.c_double * n)()
+        fl = (ctypes.c_double * n)()
+        dropped = ctypes.c_int()
+        self._check(self._lib.st_profile_stop(self._h, launches, ms, by, fl, ctypes.byref(dropped)))
+        out = {k: {"launches": launches[i], "ms": ms[i], "bytes": by[i], "flops": fl[i]}
+               for i, k in enumerate(KERNEL_CLASSES)}
+        out["_dropped"] = dropped.value
+        return out
 
     # ------------------------------------------------------------ step level
     def level_residual(self, L, f, u, adjoint=False, out=None):

@@ -17,6 +17,7 @@ Workloads (unit square / cube, homogeneous Dirichlet, p_t = DG degree):
                  smooth u0 seed 2, target u_d = low-mode sine series seed 0
   heat2d_511     2D, 511^2 nodes, p_t=1, N=2048, T = mu/128 for
                  mu in {1/16, 1/4, 1, 16}; f ~ U[-1,1] seed 0
+  heat2d_255_n256  heat2d_255 cut to its first 256 time steps (profiling)
 """
 import numpy as np
 
@@ -26,6 +27,9 @@ WORKLOADS = {
     "heat3d_63": dict(d=3, n=63, p_t=2, N=512, T=1.0, rtol=1e-8),
     "adjoint2d_127": dict(d=2, n=127, p_t=1, N=256, T=1.0, rtol=1e-10),
     "heat2d_511": dict(d=2, n=511, p_t=1, N=2048, T=1.0 / 128.0, rtol=1e-8),
+    # profiling case: the 255^2 mesh and tau of heat2d_255 on 256 time steps
+    # (33M unknowns, 266 MB per vector: above L2, a few GB on the device)
+    "heat2d_255_n256": dict(d=2, n=255, p_t=1, N=256, T=0.25, rtol=1e-8),
 }
 
 
