@@ -295,6 +295,20 @@ template <typename T, int D, int Q>
 void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r,
                        int s0, int ns) {
   auto tc = to_coef<T, Q>(h->tm);
+  if (D == 2) {
+    dim3 block(stmg::kResTX, stmg::kResTY);
+    dim3 grid((lv.n + stmg::kResTX - 1) / stmg::kResTX, (lv.n + stmg::kResTY - 1) / stmg::kResTY, 1);
+    for (int c = 0; c < ns; c += 65535) {
+      grid.z = std::min(65535, ns - c);
+      if (adj)
+        stmg::k_residual2d<T, Q, true><<<grid, block, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c, (T)lv.tau,
+                                                                       (T)lv.h, tc);
+      else
+        stmg::k_residual2d<T, Q, false><<<grid, block, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c, (T)lv.tau,
+                                                                        (T)lv.h, tc);
+    }
+    return;
+  }
   dim3 grid(blocks_for(lv.Nx), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
@@ -423,37 +437,58 @@ void copy(st_handle* h, T* y, const T* x, int64_t n) {
   stmg::k_scale_copy<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, T(1), n);
 }
 
-// DST-I along every axis of `ns` time steps of data (in place).
+// Shared-memory bytes of the sine-transform kernels (see stmg_kernels.cuh).
+constexpr int kDstWarps = 8;
+constexpr int kDstRowsPerCta = 32;
+template <typename T>
+size_t dst_rows_smem(int Nf) { return (size_t)(2 + 2 * kDstWarps) * Nf * sizeof(T); }
+template <typename T, int W>
+size_t dst_cols_smem(int Nf) {
+  return W * sizeof(int64_t) + ((size_t)2 * Nf + (size_t)W * (Nf + 1) + (size_t)kDstWarps * Nf) * sizeof(T);
+}
+
+template <typename T>
+void dst_set_smem_limits(st_handle* h, int maxNf) {
+  check(h, cudaFuncSetAttribute(stmg::k_dst_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_rows_smem<T>(maxNf)), "cudaFuncSetAttribute");
+  check(h, cudaFuncSetAttribute(stmg::k_dst_cols<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_cols_smem<T, 32>(maxNf)), "cudaFuncSetAttribute");
+  check(h, cudaFuncSetAttribute(stmg::k_dst_cols<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_cols_smem<T, 16>(maxNf)), "cudaFuncSetAttribute");
+}
+
+// DST-I along every axis of `ns` time steps of data (in place); the last axis
+// is scaled by scale_last.
 template <typename T>
 void dst_all_axes(st_handle* h, Level& lv, T* data, int ns, T scale_last) {
   const int n = lv.n, Nf = n + 1, D = h->d;
   int logh = 0;
   while ((1 << (logh + 1)) <= Nf / 2) ++logh;
-  const int W = (Nf >= 512 && sizeof(T) == 8) ? 16 : 32;
-  const int nwarps = 8;
-  const size_t smem = (size_t)(W + nwarps) * Nf * sizeof(T);
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    check(h, cudaFuncSetAttribute(stmg::k_dst_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
-          "cudaFuncSetAttribute");
-    attr_set[sizeof(T) == 8] = true;
-  }
   Tables<T>& tb = tables<T>(lv);
   stmg::DstTables<T> dt{tb.sinp, tb.twc, tb.tws};
   const int64_t slabs = (int64_t)ns * h->q;
+  const int64_t nlines = slabs * lv.Nx / n;
+  // per line: pre-processing 5 Nf, complex FFT of Nf/2 points 5 (Nf/2) log2(Nf/2),
+  // even/odd split 12 (Nf/2), prefix scan Nf, scaling n
+  const double hf = Nf / 2.0;
+  const double line_flops = 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
   int64_t inner = 1;
   for (int a = 0; a < D; ++a) {
-    const int64_t nlines = slabs * lv.Nx / n;
-    const int64_t stride = (a == 0) ? 1 : inner;
-    const unsigned grid = (unsigned)((nlines + W - 1) / W);
     const T scale = (a == D - 1) ? scale_last : T(1);
-    // per line: pre-processing 5 Nf, complex FFT of Nf/2 points 5 (Nf/2) log2(Nf/2),
-    // even/odd split 12 (Nf/2), prefix scan Nf, scaling n
-    const double hf = Nf / 2.0;
-    const double line_flops = 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
     Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines);
-    stmg::k_dst_axis<T><<<grid, nwarps * 32, smem, h->stream>>>(data, n, nlines, (a == 0) ? 1 : inner, stride, W,
-                                                                 scale, dt, logh);
+    if (a == 0) {
+      const unsigned grid = (unsigned)((nlines + kDstRowsPerCta - 1) / kDstRowsPerCta);
+      stmg::k_dst_rows<T><<<grid, kDstWarps * 32, dst_rows_smem<T>(Nf), h->stream>>>(data, n, logh, nlines,
+                                                                                     kDstRowsPerCta, scale, dt);
+    } else if (sizeof(T) == 8 && Nf >= 512) {
+      const unsigned grid = (unsigned)((nlines + 15) / 16);
+      stmg::k_dst_cols<T, 16><<<grid, kDstWarps * 32, dst_cols_smem<T, 16>(Nf), h->stream>>>(data, n, logh, nlines,
+                                                                                             inner, scale, dt);
+    } else {
+      const unsigned grid = (unsigned)((nlines + 31) / 32);
+      stmg::k_dst_cols<T, 32><<<grid, kDstWarps * 32, dst_cols_smem<T, 32>(Nf), h->stream>>>(data, n, logh, nlines,
+                                                                                             inner, scale, dt);
+    }
     inner *= n;
   }
 }
@@ -735,6 +770,10 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       h->coarse64_r = dalloc<double>(h, c.ndof);
       h->r64 = finest(h).v64.r;
     }
+    int maxNf = 2;
+    for (const Level& l : h->levels) maxNf = std::max(maxNf, l.n + 1);
+    dst_set_smem_limits<double>(h, maxNf);
+    if (mixed) dst_set_smem_limits<float>(h, maxNf);
     h->partial = dalloc<double>(h, kNormBlocks);
     h->dnorm = dalloc<double>(h, 1);
     check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");

@@ -179,6 +179,91 @@ __global__ void k_residual(const T* __restrict__ f, const T* __restrict__ u,
 }
 
 // ---------------------------------------------------------------------------
+// 2D residual with a shared-memory tile (same result as k_residual<T, 2, Q, ADJ>).
+// A CTA owns a TX x TY block of nodes of one time step.  It stages u (Q fields)
+// and the coupling trace of the neighbouring step on the tile plus a one-node
+// halo, applies the x passes of M_1 and K_1 once per staged row, then the y
+// passes per node: M_h u = M_1y (M_1x u), K_h u = K_1y (M_1x u) + M_1y (K_1x u).
+// ---------------------------------------------------------------------------
+constexpr int kResTX = 32;
+constexpr int kResTY = 8;
+
+template <typename T, int Q, bool ADJ>
+__global__ void __launch_bounds__(kResTX * kResTY) k_residual2d(const T* __restrict__ f, const T* __restrict__ u,
+                                                                const T* __restrict__ u0, T* __restrict__ r,
+                                                                int n, int N, int s0, T tau, T h,
+                                                                TimeCoef<T, Q> tc) {
+  constexpr int HX = kResTX + 2, HY = kResTY + 2;
+  __shared__ T su[Q + 1][HY][HX];        // fields 0..Q-1: u_s; field Q: coupling trace
+  __shared__ T sa[Q + 1][HY][kResTX];    // M_1 along x
+  __shared__ T sb[Q][HY][kResTX];        // K_1 along x
+  const int s = s0 + blockIdx.z;
+  const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
+  const int tid = threadIdx.y * kResTX + threadIdx.x;
+  const int64_t Nx = (int64_t)n * n;
+  const T* nb = nullptr;                 // neighbouring step (forward: s-1, adjoint: s+1)
+  if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
+  if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
+  const bool use_u0 = !ADJ && s == 0 && u0 != nullptr;
+  // stage u_s and the trace on tile + halo (zero outside the domain)
+  for (int i = tid; i < HX * HY; i += kResTX * kResTY) {
+    const int hy = i / HX, hx = i - hy * HX;
+    const int x = x0 + hx - 1, y = y0 + hy - 1;
+    const bool in = x >= 0 && x < n && y >= 0 && y < n;
+    const int64_t j = (int64_t)y * n + x;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) su[l][hy][hx] = in ? u[((int64_t)s * Q + l) * Nx + j] : T(0);
+    T t = T(0);
+    if (in) {
+      if (nb != nullptr) {
+#pragma unroll
+        for (int l = 0; l < Q; ++l) t += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + j];
+      } else if (use_u0) {
+        t = u0[j];
+      }
+    }
+    su[Q][hy][hx] = t;
+  }
+  __syncthreads();
+  const T m0 = h / T(6), m1 = T(4) * h / T(6);
+  const T k0 = T(-1) / h, k1 = T(2) / h;
+  // x passes on every staged row
+  for (int i = tid; i < HY * kResTX; i += kResTX * kResTY) {
+    const int hy = i / kResTX, tx = i - hy * kResTX;
+#pragma unroll
+    for (int l = 0; l <= Q; ++l) {
+      const T a = su[l][hy][tx], b = su[l][hy][tx + 1], c = su[l][hy][tx + 2];
+      sa[l][hy][tx] = m0 * (a + c) + m1 * b;
+      if (l < Q) sb[l][hy][tx] = k0 * (a + c) + k1 * b;
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= n || y >= n || s >= N) return;
+  T mu[Q], ku[Q];
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const T a0 = sa[l][ty][tx], a1 = sa[l][ty + 1][tx], a2 = sa[l][ty + 2][tx];
+    const T b0 = sb[l][ty][tx], b1 = sb[l][ty + 1][tx], b2 = sb[l][ty + 2][tx];
+    mu[l] = m0 * (a0 + a2) + m1 * a1;
+    ku[l] = k0 * (a0 + a2) + k1 * a1 + m0 * (b0 + b2) + m1 * b1;
+  }
+  const T mt = m0 * (sa[Q][ty][tx] + sa[Q][ty + 2][tx]) + m1 * sa[Q][ty + 1][tx];
+  const int64_t j = (int64_t)y * n + x;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    T acc = f[idx];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc -= (ADJ ? tc.K[l * Q + k] : tc.K[k * Q + l]) * mu[l];
+    acc -= tau * tc.Mh[k] * ku[k];
+    acc += (ADJ ? tc.en[k] : tc.st[k]) * mt;
+    r[idx] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Batched DST-I along one spatial axis, X_j = sum_{m=1}^{n} x_m sin(pi j m / Nf),
 // Nf = n + 1 a power of two.  Exact block inverse of Section 3.1 (the
 // eigenvectors of M_1 and K_1 are the sine vectors).
@@ -190,64 +275,76 @@ __global__ void k_residual(const T* __restrict__ f, const T* __restrict__ u,
 // The real DFT of length Nf uses a complex radix-2 FFT of length Nf/2 on
 // z_m = y_{2m} + i y_{2m+1} followed by the even/odd split.
 //
-// One warp transforms one line held in shared memory.  Each CTA stages W lines:
-// line w of the tile starts at gbase(w) and has element stride `stride`.
-// tables: sinp[j] = sin(j pi / Nf) (j < Nf), twc/tws[k] = cos/sin(2 pi k / Nf) (k < Nf).
+// One warp transforms one line held in shared memory.  Rows of the x axis are
+// contiguous: each warp streams its own rows (k_dst_rows).  Lines of the y / z
+// axes are columns with stride n^a: a CTA stages a tile of W consecutive
+// columns so that every global access is a W-wide contiguous segment
+// (k_dst_cols).  Twiddles are staged in shared memory once per CTA.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct DstTables {
-  const T* sinp;
-  const T* twc;
-  const T* tws;
+  const T* sinp;   // sin(j pi / Nf), j < Nf
+  const T* twc;    // cos(2 pi k / Nf), k < Nf
+  const T* tws;    // sin(2 pi k / Nf)
 };
+
+// sm[0..Nf) = sin(j pi / Nf); sm[Nf..Nf+half) = cos(2 pi k / Nf); then sin(2 pi k / Nf).
+template <typename T>
+__device__ __forceinline__ void stage_tables(T* sm, int Nf, DstTables<T> tb) {
+  const int half = Nf >> 1;
+  for (int i = threadIdx.x; i < Nf; i += blockDim.x) sm[i] = tb.sinp[i];
+  for (int i = threadIdx.x; i < half; i += blockDim.x) {
+    sm[Nf + i] = tb.twc[i];
+    sm[Nf + half + i] = tb.tws[i];
+  }
+}
 
 // Transform one line in place: x[0..Nf-1] (x[0] unused on input, x[j] = x_j),
 // zr/zi scratch of length Nf/2.  Output X_j in x[j], j = 1..Nf-1.
 template <typename T>
-__device__ void dst1_warp(T* x, T* zr, T* zi, int Nf, int logh, DstTables<T> tb, int lane) {
+__device__ void dst1_warp(T* x, T* zr, T* zi, int Nf, int logh, const T* sinp, const T* wc, const T* ws,
+                          int lane) {
   const int half = Nf >> 1;
   // 1. pre-processing and packing into bit-reversed order
   for (int m = lane; m < half; m += 32) {
-    T y0 = T(0), y1;
-    int j0 = 2 * m, j1 = 2 * m + 1;
-    if (j0 > 0) y0 = tb.sinp[j0] * (x[j0] + x[Nf - j0]) + T(0.5) * (x[j0] - x[Nf - j0]);
-    y1 = tb.sinp[j1] * (x[j1] + x[Nf - j1]) + T(0.5) * (x[j1] - x[Nf - j1]);
-    int br = logh > 0 ? (int)(__brev((unsigned)m) >> (32 - logh)) : 0;
+    const int j0 = 2 * m, j1 = 2 * m + 1;
+    T y0 = T(0);
+    if (j0 > 0) y0 = sinp[j0] * (x[j0] + x[Nf - j0]) + T(0.5) * (x[j0] - x[Nf - j0]);
+    const T y1 = sinp[j1] * (x[j1] + x[Nf - j1]) + T(0.5) * (x[j1] - x[Nf - j1]);
+    const int br = logh > 0 ? (int)(__brev((unsigned)m) >> (32 - logh)) : 0;
     zr[br] = y0;
     zi[br] = y1;
   }
   __syncwarp();
   // 2. radix-2 decimation-in-time FFT, e^{-2 pi i jk / half}
-  for (int len = 2; len <= half; len <<= 1) {
-    const int hl = len >> 1;
-    const int tstride = Nf / len;
+  for (int lhl = 0; lhl < logh; ++lhl) {
+    const int hl = 1 << lhl;                 // half length of the butterfly group
+    const int tshift = logh - lhl;           // twiddle index = jj * (Nf / (2 hl)) = jj << tshift
     for (int b = lane; b < (half >> 1); b += 32) {
-      int grp = b / hl, jj = b - grp * hl;
-      int i0 = grp * len + jj, i1 = i0 + hl;
-      T wc = tb.twc[tstride * jj], ws = -tb.tws[tstride * jj];   // w = e^{-2 pi i jj / len}
-      T ar = zr[i1], ai = zi[i1];
-      T tr = wc * ar - ws * ai, ti = wc * ai + ws * ar;
-      T br0 = zr[i0], bi0 = zi[i0];
-      zr[i1] = br0 - tr; zi[i1] = bi0 - ti;
-      zr[i0] = br0 + tr; zi[i0] = bi0 + ti;
+      const int grp = b >> lhl, jj = b & (hl - 1);
+      const int i0 = (grp << (lhl + 1)) + jj, i1 = i0 + hl;
+      const T wr = wc[jj << tshift], wi = -ws[jj << tshift];   // w = e^{-2 pi i jj / (2 hl)}
+      const T ar = zr[i1], ai = zi[i1];
+      const T tr = wr * ar - wi * ai, ti = wr * ai + wi * ar;
+      const T br0 = zr[i0], bi0 = zi[i0];
+      zr[i1] = br0 - tr;
+      zi[i1] = bi0 - ti;
+      zr[i0] = br0 + tr;
+      zi[i0] = bi0 + ti;
     }
     __syncwarp();
   }
   // 3. even/odd split: Y_k = E_k + W^k O_k, W = e^{-2 pi i / Nf};
   //    R_k -> x[2k+1], I_k = -Im Y_k -> x[2k]
   for (int k = lane; k < half; k += 32) {
-    int kc = (half - k) & (half - 1);
-    T zkr = zr[k], zki = zi[k];
-    T zcr = zr[kc], zci = -zi[kc];            // conj(Z_{half-k})
-    T er = T(0.5) * (zkr + zcr), ei = T(0.5) * (zki + zci);
-    // O = (Zk - Zc) / (2i) = (dI / 2) - i (dR / 2)
-    T dr = zkr - zcr, di = zki - zci;
-    T orr = T(0.5) * di, oi = T(-0.5) * dr;
-    T wc = tb.twc[k], ws = -tb.tws[k];
-    T yr = er + (wc * orr - ws * oi);
-    T yi = ei + (wc * oi + ws * orr);
-    x[2 * k + 1] = yr;
-    x[2 * k] = -yi;
+    const int kc = (half - k) & (half - 1);
+    const T zkr = zr[k], zki = zi[k];
+    const T zcr = zr[kc], zci = -zi[kc];   // conj(Z_{half-k})
+    const T er = T(0.5) * (zkr + zcr), ei = T(0.5) * (zki + zci);
+    const T orr = T(0.5) * (zki - zci), oi = T(-0.5) * (zkr - zcr);   // (Zk - Zc) / (2i)
+    const T wr = wc[k], wi = -ws[k];
+    x[2 * k + 1] = er + (wr * orr - wi * oi);
+    x[2 * k] = -(ei + (wr * oi + wi * orr));
   }
   __syncwarp();
   // 4. X_{2k+1} = sum_{k' <= k} R_k' - R_0 / 2  (warp prefix scan over half values)
@@ -265,7 +362,7 @@ __device__ void dst1_warp(T* x, T* zr, T* zi, int Nf, int logh, DstTables<T> tb,
   T incl = loc;                      // inclusive scan of chunk totals across lanes
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    T v = __shfl_up_sync(0xffffffffu, incl, off);
+    const T v = __shfl_up_sync(0xffffffffu, incl, off);
     if (lane >= off) incl += v;
   }
   const T shift = (incl - loc) - T(0.5) * R0;
@@ -275,56 +372,73 @@ __device__ void dst1_warp(T* x, T* zr, T* zi, int Nf, int logh, DstTables<T> tb,
   __syncwarp();
 }
 
+// x axis: `nrows` contiguous rows of length n; each CTA handles rows_per_cta
+// rows, each warp its own rows with warp-private buffers.
+// Shared memory: 2 Nf (tables) + nwarps * 2 Nf elements.
 template <typename T>
-__global__ void k_dst_axis(T* __restrict__ data, int n, int64_t nlines, int64_t inner,
-                           int64_t stride, int W, T scale, DstTables<T> tb, int logh) {
-  // Line id g -> (outer, in) with in < inner; base = outer * inner * n + in (axis
-  // stride = inner); for the x axis inner = 1 and stride = 1.
+__global__ void __launch_bounds__(256) k_dst_rows(T* __restrict__ data, int n, int logh, int64_t nrows,
+                                                  int rows_per_cta, T scale, DstTables<T> tb) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int Nf = n + 1;
-  const int half = Nf >> 1;
-  const int nwarps = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* xs = sm;                                   // W lines x Nf
-  T* zs = sm + (int64_t)W * Nf;                 // per warp: zr[half], zi[half]
-  T* zr = zs + (int64_t)warp * Nf;
+  const int Nf = n + 1, half = Nf >> 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const T* sinp = sm;
+  const T* wc = sm + Nf;
+  const T* ws = sm + Nf + half;
+  T* x = sm + 2 * Nf + (int64_t)warp * 2 * Nf;
+  T* zr = x + Nf;
   T* zi = zr + half;
-  const int64_t g0 = (int64_t)blockIdx.x * W;   // first line of this tile
+  stage_tables<T>(sm, Nf, tb);
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  for (int w = warp; w < rows_per_cta; w += nwarps) {
+    const int64_t g = r0 + w;
+    if (g >= nrows) break;                 // uniform across the warp
+    T* row = data + g * n;
+    for (int j = lane; j < n; j += 32) x[1 + j] = row[j];
+    __syncwarp();
+    dst1_warp<T>(x, zr, zi, Nf, logh, sinp, wc, ws, lane);
+    for (int j = lane; j < n; j += 32) row[j] = scale * x[1 + j];
+    __syncwarp();
+  }
+}
+
+// y / z axis: line g = (outer, in), in < inner, starts at outer * inner * n + in
+// and has stride inner.  Each CTA stages W consecutive lines.
+// Shared memory: 2 Nf (tables) + W int64 bases + W (Nf + 1) tile + nwarps Nf.
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_dst_cols(T* __restrict__ data, int n, int logh, int64_t nlines,
+                                                  int64_t inner, T scale, DstTables<T> tb) {
+  extern __shared__ unsigned char smem_raw[];
+  const int Nf = n + 1, half = Nf >> 1, ld = Nf + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  int64_t* base = reinterpret_cast<int64_t*>(smem_raw);
+  T* sm = reinterpret_cast<T*>(smem_raw + W * sizeof(int64_t));
+  const T* sinp = sm;
+  const T* wc = sm + Nf;
+  const T* ws = sm + Nf + half;
+  T* tile = sm + 2 * Nf;
+  T* zr = tile + (int64_t)W * ld + (int64_t)warp * Nf;
+  T* zi = zr + half;
+  const int64_t g0 = (int64_t)blockIdx.x * W;
   const int wcount = (int)((nlines - g0) < W ? (nlines - g0) : W);
-  // load
-  if (stride == 1) {
-    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
-      int w = idx / n, jj = idx - w * n;
-      int64_t g = g0 + w;
-      xs[w * Nf + 1 + jj] = data[g * n + jj];
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
-      int jj = idx / wcount, w = idx - jj * wcount;
-      int64_t g = g0 + w;
-      int64_t outer = g / inner, in = g - outer * inner;
-      xs[w * Nf + 1 + jj] = data[outer * inner * n + in + (int64_t)jj * stride];
-    }
+  if (threadIdx.x < W && (int)threadIdx.x < wcount) {
+    const int64_t g = g0 + threadIdx.x;
+    const int64_t outer = g / inner, in = g - outer * inner;
+    base[threadIdx.x] = outer * inner * n + in;
+  }
+  stage_tables<T>(sm, Nf, tb);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < W * n; idx += blockDim.x) {
+    const int w = idx % W, j = idx / W;
+    if (w < wcount) tile[w * ld + 1 + j] = data[base[w] + (int64_t)j * inner];
   }
   __syncthreads();
-  for (int w = warp; w < wcount; w += nwarps) {
-    dst1_warp<T>(xs + w * Nf, zr, zi, Nf, logh, tb, lane);
-  }
+  for (int w = warp; w < wcount; w += nwarps) dst1_warp<T>(tile + w * ld, zr, zi, Nf, logh, sinp, wc, ws, lane);
   __syncthreads();
-  if (stride == 1) {
-    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
-      int w = idx / n, jj = idx - w * n;
-      int64_t g = g0 + w;
-      data[g * n + jj] = scale * xs[w * Nf + 1 + jj];
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < wcount * n; idx += blockDim.x) {
-      int jj = idx / wcount, w = idx - jj * wcount;
-      int64_t g = g0 + w;
-      int64_t outer = g / inner, in = g - outer * inner;
-      data[outer * inner * n + in + (int64_t)jj * stride] = scale * xs[w * Nf + 1 + jj];
-    }
+  for (int idx = threadIdx.x; idx < W * n; idx += blockDim.x) {
+    const int w = idx % W, j = idx / W;
+    if (w < wcount) data[base[w] + (int64_t)j * inner] = scale * tile[w * ld + 1 + j];
   }
 }
 
