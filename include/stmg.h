@@ -182,6 +182,32 @@ int st_profile_start(st_handle* h, int max_launches);
  * Launches beyond max_launches are counted but not timed (*dropped). */
 int st_profile_stop(st_handle* h, int* launches, double* ms, double* bytes, double* flops, int* dropped);
 
+/* ---- allocation-free norm ----
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory -- an application whose allocator owns the GPU's
+ * memory after start-up, or a code path that must not take the implicit
+ * device synchronisation of cudaMalloc / cudaFree.  It needs no handle.
+ *
+ * *out (a DEVICE pointer to one double) = ||x||_2 of n FP64 values at the
+ * device pointer x, asynchronously on cuda_stream (NULL = default stream),
+ * with the same deterministic two-stage sum of squares as st_norm2 (one
+ * FP64 partial per chunk of 65536 elements, then one block adds them in a
+ * fixed order).  It calls no allocator: the partial sums live in a fixed
+ * 128 KB device array inside this library, which every GPU that loads the
+ * library holds until the process exits.
+ *  - n must not exceed ST_NOALLOC_MAX_ELEMENTS (2^30); larger n returns
+ *    ST_EINVAL before any device work.  x or out NULL: ST_EINVAL.
+ *  - The array is shared by all calls; calls whose kernels can overlap on
+ *    the GPU (different streams with no ordering) race on it and give wrong
+ *    results.  Each call overwrites every partial it reads, so nothing has to
+ *    be cleared between calls.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture.
+ * Errors: ST_EINVAL, ST_ECUDA (address lookup or launch failed). */
+#define ST_NOALLOC_MAX_ELEMENTS ((size_t)1 << 30)
+int st_norm2_noalloc(const double* x, size_t n, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

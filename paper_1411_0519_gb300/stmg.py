@@ -26,8 +26,10 @@ EXPORTS = [
     "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
     "st_level_info", "st_residual", "st_vcycle", "st_solve", "st_adjoint_solve", "st_level_residual",
     "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
-    "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop",
+    "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop", "st_norm2_noalloc",
 ]
+
+ST_NOALLOC_MAX_ELEMENTS = 1 << 30
 
 KERNEL_CLASSES = ["residual", "dst", "mode_solve", "restrict", "prolong", "norm", "vector", "smooth"]
 
@@ -84,6 +86,7 @@ def load_library(path=None):
         "st_coarsest_solve": (I, [H, I, P, P]),
         "st_norm2": (I, [H, P, ctypes.c_size_t, ctypes.POINTER(D)]),
         "st_profile_start": (I, [H, I]),
+        "st_norm2_noalloc": (I, [P, ctypes.c_size_t, P, P]),
         "st_profile_stop": (I, [H, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(I)]),
     }
@@ -287,6 +290,20 @@ class Solver:
         m = self.level_ndof(0)
         self._check(self._lib.st_coarsest_solve(self._h, int(adjoint), _ptr(f, m, "f"), _ptr(out, m, "u")))
         return out
+
+
+def norm2_noalloc(x, out=None, stream=None):
+    """||x||_2 into a one-element device tensor without any device allocation by
+    the library (st_norm2_noalloc); ``out`` must be given by callers that
+    cannot allocate either."""
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    stream = torch.cuda.current_stream(x.device) if stream is None else stream
+    rc = lib().st_norm2_noalloc(_ptr(x, None, "x"), x.numel(), _ptr(out, 1, "out"),
+                                ctypes.c_void_p(stream.cuda_stream))
+    if rc != ST_OK:
+        raise StmgError(rc, "st_norm2_noalloc failed")
+    return out
 
 
 class SpaceTimeSolve(torch.autograd.Function):
