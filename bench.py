@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--inner-cycles", type=int, default=2)
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+                    help="run one precision only (profiling); the line's value is that precision's")
     return ap.parse_args()
 
 
@@ -241,6 +243,30 @@ def run_reference(args):
     return 0
 
 
+def run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_over_ranks, local):
+    """Mixed-precision solve alone (used for profiling its kernels)."""
+    d, n, p, N, T, rtol = w["d"], w["n"], w["p_t"], w["N"], w["T"], w["rtol"]
+    smx = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="mixed", inner_cycles=args.inner_cycles)
+    clocks = ClockSampler(local)
+    clocks.start()
+    msm, itm, rrm, profm = time_solves(torch, smx, f, u0, None, args.steps, args.warmup, barrier)
+    ck = clocks.stop()
+    msm = max_over_ranks(msm)
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * smx.ndof / (msm / args.steps / 1e3), "unit": "DoF/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msm / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 V-cycle in f64 refinement", "data": "synthetic",
+                "config": {"workload": args.workload, "d": d, "n": n, "p_t": p, "N": N, "T": T, "rtol": rtol,
+                           "precision": "mixed", "inner_cycles": args.inner_cycles},
+                "iters": itm[-1], "relres": rrm, "roofline": roofline(profm, True, pk), "kernels": breakdown(profm),
+                "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_")),
+                "clocks": ck}
+        print(json.dumps(line), flush=True)
+    smx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -271,6 +297,9 @@ def main():
     f = torch.from_numpy(f_np).cuda()
     u0 = torch.from_numpy(u0_np).cuda()
     pk = peaks()
+
+    if args.only == "mixed":
+        return run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_over_ranks, local)
 
     # ---------------------------------------------------------------- FP64 (headline)
     s64 = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="fp64")
@@ -316,7 +345,7 @@ def main():
 
     # ---------------------------------------------------------------- mixed precision
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and args.only != "fp64":
         smx = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="mixed", inner_cycles=args.inner_cycles)
         msm, itm, rrm, profm = time_solves(torch, smx, f, u0, None, args.steps, max(1, args.warmup), barrier)
         msm = max_over_ranks(msm)

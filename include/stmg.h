@@ -161,12 +161,12 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
  * Kernel classes for st_profile_stop: */
 #define ST_K_RESIDUAL   0   /* residual (forward / transposed) */
 #define ST_K_DST        1   /* batched sine transform along one axis */
-#define ST_K_MODESOLVE  2   /* per-mode q x q solve */
+#define ST_K_LINESOLVE  2   /* block-tridiagonal line solve per sine mode */
 #define ST_K_RESTRICT   3
 #define ST_K_PROLONG    4
 #define ST_K_NORM       5   /* both reduction stages */
 #define ST_K_VECTOR     6   /* axpy, casts, copies, memsets */
-#define ST_K_SMOOTH     7   /* fused smoothing kernels */
+#define ST_K_RHS        7   /* smoother right-hand side f - B u_prev */
 #define ST_K_COUNT      8
 
 /* Record a CUDA event pair around every kernel launched by this handle, for up

@@ -134,11 +134,11 @@ double mu_star(int p) {
 
 template <typename T>
 struct Tables {
-  T* mval = nullptr;  // m_k = h/3 (2 + cos(k pi / Nf)), k = 1..n
-  T* kval = nullptr;  // kappa_k = 2/h (1 - cos(k pi / Nf))
   T* sinp = nullptr;  // sin(j pi / Nf), j = 0..Nf-1
   T* twc = nullptr;   // cos(2 pi k / Nf), k = 0..Nf-1
   T* tws = nullptr;   // sin(2 pi k / Nf)
+  T* fac[2] = {nullptr, nullptr};    // line-solve LU factors (forward, adjoint)
+  T* ecoef[2] = {nullptr, nullptr};  // off-diagonal blocks E per mode
 };
 
 template <typename T>
@@ -253,30 +253,123 @@ void upload(st_handle* h, T* dst, const std::vector<double>& src) {
   check(h, cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice), "upload table");
 }
 
+// Host FP64 block-LU factors of the per-mode line systems (see k_line_solve):
+// fac[((j*2 + w)*q*q + e)*nmodes + mode] (w = 0: L_j, w = 1: W_j^{-1}),
+// ecoef[e*nmodes + mode].
+void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool adj, std::vector<double>& fac,
+                  std::vector<double>& ecoef) {
+  const int q = tm.q, qq = q * q;
+  const int Nf = n + 1;
+  int64_t nmodes = 1;
+  for (int a = 0; a < D - 1; ++a) nmodes *= n;
+  std::vector<double> m1(n), k1(n);
+  for (int k = 1; k <= n; ++k) {
+    const double c = std::cos(k * M_PI / Nf);
+    m1[k - 1] = h / 3.0 * (2.0 + c);
+    k1[k - 1] = 2.0 / h * (1.0 - c);
+  }
+  fac.assign((size_t)n * 2 * qq * nmodes, 0.0);
+  ecoef.assign((size_t)qq * nmodes, 0.0);
+  std::vector<double> K(qq), Dg(qq), E(qq), W(qq), Wi(qq), L(qq), tmp(qq);
+  for (int k = 0; k < q; ++k)
+    for (int l = 0; l < q; ++l) K[k * q + l] = adj ? tm.K[l * q + k] : tm.K[k * q + l];
+  auto inv = [q](const std::vector<double>& A, std::vector<double>& X) {
+    // Gauss-Jordan with partial pivoting on a q x q matrix
+    std::vector<double> M(A);
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) X[i * q + j] = (i == j) ? 1.0 : 0.0;
+    for (int c = 0; c < q; ++c) {
+      int p = c;
+      for (int r = c + 1; r < q; ++r)
+        if (std::fabs(M[r * q + c]) > std::fabs(M[p * q + c])) p = r;
+      if (p != c)
+        for (int j = 0; j < q; ++j) {
+          std::swap(M[c * q + j], M[p * q + j]);
+          std::swap(X[c * q + j], X[p * q + j]);
+        }
+      const double d = 1.0 / M[c * q + c];
+      for (int j = 0; j < q; ++j) {
+        M[c * q + j] *= d;
+        X[c * q + j] *= d;
+      }
+      for (int r = 0; r < q; ++r) {
+        if (r == c) continue;
+        const double f = M[r * q + c];
+        for (int j = 0; j < q; ++j) {
+          M[r * q + j] -= f * M[c * q + j];
+          X[r * q + j] -= f * X[c * q + j];
+        }
+      }
+    }
+  };
+  for (int64_t mode = 0; mode < nmodes; ++mode) {
+    double lamM = 1.0, lamK = 0.0;
+    if (D == 2) {
+      lamM = m1[mode];
+      lamK = k1[mode];
+    } else if (D == 3) {
+      const int ix = (int)(mode % n), iy = (int)(mode / n);
+      lamM = m1[ix] * m1[iy];
+      lamK = k1[ix] * m1[iy] + m1[ix] * k1[iy];
+    }
+    for (int k = 0; k < q; ++k)
+      for (int l = 0; l < q; ++l) {
+        const double mt = (k == l) ? tau * tm.Mh[k] : 0.0;
+        Dg[k * q + l] = lamM * (4.0 * h / 6.0) * K[k * q + l] + mt * (lamM * 2.0 / h + lamK * 4.0 * h / 6.0);
+        E[k * q + l] = lamM * (h / 6.0) * K[k * q + l] + mt * (-lamM / h + lamK * h / 6.0);
+      }
+    for (int e = 0; e < qq; ++e) ecoef[(size_t)e * nmodes + mode] = E[e];
+    W = Dg;
+    for (int j = 0; j < n; ++j) {
+      if (j > 0) {
+        // L_j = E W_{j-1}^{-1};  W_j = Dg - L_j E
+        for (int a = 0; a < q; ++a)
+          for (int b = 0; b < q; ++b) {
+            double acc = 0.0;
+            for (int c = 0; c < q; ++c) acc += E[a * q + c] * Wi[c * q + b];
+            L[a * q + b] = acc;
+          }
+        for (int a = 0; a < q; ++a)
+          for (int b = 0; b < q; ++b) {
+            double acc = Dg[a * q + b];
+            for (int c = 0; c < q; ++c) acc -= L[a * q + c] * E[c * q + b];
+            W[a * q + b] = acc;
+          }
+      } else {
+        std::fill(L.begin(), L.end(), 0.0);
+      }
+      inv(W, Wi);
+      for (int e = 0; e < qq; ++e) {
+        fac[(((size_t)j * 2 + 0) * qq + e) * nmodes + mode] = L[e];
+        fac[(((size_t)j * 2 + 1) * qq + e) * nmodes + mode] = Wi[e];
+      }
+    }
+  }
+}
+
 template <typename T>
 void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
   const int n = lv.n, Nf = n + 1;
-  std::vector<double> mv(n), kv(n), sp(Nf), tc(Nf), ts(Nf);
-  for (int k = 1; k <= n; ++k) {
-    double c = std::cos(k * M_PI / Nf);
-    mv[k - 1] = lv.h / 3.0 * (2.0 + c);
-    kv[k - 1] = 2.0 / lv.h * (1.0 - c);
-  }
+  std::vector<double> sp(Nf), tc(Nf), ts(Nf);
   for (int j = 0; j < Nf; ++j) {
     sp[j] = std::sin(j * M_PI / Nf);
     tc[j] = std::cos(2.0 * M_PI * j / Nf);
     ts[j] = std::sin(2.0 * M_PI * j / Nf);
   }
-  tb.mval = dalloc<T>(h, n);
-  tb.kval = dalloc<T>(h, n);
   tb.sinp = dalloc<T>(h, Nf);
   tb.twc = dalloc<T>(h, Nf);
   tb.tws = dalloc<T>(h, Nf);
-  upload(h, tb.mval, mv);
-  upload(h, tb.kval, kv);
   upload(h, tb.sinp, sp);
   upload(h, tb.twc, tc);
   upload(h, tb.tws, ts);
+  for (int adj = 0; adj < 2; ++adj) {
+    std::vector<double> fac, ec;
+    line_factors(h->tm, h->d, n, lv.h, lv.tau, adj != 0, fac, ec);
+    tb.fac[adj] = dalloc<T>(h, fac.size());
+    tb.ecoef[adj] = dalloc<T>(h, ec.size());
+    upload(h, tb.fac[adj], fac);
+    upload(h, tb.ecoef[adj], ec);
+  }
 }
 
 template <typename T> Vecs<T>& vecs(Level& lv);
@@ -322,19 +415,40 @@ void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, cons
 }
 
 template <typename T, int D, int Q>
-void launch_mode_solve_t(st_handle* h, Level& lv, bool adj, const T* in, T* out, int ns, T scale) {
-  auto tc = to_coef<T, Q>(h->tm);
+void launch_line_solve_t(st_handle* h, Level& lv, bool adj, T* data, int ns, T scale) {
   Tables<T>& tb = tables<T>(lv);
+  const int64_t nmodes = lv.Nx / lv.n;
+  dim3 grid(blocks_for(nmodes, 128), 1);
+  for (int c = 0; c < ns; c += 65535) {
+    grid.y = std::min(65535, ns - c);
+    stmg::k_line_solve<T, Q><<<grid, 128, 0, h->stream>>>(data + (int64_t)c * Q * lv.Nx, lv.n, nmodes, grid.y,
+                                                          tb.fac[adj ? 1 : 0], tb.ecoef[adj ? 1 : 0], scale);
+  }
+}
+
+template <typename T, int D, int Q>
+void launch_rhs_t(st_handle* h, const Level& lv, bool adj, const T* f, const T* u, const T* u0, T* g, int s0,
+                  int ns) {
+  auto tc = to_coef<T, Q>(h->tm);
+  if (D == 2) {
+    dim3 block(stmg::kResTX, stmg::kResTY);
+    dim3 grid((lv.n + stmg::kResTX - 1) / stmg::kResTX, (lv.n + stmg::kResTY - 1) / stmg::kResTY, 1);
+    for (int c = 0; c < ns; c += 65535) {
+      grid.z = std::min(65535, ns - c);
+      if (adj)
+        stmg::k_rhs2d<T, Q, true><<<grid, block, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
+      else
+        stmg::k_rhs2d<T, Q, false><<<grid, block, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
+    }
+    return;
+  }
   dim3 grid(blocks_for(lv.Nx), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
-    const int64_t off = (int64_t)c * Q * lv.Nx;
     if (adj)
-      stmg::k_mode_solve<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(in + off, out + off, lv.n, grid.y, tb.mval,
-                                                                          tb.kval, (T)lv.tau, scale, tc);
+      stmg::k_rhs<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
     else
-      stmg::k_mode_solve<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(in + off, out + off, lv.n, grid.y,
-                                                                           tb.mval, tb.kval, (T)lv.tau, scale, tc);
+      stmg::k_rhs<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
   }
 }
 
@@ -397,12 +511,21 @@ void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T
 }
 
 template <typename T>
-void mode_solve(st_handle* h, Level& lv, bool adj, const T* in, T* out, int ns, T scale) {
+void line_solve(st_handle* h, Level& lv, bool adj, T* data, int ns, T scale) {
   const double nodes = (double)ns * lv.Nx;
   const double Q = h->q;
-  Prof pr(h, ST_K_MODESOLVE, sizeof(T) * 2.0 * nodes * Q,
-          nodes * (2.0 * Q * Q * Q / 3.0 + 2.0 * Q * Q + 3.0 * Q + 3.0 * h->d));
-  STMG_DISPATCH(launch_mode_solve_t, h, lv, adj, in, out, ns, scale);
+  // per node: forward Q^2 FMA, backward 2 Q^2 FMA; bytes: read + write (one pass each)
+  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * 2.0 * nodes * Q, nodes * 6.0 * Q * Q);
+  STMG_DISPATCH(launch_line_solve_t, h, lv, adj, data, ns, scale);
+}
+
+template <typename T>
+void rhs(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* g) {
+  const double nodes = (double)lv.N * lv.Nx;
+  const int D = h->d, Q = h->q;
+  // per node: trace Q FMA, M_h stencil 3D FMA, output Q FMA; bytes: read f, u (neighbour step), write g
+  Prof pr(h, ST_K_RHS, sizeof(T) * 3.0 * nodes * Q, 2.0 * nodes * (2.0 * Q + 3.0 * D));
+  STMG_DISPATCH(launch_rhs_t, h, lv, adj, f, u, u0, g, 0, lv.N);
 }
 
 template <typename T>
@@ -457,11 +580,10 @@ void dst_set_smem_limits(st_handle* h, int maxNf) {
                                 (int)dst_cols_smem<T, 16>(maxNf)), "cudaFuncSetAttribute");
 }
 
-// DST-I along every axis of `ns` time steps of data (in place); the last axis
-// is scaled by scale_last.
+// DST-I along spatial axes 0..naxes-1 of `ns` time steps of data (in place).
 template <typename T>
-void dst_all_axes(st_handle* h, Level& lv, T* data, int ns, T scale_last) {
-  const int n = lv.n, Nf = n + 1, D = h->d;
+void dst_axes(st_handle* h, Level& lv, T* data, int ns, int naxes) {
+  const int n = lv.n, Nf = n + 1;
   int logh = 0;
   while ((1 << (logh + 1)) <= Nf / 2) ++logh;
   Tables<T>& tb = tables<T>(lv);
@@ -473,8 +595,8 @@ void dst_all_axes(st_handle* h, Level& lv, T* data, int ns, T scale_last) {
   const double hf = Nf / 2.0;
   const double line_flops = 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
   int64_t inner = 1;
-  for (int a = 0; a < D; ++a) {
-    const T scale = (a == D - 1) ? scale_last : T(1);
+  for (int a = 0; a < naxes; ++a) {
+    const T scale = T(1);
     Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines);
     if (a == 0) {
       const unsigned grid = (unsigned)((nlines + kDstRowsPerCta - 1) / kDstRowsPerCta);
@@ -493,17 +615,25 @@ void dst_all_axes(st_handle* h, Level& lv, T* data, int ns, T scale_last) {
   }
 }
 
-// d = D^{-1} r on time steps [s0, s0 + ns) (exact block inverse: DST, per-mode
-// solve, inverse DST).  r and d may be the same buffer.
+// d = D^{-1} r on time steps [s0, s0 + ns) (exact block inverse, Section 3.1):
+// sine transform along the first D-1 axes, block-tridiagonal line solve along
+// the last axis per mode (with the inverse-transform scale (2/Nf)^{D-1}),
+// inverse sine transform.  r and d may be the same buffer.
 template <typename T>
 void block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d, int s0, int ns) {
   const int64_t off = (int64_t)s0 * h->q * lv.Nx;
   const int64_t cnt = (int64_t)ns * h->q * lv.Nx;
   if (r != d) copy<T>(h, d + off, r + off, cnt);
-  dst_all_axes<T>(h, lv, d + off, ns, T(1));
-  const T scale = (T)std::pow(2.0 / (lv.n + 1), h->d);
-  mode_solve<T>(h, lv, adj, d + off, d + off, ns, scale);
-  dst_all_axes<T>(h, lv, d + off, ns, T(1));
+  dst_axes<T>(h, lv, d + off, ns, h->d - 1);
+  const T scale = (T)std::pow(2.0 / (lv.n + 1), h->d - 1);
+  line_solve<T>(h, lv, adj, d + off, ns, scale);
+  dst_axes<T>(h, lv, d + off, ns, h->d - 1);
+}
+
+template <typename T>
+void axpby(st_handle* h, T* y, const T* x, T a, T b, int64_t n) {
+  Prof pr(h, ST_K_VECTOR, 3.0 * sizeof(T) * (double)n, 3.0 * (double)n);
+  stmg::k_axpby<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, b, n);
 }
 
 template <typename T>
@@ -512,12 +642,14 @@ void axpy(st_handle* h, T* y, const T* x, T a, int64_t n) {
   stmg::k_axpy<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, n);
 }
 
-// One damped block-Jacobi step (eq. chap4_smoother).
+// One damped block-Jacobi step (eq. chap4_smoother), u <- u + w D^{-1}(f - L u),
+// evaluated as u <- (1 - w) u + w A^{-1} (f - B u_prev): the block inverse of
+// the block row removes A u_n, so only the rank-one time coupling is applied.
 template <typename T>
 void smooth_step(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
-  residual<T>(h, lv, adj, f, u, u0, work);
+  rhs<T>(h, lv, adj, f, u, u0, work);
   block_solve<T>(h, lv, adj, work, work, 0, lv.N);
-  axpy<T>(h, u, work, (T)h->opt.omega, lv.ndof);
+  axpby<T>(h, u, work, (T)(1.0 - h->opt.omega), (T)h->opt.omega, lv.ndof);
 }
 
 // Exact coarsest solve (Section 2): one step via the block inverse, several by

@@ -443,79 +443,181 @@ __global__ void __launch_bounds__(256) k_dst_cols(T* __restrict__ data, int n, i
 }
 
 // ---------------------------------------------------------------------------
-// Per-mode q x q solve in the sine basis (Section 3.1 with the eigenvalues of
-// Lemma 17): (lamM K + lamK tau Mh) d = r (adjoint: K^T), where
-// lamM = prod_a m_{k_a}, lamK = sum_a kappa_{k_a} prod_{b != a} m_{k_b},
-// m_k = h/3 (2 + cos(k pi / Nf)), kappa_k = 2/h (1 - cos(k pi / Nf)).
-// The result is multiplied by `scale` (the inverse-DST normalisation).
-// Gaussian elimination with partial pivoting in registers.
+// Line solve of the exact block inverse (Section 3.1).  After the sine
+// transform along the first D-1 axes, A = K_tau (x) M_h + M_tau (x) K_h
+// decouples into one block-tridiagonal system per mode i of those axes along
+// the last axis:
+//     A_i = tridiag(E_i, Dg_i, E_i),
+//     Dg_i = lamM (4h/6) K + tau Mh (lamM (2/h) + lamK (4h/6)),
+//     E_i  = lamM ( h/6) K + tau Mh (-lamM / h  + lamK ( h/6)),
+// with lamM, lamK the products / sums of the 1D eigenvalues m_k = h/3 (2 + cos),
+// kappa_k = 2/h (1 - cos) over the transformed axes (lamM = 1, lamK = 0 in 1D),
+// K = K_tau (adjoint: K_tau^T).  Block LU without pivoting, factors precomputed
+// on the host in FP64: W_0 = Dg, L_j = E W_{j-1}^{-1}, W_j = Dg - L_j E.
+//   forward  z_j = g_j - L_j z_{j-1}
+//   backward x_j = W_j^{-1} (z_j - E x_{j+1})
+// One thread per (time step, mode); consecutive threads take consecutive modes
+// so every access along the sweep is coalesced.  Table layout:
+//   fac[((j * 2 + w) * Q*Q + e) * nmodes + mode], w = 0: L_j, w = 1: W_j^{-1}
+//   ecoef[e * nmodes + mode]
+// The result is multiplied by `scale` (inverse sine-transform normalisation).
 // ---------------------------------------------------------------------------
 template <typename T, int Q>
-__device__ __forceinline__ void small_solve(T A[Q][Q], T b[Q]) {
+__global__ void k_line_solve(T* __restrict__ data, int n, int64_t nmodes, int nsteps,
+                             const T* __restrict__ fac, const T* __restrict__ ecoef, T scale) {
+  const int64_t mode = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (mode >= nmodes || s >= nsteps) return;
+  const int64_t Nx = nmodes * n;
+  T* base = data + (int64_t)s * Q * Nx + mode;
+  constexpr int QQ = Q * Q;
+  T z[Q];
+  // forward elimination, z_j stored in place
+  for (int j = 0; j < n; ++j) {
+    T g[Q];
 #pragma unroll
-  for (int c = 0; c < Q; ++c) {
-    int p = c;
-    T best = fabs(A[c][c]);
+    for (int l = 0; l < Q; ++l) g[l] = base[(int64_t)l * Nx + (int64_t)j * nmodes];
+    if (j > 0) {
+      const T* Lj = fac + ((int64_t)(j * 2 + 0) * QQ) * nmodes + mode;
 #pragma unroll
-    for (int r2 = c + 1; r2 < Q; ++r2) {
-      T v = fabs(A[r2][c]);
-      if (v > best) { best = v; p = r2; }
+      for (int k = 0; k < Q; ++k) {
+        T acc = g[k];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) acc -= Lj[(int64_t)(k * Q + l) * nmodes] * z[l];
+        g[k] = acc;
+      }
     }
-    if (p != c) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) { T t = A[c][k]; A[c][k] = A[p][k]; A[p][k] = t; }
-      T t = b[c]; b[c] = b[p]; b[p] = t;
-    }
-    T inv = T(1) / A[c][c];
-#pragma unroll
-    for (int r2 = c + 1; r2 < Q; ++r2) {
-      T fct = A[r2][c] * inv;
-#pragma unroll
-      for (int k = c; k < Q; ++k) A[r2][k] -= fct * A[c][k];
-      b[r2] -= fct * b[c];
+    for (int l = 0; l < Q; ++l) {
+      z[l] = g[l];
+      base[(int64_t)l * Nx + (int64_t)j * nmodes] = g[l];
     }
   }
+  T E[QQ];
 #pragma unroll
-  for (int c = Q - 1; c >= 0; --c) {
-    T acc = b[c];
+  for (int e = 0; e < QQ; ++e) E[e] = ecoef[(int64_t)e * nmodes + mode];
+  // backward substitution; x_{j+1} kept unscaled in registers
+  T xn[Q];
+  for (int j = n - 1; j >= 0; --j) {
+    T t[Q];
 #pragma unroll
-    for (int k = c + 1; k < Q; ++k) acc -= A[c][k] * b[k];
-    b[c] = acc / A[c][c];
+    for (int l = 0; l < Q; ++l) t[l] = (j == n - 1) ? z[l] : base[(int64_t)l * Nx + (int64_t)j * nmodes];
+    if (j < n - 1) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        T acc = t[k];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) acc -= E[k * Q + l] * xn[l];
+        t[k] = acc;
+      }
+    }
+    const T* Wi = fac + ((int64_t)(j * 2 + 1) * QQ) * nmodes + mode;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) acc += Wi[(int64_t)(k * Q + l) * nmodes] * t[l];
+      xn[k] = acc;
+    }
+#pragma unroll
+    for (int l = 0; l < Q; ++l) base[(int64_t)l * Nx + (int64_t)j * nmodes] = scale * xn[l];
   }
 }
 
+// ---------------------------------------------------------------------------
+// Right-hand side of one damped block-Jacobi step written without A u:
+//     u + w D^{-1} (f - A u_n - B u_{n-1}) = (1 - w) u + w A^{-1} (f_n - B u_{n-1}),
+// so the step needs g = f - B u_prev only (B = -N_tau (x) M_h, rank one in time):
+//   forward  g_{s,k} = f_{s,k} + st[k] M_h (sum_l en[l] u_{s-1,l})   (s = 0: M_h u0)
+//   adjoint  g_{s,k} = f_{s,k} + en[k] M_h (sum_l st[l] u_{s+1,l})
+// One thread per (spatial node, time step).
+// ---------------------------------------------------------------------------
 template <typename T, int D, int Q, bool ADJ>
-__global__ void k_mode_solve(const T* __restrict__ in, T* __restrict__ out, int n, int nsteps,
-                             const T* __restrict__ mval, const T* __restrict__ kval,
-                             T tau, T scale, TimeCoef<T, Q> tc) {
+__global__ void k_rhs(const T* __restrict__ f, const T* __restrict__ u, const T* __restrict__ u0,
+                      T* __restrict__ g, int n, int N, int s0, T h, TimeCoef<T, Q> tc) {
   const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (j >= Nx || s >= nsteps) return;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N) return;
   int ix, iy, iz;
   node_coords(j, n, D, ix, iy, iz);
-  T lamM, lamK;
-  if (D == 1) {
-    lamM = mval[ix];
-    lamK = kval[ix];
-  } else if (D == 2) {
-    lamM = mval[ix] * mval[iy];
-    lamK = kval[ix] * mval[iy] + mval[ix] * kval[iy];
-  } else {
-    lamM = mval[ix] * mval[iy] * mval[iz];
-    lamK = kval[ix] * mval[iy] * mval[iz] + mval[ix] * kval[iy] * mval[iz] + mval[ix] * mval[iy] * kval[iz];
+  Stencil<T, D> S(h);
+  T mt = T(0);
+  const T* nb = nullptr;
+  if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
+  if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
+  if (nb != nullptr) {
+    mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) {
+      T t = T(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) t += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + q];
+      return t;
+    });
+  } else if (!ADJ && s == 0 && u0 != nullptr) {
+    mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) { return u0[q]; });
   }
-  T A[Q][Q], b[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-#pragma unroll
-    for (int l = 0; l < Q; ++l) A[k][l] = lamM * (ADJ ? tc.K[l * Q + k] : tc.K[k * Q + l]);
-    A[k][k] += lamK * tau * tc.Mh[k];
-    b[k] = in[((int64_t)s * Q + k) * Nx + j];
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    g[idx] = f[idx] + (ADJ ? tc.en[k] : tc.st[k]) * mt;
   }
-  small_solve<T, Q>(A, b);
+}
+
+// 2D smoother right-hand side with a shared-memory tile (same result as
+// k_rhs<T, 2, Q, ADJ>): the coupling trace of the neighbouring step is formed
+// once per staged node, M_1 along x once per staged row, M_1 along y per node.
+template <typename T, int Q, bool ADJ>
+__global__ void __launch_bounds__(kResTX * kResTY) k_rhs2d(const T* __restrict__ f, const T* __restrict__ u,
+                                                           const T* __restrict__ u0, T* __restrict__ g, int n,
+                                                           int N, int s0, T h, TimeCoef<T, Q> tc) {
+  constexpr int HX = kResTX + 2, HY = kResTY + 2;
+  __shared__ T st[HY][HX];        // trace of the neighbouring step on tile + halo
+  __shared__ T sa[HY][kResTX];    // M_1 along x
+  const int s = s0 + blockIdx.z;
+  const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
+  const int tid = threadIdx.y * kResTX + threadIdx.x;
+  const int64_t Nx = (int64_t)n * n;
+  const T* nb = nullptr;
+  if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
+  if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
+  const bool use_u0 = !ADJ && s == 0 && u0 != nullptr;
+  const bool any = nb != nullptr || use_u0;
+  if (any) {
+    for (int i = tid; i < HX * HY; i += kResTX * kResTY) {
+      const int hy = i / HX, hx = i - hy * HX;
+      const int x = x0 + hx - 1, y = y0 + hy - 1;
+      T t = T(0);
+      if (x >= 0 && x < n && y >= 0 && y < n) {
+        const int64_t j = (int64_t)y * n + x;
+        if (nb != nullptr) {
 #pragma unroll
-  for (int k = 0; k < Q; ++k) out[((int64_t)s * Q + k) * Nx + j] = scale * b[k];
+          for (int l = 0; l < Q; ++l) t += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + j];
+        } else {
+          t = u0[j];
+        }
+      }
+      st[hy][hx] = t;
+    }
+  }
+  __syncthreads();
+  const T m0 = h / T(6), m1 = T(4) * h / T(6);
+  if (any) {
+    for (int i = tid; i < HY * kResTX; i += kResTX * kResTY) {
+      const int hy = i / kResTX, tx = i - hy * kResTX;
+      sa[hy][tx] = m0 * (st[hy][tx] + st[hy][tx + 2]) + m1 * st[hy][tx + 1];
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= n || y >= n || s >= N) return;
+  const T mt = any ? m0 * (sa[ty][tx] + sa[ty + 2][tx]) + m1 * sa[ty + 1][tx] : T(0);
+  const int64_t j = (int64_t)y * n + x;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    g[idx] = f[idx] + (ADJ ? tc.en[k] : tc.st[k]) * mt;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -580,6 +682,22 @@ __global__ void k_restrict(const T* __restrict__ r, T* __restrict__ fc, int nf, 
 // Prolongation and correction u_f += P e_c, P = R^T: fine step 2m+sl, dof l gets
 // sum_k R_sl[k,l] (Px e)[m, k, I]; Px = Rx^T is linear interpolation (fine node
 // 2J+1 <- coarse J with weight 1, fine node 2J <- coarse J-1, J with weight 1/2).
+// Per axis a fine index i maps to at most two coarse indices (c0, w0), (c1, w1);
+// a missing neighbour gets weight 0 and a clamped index.
+__device__ __forceinline__ void interp_pair(int i, int nc, int& c0, int& c1, float& w0, float& w1) {
+  if (i & 1) {
+    c0 = c1 = (i - 1) >> 1;
+    w0 = 1.0f;
+    w1 = 0.0f;
+  } else {
+    const int jl = (i >> 1) - 1, jr = i >> 1;
+    c0 = jl >= 0 ? jl : 0;
+    w0 = jl >= 0 ? 0.5f : 0.0f;
+    c1 = jr < nc ? jr : nc - 1;
+    w1 = jr < nc ? 0.5f : 0.0f;
+  }
+}
+
 template <typename T, int D, int Q, bool FULL>
 __global__ void k_prolong(const T* __restrict__ ec, T* __restrict__ uf, int nf, int nc, int Nf_steps,
                           TimeCoef<T, Q> tc) {
@@ -591,6 +709,13 @@ __global__ void k_prolong(const T* __restrict__ ec, T* __restrict__ uf, int nf, 
   const int m = s >> 1, sl = s & 1;
   int ix, iy, iz;
   node_coords(I, nf, D, ix, iy, iz);
+  int cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0, cz0 = 0, cz1 = 0;
+  float wx0 = 1.f, wx1 = 0.f, wy0 = 1.f, wy1 = 0.f, wz0 = 1.f, wz1 = 0.f;
+  if (FULL) {
+    interp_pair(ix, nc, cx0, cx1, wx0, wx1);
+    if (D >= 2) interp_pair(iy, nc, cy0, cy1, wy0, wy1);
+    if (D >= 3) interp_pair(iz, nc, cz0, cz1, wz0, wz1);
+  }
   T e[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
@@ -598,38 +723,22 @@ __global__ void k_prolong(const T* __restrict__ ec, T* __restrict__ uf, int nf, 
     T acc;
     if (!FULL) {
       acc = ek[I];
+    } else if (D == 1) {
+      acc = T(wx0) * ek[cx0] + T(wx1) * ek[cx1];
+    } else if (D == 2) {
+      const T r0 = T(wx0) * ek[(int64_t)cy0 * nc + cx0] + T(wx1) * ek[(int64_t)cy0 * nc + cx1];
+      const T r1 = T(wx0) * ek[(int64_t)cy1 * nc + cx0] + T(wx1) * ek[(int64_t)cy1 * nc + cx1];
+      acc = T(wy0) * r0 + T(wy1) * r1;
     } else {
-      // per axis: list of (coarse index, weight)
-      int ci[3][2];
-      T cw[3][2];
-      int cnt[3];
-      int coord[3] = {ix, iy, iz};
+      T pz[2];
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        int i = coord[a];
-        if (i & 1) { ci[a][0] = (i - 1) >> 1; cw[a][0] = T(1); cnt[a] = 1; }
-        else {
-          int c = 0;
-          int jl = (i >> 1) - 1, jr = i >> 1;
-          if (jl >= 0) { ci[a][c] = jl; cw[a][c] = T(0.5); ++c; }
-          if (jr < nc) { ci[a][c] = jr; cw[a][c] = T(0.5); ++c; }
-          cnt[a] = c;
-        }
+      for (int a = 0; a < 2; ++a) {
+        const int64_t zoff = (int64_t)(a ? cz1 : cz0) * nc;
+        const T r0 = T(wx0) * ek[(zoff + cy0) * nc + cx0] + T(wx1) * ek[(zoff + cy0) * nc + cx1];
+        const T r1 = T(wx0) * ek[(zoff + cy1) * nc + cx0] + T(wx1) * ek[(zoff + cy1) * nc + cx1];
+        pz[a] = T(wy0) * r0 + T(wy1) * r1;
       }
-      acc = T(0);
-      if (D == 1) {
-        for (int p = 0; p < cnt[0]; ++p) acc += cw[0][p] * ek[ci[0][p]];
-      } else if (D == 2) {
-        for (int py = 0; py < cnt[1]; ++py)
-          for (int px = 0; px < cnt[0]; ++px)
-            acc += cw[1][py] * cw[0][px] * ek[(int64_t)ci[1][py] * nc + ci[0][px]];
-      } else {
-        for (int pz = 0; pz < cnt[2]; ++pz)
-          for (int py = 0; py < cnt[1]; ++py)
-            for (int px = 0; px < cnt[0]; ++px)
-              acc += cw[2][pz] * cw[1][py] * cw[0][px] *
-                     ek[((int64_t)ci[2][pz] * nc + ci[1][py]) * nc + ci[0][px]];
-      }
+      acc = T(wz0) * pz[0] + T(wz1) * pz[1];
     }
     e[k] = acc;
   }
@@ -668,6 +777,12 @@ template <typename T>
 __global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, T a, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * x[i];
+}
+
+template <typename T>
+__global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, T a, T b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * y[i] + b * x[i];
 }
 
 template <typename T>

@@ -31,7 +31,7 @@ EXPORTS = [
 
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
 
-KERNEL_CLASSES = ["residual", "dst", "mode_solve", "restrict", "prolong", "norm", "vector", "smooth"]
+KERNEL_CLASSES = ["residual", "dst", "line_solve", "restrict", "prolong", "norm", "vector", "rhs"]
 
 
 class StMesh(ctypes.Structure):
