@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--inner-cycles", type=int, default=2)
+    ap.add_argument("--inner-cycles", type=int, default=4)
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="run one precision only (profiling); the line's value is that precision's")
     return ap.parse_args()
@@ -272,24 +272,16 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     import torch
-    import torch.distributed as dist
+    from paper_1411_0519_gb300 import dist as pd
     from paper_1411_0519_gb300 import stmg, workloads
 
-    rank, world, local = dist_env()
+    rank, world, local = pd.env()
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    pd.init("nccl", torch.device("cuda", local))
+    barrier = pd.barrier
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return pd.max_over_ranks(x, device="cuda")
 
     w = workloads.WORKLOADS[args.workload]
     d, n, p, N, T, rtol = w["d"], w["n"], w["p_t"], w["N"], w["T"], w["rtol"]
@@ -309,7 +301,7 @@ def main():
     ck = clocks.stop()
     ms64 = max_over_ranks(ms64)
     per_step = ms64 / args.steps
-    value = world * s64.ndof / (per_step / 1e3)
+    value = pd.job_throughput(world, s64.ndof, per_step / 1e3)
     launches = sum(v["launches"] for k, v in prof64.items() if not k.startswith("_"))
 
     # ---------------------------------------------------------------- end to end (host buffers)
@@ -357,8 +349,7 @@ def main():
         smx.close()
 
     if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
+        pd.finalize()
         return 0
 
     cpu = None
@@ -384,8 +375,7 @@ def main():
         "clocks": ck,
     }
     print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    pd.finalize()
     return 0
 
 
