@@ -157,30 +157,54 @@ def time_solves(torch, solver, f, u0, u, steps, warmup, barrier):
     return e0.elapsed_time(e1), iters, relres, prof
 
 
-def roofline(prof, fp32, pk):
-    """Dominant kernel class in the timed region and its achieved fraction."""
+def traffic_table():
+    """DRAM bytes per row of the finest-level sine-transform kernels, from the
+    ncu captures summarised in profiles/ (measured on heat2d_255_n256 and scaled
+    by rows; the captures name the kernel they were taken on)."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_row.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def roofline(solver, prof, fp32, pk, w):
+    """Dominant kernel class of the timed region, evaluated on the finest level
+    (one launch = one pass over the finest level)."""
     classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["ms"] > 0}
     dom = max(classes, key=lambda k: classes[k]["ms"])
-    v = classes[dom]
+    total_ms = sum(c["ms"] for c in classes.values())
+    L = solver.num_levels - 1
+    v = solver.profile_level(dom, L)
+    if v["launches"] == 0 or v["ms"] <= 0:
+        v = classes[dom]
     sec = v["ms"] / 1e3
     gbs = v["bytes"] / sec / 1e9
     tfl = v["flops"] / sec / 1e12
     alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     f_hbm = gbs / pk["hbm_gbs"]
     f_alu = tfl / alu_peak
-    total_ms = sum(c["ms"] for c in classes.values())
-    share = v["ms"] / total_ms
     if f_alu >= f_hbm:
         rf = {"bound": "alu", "achieved": round(tfl, 4), "peak": alu_peak, "unit": "TFLOP/s",
               "frac": round(f_alu, 4), "peak_src": "FP32 lanes x clock" if fp32 else
-              "published FP64 rate (probe: 1.196 TFLOP/s)"}
+              "published FP64 rate 1.25 TFLOP/s (FMA probe on this part: 1.196)"}
     else:
         rf = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
               "frac": round(f_hbm, 4), "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)"}
-    rf.update({"kernel": dom, "launches": v["launches"], "avg_launch_ms": round(v["ms"] / max(1, v["launches"]), 4),
-               "share": round(share, 3), "traffic": None,
-               "alg_bytes_per_launch": v["bytes"] / max(1, v["launches"]),
-               "alg_flops_per_launch": v["flops"] / max(1, v["launches"])})
+    launches = max(1, v["launches"])
+    rows = w["N"] * (w["p_t"] + 1) * w["n"] ** (w["d"] - 1)
+    name = None
+    traffic = None
+    if dom == "dst" and w["d"] == 2 and w["n"] + 1 == 256:
+        name = "k_dst_rows_reg<%s,4,3>" % ("float" if fp32 else "double")
+        t = traffic_table().get(name)
+        if t is not None:
+            traffic = t["bytes_per_row"] * rows
+    rf.update({"kernel": name or dom, "level": "finest", "launches": v["launches"],
+               "avg_launch_ms": round(v["ms"] / launches, 4), "share_of_class_total": round(
+                   classes[dom]["ms"] / total_ms, 3),
+               "alg_bytes_per_launch": v["bytes"] / launches, "alg_flops_per_launch": v["flops"] / launches,
+               "traffic": traffic})
     return rf
 
 
@@ -259,7 +283,8 @@ def run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_ov
                 "dtype": "f32 V-cycle in f64 refinement", "data": "synthetic",
                 "config": {"workload": args.workload, "d": d, "n": n, "p_t": p, "N": N, "T": T, "rtol": rtol,
                            "precision": "mixed", "inner_cycles": args.inner_cycles},
-                "iters": itm[-1], "relres": rrm, "roofline": roofline(profm, True, pk), "kernels": breakdown(profm),
+                "iters": itm[-1], "relres": rrm, "roofline": roofline(smx, profm, True, pk, w),
+                "kernels": breakdown(profm),
                 "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_")),
                 "clocks": ck}
         print(json.dumps(line), flush=True)
@@ -331,7 +356,7 @@ def main():
                "h2d_bytes_per_step": fh.numel() * 8 + u0h.numel() * 8, "d2h_bytes_per_step": uh.numel() * 8,
                "ms_per_step": 1e3 * dt / args.steps}
         del fh, u0h, uh, fd, u0d, ud
-    rf64 = roofline(prof64, False, pk)
+    rf64 = roofline(s64, prof64, False, pk, w)
     s64.close()
     torch.cuda.empty_cache()
 
@@ -344,7 +369,7 @@ def main():
         mixed = {"value": world * smx.ndof / (msm / args.steps / 1e3), "unit": "DoF/s",
                  "ms_per_step": msm / args.steps, "iters": itm[-1], "relres": rrm,
                  "inner_cycles": args.inner_cycles, "dtype": "f32 V-cycle in f64 refinement",
-                 "roofline": roofline(profm, True, pk), "kernels": breakdown(profm),
+                 "roofline": roofline(smx, profm, True, pk, w), "kernels": breakdown(profm),
                  "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_"))}
         smx.close()
 

@@ -182,6 +182,12 @@ int st_profile_start(st_handle* h, int max_launches);
  * Launches beyond max_launches are counted but not timed (*dropped). */
 int st_profile_stop(st_handle* h, int* launches, double* ms, double* bytes, double* flops, int* dropped);
 
+/* After st_profile_stop: the same four totals for kernel class cls restricted
+ * to the launches that worked on level L (0 = coarsest).  Classes without a
+ * level (norms, vector operations) report zeros.  Errors: ST_EINVAL (bad
+ * class or level, or no timed region recorded yet). */
+int st_profile_level(const st_handle* h, int cls, int L, int* launches, double* ms, double* bytes, double* flops);
+
 /* ---- allocation-free norm ----
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory -- an application whose allocator owns the GPU's

@@ -182,6 +182,9 @@ struct st_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev;          // pool, 2 per timed launch
   std::vector<int> ev_class;            // class of each recorded pair
+  std::vector<int> ev_level;            // level of each recorded pair (-1: not level-specific)
+  // per (class, level) totals of the last timed region: launches, ms, bytes, flops
+  std::vector<double> lv_stats;
   int prof_launches[ST_K_COUNT] = {0};
   double prof_bytes[ST_K_COUNT] = {0};   // algorithmic HBM bytes of the counted launches
   double prof_flops[ST_K_COUNT] = {0};   // algorithmic floating-point operations
@@ -214,21 +217,30 @@ void fail(st_handle* h, int code, const std::string& msg) {
 struct Prof {
   st_handle* h;
   int slot = -1;
-  Prof(st_handle* hh, int cls, double bytes = 0.0, double flops = 0.0, int kernels = 1) : h(hh) {
+  Prof(st_handle* hh, int cls, double bytes = 0.0, double flops = 0.0, int kernels = 1, int level = -1) : h(hh) {
     if (!h->prof) return;
     h->prof_launches[cls] += kernels;
     h->prof_bytes[cls] += bytes;
     h->prof_flops[cls] += flops;
+    if (level >= 0) {
+      const size_t b = ((size_t)cls * h->levels.size() + level) * 4;
+      h->lv_stats[b + 0] += kernels;
+      h->lv_stats[b + 2] += bytes;
+      h->lv_stats[b + 3] += flops;
+    }
     const int pair = (int)h->ev_class.size();
     if (2 * pair + 1 >= (int)h->ev.size()) { h->prof_dropped++; return; }
     slot = pair;
     h->ev_class.push_back(cls);
+    h->ev_level.push_back(level);
     cudaEventRecord(h->ev[2 * pair], h->stream);
   }
   ~Prof() {
     if (slot >= 0) cudaEventRecord(h->ev[2 * slot + 1], h->stream);
   }
 };
+
+int level_of(st_handle* h, const Level& lv) { return (int)(&lv - h->levels.data()); }
 
 template <typename T>
 T* dalloc(st_handle* h, size_t count) {
@@ -506,7 +518,8 @@ void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T
   // per node: Q fields x (9D-3) FMA for M_h, K_h (tensor-product passes), trace Q + 3D,
   // time mixing Q^2 + 2Q; bytes: read u, f, write r (+ u0)
   const double fma = Q * (9.0 * D - 3.0) + Q + 3.0 * D + Q * Q + 2.0 * Q;
-  Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)), 2.0 * fma * nodes);
+  Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)), 2.0 * fma * nodes, 1,
+          level_of(h, lv));
   STMG_DISPATCH(launch_residual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
@@ -515,7 +528,7 @@ void line_solve(st_handle* h, Level& lv, bool adj, T* data, int ns, T scale) {
   const double nodes = (double)ns * lv.Nx;
   const double Q = h->q;
   // per node: forward Q^2 FMA, backward 2 Q^2 FMA; bytes: read + write (one pass each)
-  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * 2.0 * nodes * Q, nodes * 6.0 * Q * Q);
+  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * 2.0 * nodes * Q, nodes * 6.0 * Q * Q, 1, level_of(h, lv));
   STMG_DISPATCH(launch_line_solve_t, h, lv, adj, data, ns, scale);
 }
 
@@ -524,7 +537,7 @@ void rhs(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0,
   const double nodes = (double)lv.N * lv.Nx;
   const int D = h->d, Q = h->q;
   // per node: trace Q FMA, M_h stencil 3D FMA, output Q FMA; bytes: read f, u (neighbour step), write g
-  Prof pr(h, ST_K_RHS, sizeof(T) * 3.0 * nodes * Q, 2.0 * nodes * (2.0 * Q + 3.0 * D));
+  Prof pr(h, ST_K_RHS, sizeof(T) * 3.0 * nodes * Q, 2.0 * nodes * (2.0 * Q + 3.0 * D), 1, level_of(h, lv));
   STMG_DISPATCH(launch_rhs_t, h, lv, adj, f, u, u0, g, 0, lv.N);
 }
 
@@ -534,7 +547,7 @@ void restrict_to(st_handle* h, int L, const T* r, T* fc) {
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_),
-          2.0 * cn * (2.0 * (fine.coarsen_full ? std::pow(3.0, h->d) : 1.0) + 2.0 * h->q));
+          2.0 * cn * (2.0 * (fine.coarsen_full ? std::pow(3.0, h->d) : 1.0) + 2.0 * h->q), 1, L);
   STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
 }
 
@@ -544,7 +557,7 @@ void prolong_add(st_handle* h, int L, const T* ec, T* uf) {
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_),
-          2.0 * fn_ * ((fine.coarsen_full ? std::pow(2.0, h->d) : 1.0) + h->q));
+          2.0 * fn_ * ((fine.coarsen_full ? std::pow(2.0, h->d) : 1.0) + h->q), 1, L);
   STMG_DISPATCH(launch_prolong_t, h, fine, coarse, ec, uf);
 }
 
@@ -570,14 +583,45 @@ size_t dst_cols_smem(int Nf) {
   return W * sizeof(int64_t) + ((size_t)2 * Nf + (size_t)W * (Nf + 1) + (size_t)kDstWarps * Nf) * sizeof(T);
 }
 
+// Register sine transform (k_dst_rows_reg): rows per CTA = threads / G;
+// 256 threads for FP32, 128 for FP64 (FP64 is bound by the FP64 pipe, so fewer
+// rows per CTA keep the shared-memory footprint down).
+template <typename T>
+int dst_reg_threads() { return sizeof(T) == 8 ? 128 : 256; }
+template <typename T, int LP, int LG>
+size_t dst_reg_smem() {
+  using Lay = stmg::DstRegLayout<LP, LG>;
+  const int rows = dst_reg_threads<T>() / Lay::G;
+  return ((size_t)Lay::TAB + (size_t)rows * Lay::RS) * sizeof(T);
+}
+
 template <typename T>
 void dst_set_smem_limits(st_handle* h, int maxNf) {
+  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_reg_smem<T, 3, 2>()), "cudaFuncSetAttribute");
+  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_reg_smem<T, 3, 3>()), "cudaFuncSetAttribute");
+  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_reg_smem<T, 4, 3>()), "cudaFuncSetAttribute");
+  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dst_reg_smem<T, 4, 4>()), "cudaFuncSetAttribute");
   check(h, cudaFuncSetAttribute(stmg::k_dst_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)dst_rows_smem<T>(maxNf)), "cudaFuncSetAttribute");
   check(h, cudaFuncSetAttribute(stmg::k_dst_cols<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)dst_cols_smem<T, 32>(maxNf)), "cudaFuncSetAttribute");
   check(h, cudaFuncSetAttribute(stmg::k_dst_cols<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)dst_cols_smem<T, 16>(maxNf)), "cudaFuncSetAttribute");
+}
+
+// Algorithmic flops of one sine transform of a line of n = Nf - 1 values:
+// pre-processing 5 Nf, complex FFT of Nf/2 points 5 (Nf/2) log2(Nf/2),
+// even/odd split 12 (Nf/2), prefix scan Nf, scaling n.
+double dst_line_flops(int n) {
+  const int Nf = n + 1;
+  int logh = 0;
+  while ((1 << (logh + 1)) <= Nf / 2) ++logh;
+  const double hf = Nf / 2.0;
+  return 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
 }
 
 // DST-I along spatial axes 0..naxes-1 of `ns` time steps of data (in place).
@@ -590,15 +634,31 @@ void dst_axes(st_handle* h, Level& lv, T* data, int ns, int naxes) {
   stmg::DstTables<T> dt{tb.sinp, tb.twc, tb.tws};
   const int64_t slabs = (int64_t)ns * h->q;
   const int64_t nlines = slabs * lv.Nx / n;
-  // per line: pre-processing 5 Nf, complex FFT of Nf/2 points 5 (Nf/2) log2(Nf/2),
-  // even/odd split 12 (Nf/2), prefix scan Nf, scaling n
-  const double hf = Nf / 2.0;
-  const double line_flops = 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
+  const double line_flops = dst_line_flops(n);
   int64_t inner = 1;
   for (int a = 0; a < naxes; ++a) {
     const T scale = T(1);
-    Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines);
-    if (a == 0) {
+    Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines, 1, level_of(h, lv));
+    if (a == 0 && Nf >= 64 && Nf <= 512) {
+      const int thr = dst_reg_threads<T>();
+      const int G = (Nf == 64) ? 4 : (Nf == 512) ? 16 : 8;
+      const int rows = thr / G;
+      const unsigned grid = (unsigned)((nlines + rows - 1) / rows);
+      switch (Nf) {
+        case 64:
+          stmg::k_dst_rows_reg<T, 3, 2><<<grid, thr, dst_reg_smem<T, 3, 2>(), h->stream>>>(data, n, nlines, scale, dt);
+          break;
+        case 128:
+          stmg::k_dst_rows_reg<T, 3, 3><<<grid, thr, dst_reg_smem<T, 3, 3>(), h->stream>>>(data, n, nlines, scale, dt);
+          break;
+        case 256:
+          stmg::k_dst_rows_reg<T, 4, 3><<<grid, thr, dst_reg_smem<T, 4, 3>(), h->stream>>>(data, n, nlines, scale, dt);
+          break;
+        default:
+          stmg::k_dst_rows_reg<T, 4, 4><<<grid, thr, dst_reg_smem<T, 4, 4>(), h->stream>>>(data, n, nlines, scale, dt);
+          break;
+      }
+    } else if (a == 0) {
       const unsigned grid = (unsigned)((nlines + kDstRowsPerCta - 1) / kDstRowsPerCta);
       stmg::k_dst_rows<T><<<grid, kDstWarps * 32, dst_rows_smem<T>(Nf), h->stream>>>(data, n, logh, nlines,
                                                                                      kDstRowsPerCta, scale, dt);
@@ -1060,6 +1120,8 @@ int st_profile_start(st_handle* h, int max_launches) {
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
     h->ev_class.clear();
+    h->ev_level.clear();
+    h->lv_stats.assign((size_t)ST_K_COUNT * h->levels.size() * 4, 0.0);
     h->ev.resize(2 * (size_t)max_launches);
     for (auto& e : h->ev) check(h, cudaEventCreate(&e), "cudaEventCreate");
     for (int c = 0; c < ST_K_COUNT; ++c) {
@@ -1083,6 +1145,8 @@ int st_profile_stop(st_handle* h, int* launches, double* ms, double* bytes, doub
       float t = 0.f;
       check(h, cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]), "cudaEventElapsedTime");
       tot[h->ev_class[i]] += t;
+      if (h->ev_level[i] >= 0)
+        h->lv_stats[((size_t)h->ev_class[i] * h->levels.size() + h->ev_level[i]) * 4 + 1] += t;
     }
     for (int c = 0; c < ST_K_COUNT; ++c) {
       if (launches) launches[c] = h->prof_launches[c];
@@ -1094,8 +1158,20 @@ int st_profile_stop(st_handle* h, int* launches, double* ms, double* bytes, doub
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
     h->ev_class.clear();
+    h->ev_level.clear();
     return ST_OK;
   });
+}
+
+int st_profile_level(const st_handle* h, int cls, int L, int* launches, double* ms, double* bytes, double* flops) {
+  if (!h || cls < 0 || cls >= ST_K_COUNT || L < 0 || L >= (int)h->levels.size() || h->lv_stats.empty())
+    return ST_EINVAL;
+  const size_t b = ((size_t)cls * h->levels.size() + L) * 4;
+  if (launches) *launches = (int)h->lv_stats[b + 0];
+  if (ms) *ms = h->lv_stats[b + 1];
+  if (bytes) *bytes = h->lv_stats[b + 2];
+  if (flops) *flops = h->lv_stats[b + 3];
+  return ST_OK;
 }
 
 int st_norm2(st_handle* h, const double* x, size_t n, double* out) {

@@ -403,6 +403,253 @@ __global__ void __launch_bounds__(256) k_dst_rows(T* __restrict__ data, int n, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register version of the x-axis sine transform for Nf = 2^(LP+LG+1) >= 64.
+// Same algorithm as dst1_warp; the complex FFT of length H = Nf/2 = P G runs as
+// a four-step FFT: a group of G threads owns one row, thread g holds the P
+// points z_{g + G p}, does a P-point DFT in registers, multiplies by
+// W_H^{g k1}, exchanges through shared memory, and does the G-point DFTs in
+// registers:  Z_{k1 + P k2} = sum_g W_G^{g k2} W_H^{g k1} sum_p z_{g+Gp} W_P^{p k1}.
+// Radix-2 stages are unrolled at compile time, so the multiplications by 1 and
+// -i are skipped.  Rows are loaded and stored with whole warps (coalesced).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+__host__ __device__ constexpr int brevc(int v, int bits) {
+  return bits == 0 ? 0 : (((v & 1) << (bits - 1)) | brevc(v >> 1, bits - 1));
+}
+
+// In-place radix-2 decimation-in-frequency DFT of P points in registers,
+// X_k = sum_m x_m e^{-2 pi i m k / P}; X_k ends at position brevc(k, log2 P).
+// wc/ws: cos/sin(2 pi j / Nf), j < Nf, with Nf = 2^lnf >= 2 P.
+template <typename T, int P>
+__device__ __forceinline__ void fft_dif_reg(T (&re)[P], T (&im)[P], const T* wc, const T* ws, int lnf) {
+  constexpr int LP = ilog2c(P);
+#pragma unroll
+  for (int st = 0; st < LP; ++st) {
+    const int len = P >> st;
+    const int hl = len >> 1;
+    const int lsh = lnf - (LP - st);         // table index = j * (Nf / len)
+#pragma unroll
+    for (int b0 = 0; b0 < P; b0 += len) {
+#pragma unroll
+      for (int j = 0; j < hl; ++j) {
+        const int i0 = b0 + j, i1 = i0 + hl;
+        const T ar = re[i0], ai = im[i0], br = re[i1], bi = im[i1];
+        re[i0] = ar + br;
+        im[i0] = ai + bi;
+        const T dr = ar - br, di = ai - bi;
+        if (j == 0) {
+          re[i1] = dr;
+          im[i1] = di;
+        } else if (4 * j == len) {             // times e^{-i pi / 2} = -i
+          re[i1] = di;
+          im[i1] = -dr;
+        } else {
+          const int idx = j << lsh;
+          const T c = wc[idx], sn = ws[idx];   // e^{-2 pi i j / len} = c - i sn
+          re[i1] = dr * c + di * sn;
+          im[i1] = di * c - dr * sn;
+        }
+      }
+    }
+  }
+}
+
+// Shared-memory layout of k_dst_rows_reg (in elements of T), chosen so that
+// every access of a warp touches distinct banks:
+//  * per row one planar complex buffer (re part at 0, im part at BS): it holds
+//    the input de-interleaved (x_{2k} in re[k], x_{2k+1} in im[k]), then the
+//    stage-1 -> stage-2 exchange at k1 (G+1) + g, then Z_k at k + (k >> LP),
+//    then the output (X_{2k} in re[k], X_{2k+1} in im[k]);
+//  * BS = 16 mod 32 so re[k] and im[k] are half a bank cycle apart, and the
+//    row stride RS = G mod 32 so the rows of one warp fall on disjoint banks;
+//  * per CTA: sin(j pi / Nf) de-interleaved, the step-3 twiddles W_H^{g k1} at
+//    k1 G + g, the split twiddles W_Nf^{g P + c} at c G + g, and
+//    cos / sin(2 pi j / Nf) for j < Nf/2 (broadcast reads inside the register FFTs).
+template <int LP, int LG>
+struct DstRegLayout {
+  static constexpr int P = 1 << LP, G = 1 << LG, H = P * G, NF = 2 * H;
+  static constexpr int NEED = (H + H / P) > (P * (G + 1)) ? (H + H / P) : (P * (G + 1));
+  static constexpr int BS = ((NEED + 31) / 32) * 32 + 16;
+  static constexpr int RS = ((2 * BS + 31) / 32) * 32 + G;
+  static constexpr int TAB = 2 * H + 4 * H + NF;   // sin e/o, two twiddle tables (re, im), cos/sin half
+};
+
+// Per-CTA tables of the register sine transform (see DstRegLayout).
+template <typename T, int LP, int LG>
+__device__ __forceinline__ void dst_reg_stage_tables(T* sm, DstTables<T> tb) {
+  using Lay = DstRegLayout<LP, LG>;
+  constexpr int P = Lay::P, G = Lay::G, H = Lay::H, NF = Lay::NF;
+  T* se = sm;
+  T* so = se + H;
+  T* t1r = so + H;
+  T* t1i = t1r + H;
+  T* t3r = t1i + H;
+  T* t3i = t3r + H;
+  T* wc = t3i + H;
+  T* ws = wc + NF / 2;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    se[i] = tb.sinp[2 * i];
+    so[i] = tb.sinp[2 * i + 1];
+    const int k1 = i / G, gg = i - k1 * G;                 // t1 entry (k1, g)
+    const int j1 = (2 * gg * k1) & (NF - 1);               // W_H^{g k1} = e^{-2 pi i (2 g k1) / Nf}
+    t1r[i] = tb.twc[j1];
+    t1i[i] = -tb.tws[j1];
+    const int c = i / G, g3 = i - c * G;                   // t3 entry (c, g): W_Nf^{g P + c}
+    const int j3 = g3 * P + c;
+    t3r[i] = tb.twc[j3];
+    t3i[i] = -tb.tws[j3];
+  }
+  for (int i = threadIdx.x; i < NF / 2; i += blockDim.x) {
+    wc[i] = tb.twc[i];
+    ws[i] = tb.tws[i];
+  }
+}
+
+// Sine transform of one row by the G threads of a group (g = rank in the
+// group).  On entry bre[k] = x_{2k}, bim[k] = x_{2k+1} (x_0 = 0); on exit
+// bre[k] = X_{2k}, bim[k] = X_{2k+1}.  Only __syncwarp is used: a group never
+// spans two warps.
+template <typename T, int LP, int LG>
+__device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) {
+  using Lay = DstRegLayout<LP, LG>;
+  constexpr int P = Lay::P, G = Lay::G, H = Lay::H, NF = Lay::NF, LNF = LP + LG + 1;
+  const T* se = sm;
+  const T* so = se + H;
+  const T* t1r = so + H;
+  const T* t1i = t1r + H;
+  const T* t3r = t1i + H;
+  const T* t3i = t3r + H;
+  const T* wc = t3i + H;
+  const T* ws = wc + NF / 2;
+  T re[P], im[P];
+  // 1. pre-processing fused with the stage-1 gather, z_m = y_{2m} + i y_{2m+1}, m = g + G p
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int m = g + G * p;
+    const T a0 = bre[m], b0 = bre[(H - m) & (H - 1)];      // x_{2m}, x_{Nf - 2m}
+    const T a1 = bim[m], b1 = bim[H - 1 - m];              // x_{2m+1}, x_{Nf - 2m - 1}
+    re[p] = (m == 0) ? T(0) : se[m] * (a0 + b0) + T(0.5) * (a0 - b0);
+    im[p] = so[m] * (a1 + b1) + T(0.5) * (a1 - b1);
+  }
+  __syncwarp();
+  // 2. P-point DFTs over p
+  fft_dif_reg<T, P>(re, im, wc, ws, LNF);
+  // 3. twiddle and exchange at k1 (G + 1) + g
+#pragma unroll
+  for (int pos = 0; pos < P; ++pos) {
+    const int k1 = brevc(pos, LP);
+    const T c = t1r[k1 * G + g], sn = t1i[k1 * G + g];     // W = c + i sn
+    bre[k1 * (G + 1) + g] = re[pos] * c - im[pos] * sn;
+    bim[k1 * (G + 1) + g] = re[pos] * sn + im[pos] * c;
+  }
+  __syncwarp();
+  // 4. G-point DFTs over g for k1 = g + G i (results kept in registers)
+  T zr2[P], zi2[P];
+#pragma unroll
+  for (int i = 0; i < P / G; ++i) {
+    const int k1 = g + G * i;
+    T r2[G], i2[G];
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      r2[gg] = bre[k1 * (G + 1) + gg];
+      i2[gg] = bim[k1 * (G + 1) + gg];
+    }
+    fft_dif_reg<T, G>(r2, i2, wc, ws, LNF);
+#pragma unroll
+    for (int pos = 0; pos < G; ++pos) {
+      zr2[i * G + pos] = r2[pos];
+      zi2[i * G + pos] = i2[pos];
+    }
+  }
+  __syncwarp();
+  // Z_{k1 + P k2} at k + (k >> LP)
+#pragma unroll
+  for (int i = 0; i < P / G; ++i) {
+#pragma unroll
+    for (int pos = 0; pos < G; ++pos) {
+      const int k2 = brevc(pos, LG);
+      const int k = g + G * i + P * k2;
+      bre[k + k2] = zr2[i * G + pos];
+      bim[k + k2] = zi2[i * G + pos];
+    }
+  }
+  __syncwarp();
+  // 5. even/odd split for k = g P + c: R_k (prefix-summed) and I_k
+  T Rk[P], Ik[P];
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    const int k = g * P + c;
+    const int kc = (H - k) & (H - 1);
+    const T zkr = bre[k + (k >> LP)], zki = bim[k + (k >> LP)];
+    const T zcr = bre[kc + (kc >> LP)], zci = -bim[kc + (kc >> LP)];
+    const T er = T(0.5) * (zkr + zcr), ei = T(0.5) * (zki + zci);
+    const T orr = T(0.5) * (zki - zci), oi = T(-0.5) * (zkr - zcr);
+    const T wr = t3r[c * G + g], wi = t3i[c * G + g];     // W_Nf^k = wr + i wi
+    Rk[c] = er + (wr * orr - wi * oi);
+    Ik[c] = -(ei + (wr * oi + wi * orr));
+  }
+  __syncwarp();
+  T loc = T(0);
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    loc += Rk[c];
+    Rk[c] = loc;
+  }
+  T incl = loc;
+#pragma unroll
+  for (int off = 1; off < G; off <<= 1) {
+    const T v = __shfl_up_sync(0xffffffffu, incl, off, G);
+    if (g >= off) incl += v;
+  }
+  const T R0 = __shfl_sync(0xffffffffu, Rk[0], 0, G);      // thread 0's first prefix is R_0
+  const T shift = (incl - loc) - T(0.5) * R0;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    const int k = g * P + c;
+    bre[k] = Ik[c];             // X_{2k}
+    bim[k] = Rk[c] + shift;     // X_{2k+1}
+  }
+}
+
+// x-axis sine transform of nrows contiguous rows: data <- scale * DST(data).
+template <typename T, int LP, int LG>
+__global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int n, int64_t nrows, T scale,
+                                                      DstTables<T> tb) {
+  using Lay = DstRegLayout<LP, LG>;
+  constexpr int BS = Lay::BS, RS = Lay::RS;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* rows = sm + Lay::TAB;
+  const int tid = threadIdx.x;
+  const int rpc = blockDim.x >> LG;
+  dst_reg_stage_tables<T, LP, LG>(sm, tb);
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const int rcount = (int)((nrows - r0) < rpc ? (nrows - r0) : rpc);
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int r = warp; r < rcount; r += nw) {     // coalesced, de-interleaved load
+    const T* src = data + (r0 + r) * n;
+    T* br = rows + r * RS;
+    for (int c = lane; c < n; c += 32) {
+      const int j = c + 1;
+      br[(j & 1) * BS + (j >> 1)] = src[c];
+    }
+    if (lane == 0) br[0] = T(0);
+  }
+  __syncthreads();
+  const int rr = tid >> LG, g = tid & (Lay::G - 1);
+  dst_reg_row<T, LP, LG>(rows + rr * RS, rows + rr * RS + BS, g, sm);   // rows >= rcount are not stored
+  __syncthreads();
+  for (int r = warp; r < rcount; r += nw) {
+    T* dst = data + (r0 + r) * n;
+    const T* br = rows + r * RS;
+    for (int c = lane; c < n; c += 32) {
+      const int j = c + 1;
+      dst[c] = scale * br[(j & 1) * BS + (j >> 1)];
+    }
+  }
+}
+
 // y / z axis: line g = (outer, in), in < inner, starts at outer * inner * n + in
 // and has stride inner.  Each CTA stages W consecutive lines.
 // Shared memory: 2 Nf (tables) + W int64 bases + W (Nf + 1) tile + nwarps Nf.
@@ -798,19 +1045,19 @@ __global__ void k_scale_copy(T* __restrict__ y, const T* __restrict__ x, T a, in
 }
 
 // y32 = (float)(a * x64)
-__global__ void k_cast_down(float* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
+static __global__ void k_cast_down(float* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)(a * x[i]);
 }
 
 // y64 += a * (double)x32
-__global__ void k_axpy_up(double* __restrict__ y, const float* __restrict__ x, double a, int64_t n) {
+static __global__ void k_axpy_up(double* __restrict__ y, const float* __restrict__ x, double a, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * (double)x[i];
 }
 
 // y64 = (double)x32
-__global__ void k_cast_up(double* __restrict__ y, const float* __restrict__ x, int64_t n) {
+static __global__ void k_cast_up(double* __restrict__ y, const float* __restrict__ x, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
@@ -841,7 +1088,7 @@ __global__ void k_sumsq_partial(const T* __restrict__ x, int64_t n, double* __re
   }
 }
 
-__global__ void k_sum_final(const double* __restrict__ partial, int np, double* __restrict__ out) {
+static __global__ void k_sum_final(const double* __restrict__ partial, int np, double* __restrict__ out) {
   __shared__ double red[32];
   double acc = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];

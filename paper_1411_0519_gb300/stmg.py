@@ -26,7 +26,7 @@ EXPORTS = [
     "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
     "st_level_info", "st_residual", "st_vcycle", "st_solve", "st_adjoint_solve", "st_level_residual",
     "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
-    "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop", "st_norm2_noalloc",
+    "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop", "st_profile_level", "st_norm2_noalloc",
 ]
 
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
@@ -87,6 +87,8 @@ def load_library(path=None):
         "st_norm2": (I, [H, P, ctypes.c_size_t, ctypes.POINTER(D)]),
         "st_profile_start": (I, [H, I]),
         "st_norm2_noalloc": (I, [P, ctypes.c_size_t, P, P]),
+        "st_profile_level": (I, [H, I, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D),
+                                 ctypes.POINTER(D)]),
         "st_profile_stop": (I, [H, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(I)]),
     }
@@ -254,6 +256,14 @@ class Solver:
                for i, k in enumerate(KERNEL_CLASSES)}
         out["_dropped"] = dropped.value
         return out
+
+    def profile_level(self, kernel_class, L):
+        """dict(launches, ms, bytes, flops) of one kernel class on level L (after profile_stop)."""
+        i = KERNEL_CLASSES.index(kernel_class)
+        launches, ms, by, fl = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.st_profile_level(self._h, i, L, ctypes.byref(launches), ctypes.byref(ms),
+                                               ctypes.byref(by), ctypes.byref(fl)))
+        return {"launches": launches.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
 
     # ------------------------------------------------------------ step level
     def level_residual(self, L, f, u, adjoint=False, out=None):
