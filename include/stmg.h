@@ -57,6 +57,10 @@ extern "C" {
 
 #define ST_INIT_GIVEN 1  /* st_solve flag: u holds the initial iterate (else u^0 = 0) */
 
+#define ST_SMOOTH_EXACT  0  /* block inverse D^{-1} exact (Section 3.1): sine transforms + line solves */
+#define ST_SMOOTH_VCYCLE 1  /* D~^{-1}: one spatial multigrid V-cycle per step (Remark on the V-cycle
+                               approximation in space; damped point-block Jacobi, nu_x, omega_x) */
+
 #define ST_MAX_PT    3   /* largest supported DG degree p_t (q <= 4) */
 
 typedef struct st_mesh {
@@ -74,6 +78,9 @@ typedef struct st_options {
   int coarsest_steps;    /* time steps on the coarsest level, power of 2, default 1 (Section 2) */
   int inner_cycles;      /* ST_MIXED: FP32 V-cycles per FP64 refinement step, default 1 */
   size_t max_workspace_bytes;  /* 0 = unlimited; setup fails with ST_ENOMEM above it */
+  int smoother;          /* ST_SMOOTH_EXACT (default) or ST_SMOOTH_VCYCLE */
+  int nu_x;              /* ST_SMOOTH_VCYCLE: spatial pre-/post-smoothing steps, default 2 (Section 4) */
+  double omega_x;        /* ST_SMOOTH_VCYCLE: spatial Jacobi damping, default 2/3 (Section 4) */
 } st_options;
 
 typedef struct st_handle st_handle;
@@ -137,7 +144,8 @@ int st_adjoint_solve(st_handle* h, const double* g, double* lambda, double* grad
 /* r = f - L_L u (no IC term) or f - L_L^T u. */
 int st_level_residual(st_handle* h, int L, int adjoint, const double* f, const double* u, double* r);
 
-/* d = D_L^{-1} r (exact block inverse of diag{A}, Section 3.1), in FP64. */
+/* d = D_L^{-1} r in FP64: the smoother's block inverse -- exact (Section 3.1)
+ * with ST_SMOOTH_EXACT, one spatial V-cycle per step with ST_SMOOTH_VCYCLE. */
 int st_level_block_solve(st_handle* h, int L, int adjoint, const double* r, double* d);
 
 /* nu damped block-Jacobi steps u <- u + omega D^{-1}(f - L u) (eq. chap4_smoother). */
@@ -167,7 +175,8 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
 #define ST_K_NORM       5   /* both reduction stages */
 #define ST_K_VECTOR     6   /* axpy, casts, copies, memsets */
 #define ST_K_RHS        7   /* smoother right-hand side f - B u_prev */
-#define ST_K_COUNT      8
+#define ST_K_SPACEMG    8   /* spatial V-cycle of the inexact block inverse */
+#define ST_K_COUNT      9
 
 /* Record a CUDA event pair around every kernel launched by this handle, for up
  * to max_launches launches (events are created here, not per launch).  Adds a

@@ -167,3 +167,161 @@ def smoothing_factor(p_t, mu, full, Nx=1024, Nt=256, omega=0.5):
             if high:
                 best = max(best, spectral_radius(sym.S(a, b)))
     return best
+
+
+# ---------------------------------------------------------------------------
+# Batched evaluation over many frequencies (same formulas as Symbols, written
+# with numpy broadcasting so that the full frequency grid of the paper's
+# experiments, N_x = 1024 and N_t = 256, takes seconds).
+# ---------------------------------------------------------------------------
+def _L_batch(K, M, N, tx, tt, tau, h):
+    """Lhat for arrays tx, tt (Lemma 17): shape (F, q, q)."""
+    pref = (h / 3.0 * (2.0 + np.cos(tx)))[:, None, None]
+    b = (beta(tx) / h ** 2)[:, None, None]
+    ph = np.exp(-1j * tt)[:, None, None]
+    return pref * (K[None] + b * M[None] - ph * N[None])
+
+
+def _S_batch(K, M, N, tx, tt, h, omega):
+    q = K.shape[0]
+    A = K[None] + (beta(tx) / h ** 2)[:, None, None] * M[None]
+    inner = np.linalg.solve(A, np.broadcast_to(N, A.shape))
+    return (1.0 - omega) * np.eye(q)[None] + omega * np.exp(-1j * tt)[:, None, None] * inner
+
+
+def _gam_arr(t):
+    return np.where(t > 0, t - np.pi, t + np.pi)
+
+
+def two_grid_factor_batch(p_t, mu, nu, full, Nx=1024, Nt=256, omega=0.5):
+    """rho(Mhat_mu^{s|f}) over all low frequencies with tx != 0, vectorised;
+    equal to two_grid_factor (checked by a test)."""
+    h = 1.0 / Nx
+    tau = mu * h ** 2
+    q = p_t + 1
+    K, M, N = dg_time.time_matrices(p_t, tau)
+    K2, M2, N2 = dg_time.time_matrices(p_t, 2 * tau)
+    R1, R2 = transfer.time_blocks(p_t, tau)
+    txs, tts = low_frequencies(Nx, Nt)
+    TX, TT = np.meshgrid(txs, tts, indexing="ij")
+    tx, tt = TX.ravel(), TT.ravel()
+    F = tx.size
+    harm = [(tx, tt), (_gam_arr(tx), tt), (tx, _gam_arr(tt)), (_gam_arr(tx), _gam_arr(tt))]
+    Lt = np.zeros((F, 4 * q, 4 * q), dtype=complex)
+    St = np.zeros((F, 4 * q, 4 * q), dtype=complex)
+    for i, (a, b) in enumerate(harm):
+        Lt[:, i * q:(i + 1) * q, i * q:(i + 1) * q] = _L_batch(K, M, N, a, b, tau, h)
+        St[:, i * q:(i + 1) * q, i * q:(i + 1) * q] = _S_batch(K, M, N, a, b, h, omega)
+
+    def Rt(t):
+        return np.exp(-1j * t)[:, None, None] * R1[None] + R2[None]
+
+    def Pt(t):
+        return 0.5 * (np.exp(1j * t)[:, None, None] * R1.T[None] + R2.T[None])
+
+    if full:
+        Rf = np.concatenate([(1.0 + np.cos(a))[:, None, None] * Rt(b) for (a, b) in harm], axis=2)
+        Pf = np.concatenate([(0.5 * (1.0 + np.cos(a)))[:, None, None] * Pt(b) for (a, b) in harm], axis=1)
+        K4, M4, N4 = dg_time.time_matrices(p_t, 2 * tau)
+        Lc = _L_batch(K4, M4, N4, 2 * tx, 2 * tt, 2 * tau, 2 * h)
+        Kt = np.eye(4 * q)[None] - Pf @ np.linalg.solve(Lc, Rf @ Lt)
+    else:
+        Z = np.zeros((F, q, q), dtype=complex)
+        Rs = np.concatenate([np.concatenate([Rt(tt), Z, Rt(_gam_arr(tt)), Z], axis=2),
+                             np.concatenate([Z, Rt(tt), Z, Rt(_gam_arr(tt))], axis=2)], axis=1)
+        Ps = np.concatenate([np.concatenate([Pt(tt), Z], axis=2), np.concatenate([Z, Pt(tt)], axis=2),
+                             np.concatenate([Pt(_gam_arr(tt)), Z], axis=2),
+                             np.concatenate([Z, Pt(_gam_arr(tt))], axis=2)], axis=1)
+        Lc = np.zeros((F, 2 * q, 2 * q), dtype=complex)
+        Lc[:, :q, :q] = _L_batch(K2, M2, N2, tx, 2 * tt, 2 * tau, h)
+        Lc[:, q:, q:] = _L_batch(K2, M2, N2, _gam_arr(tx), 2 * tt, 2 * tau, h)
+        Kt = np.eye(4 * q)[None] - Ps @ np.linalg.solve(Lc, Rs @ Lt)
+    Mt = np.linalg.matrix_power(St, nu) @ Kt @ np.linalg.matrix_power(St, nu)
+    return float(np.max(np.abs(np.linalg.eigvals(Mt))))
+
+
+def _Ahat_batch(K, M, tx, h):
+    """Ahat(tx) = h/3 (2 + cos tx) K + 2/h (1 - cos tx) M (proof of Lemma 18)."""
+    return (h / 3.0 * (2.0 + np.cos(tx)))[:, None, None] * K[None] + \
+        (2.0 / h * (1.0 - np.cos(tx)))[:, None, None] * M[None]
+
+
+def spatial_iteration_symbol(K, M, tx, h, nu_x=2, omega_x=2.0 / 3.0):
+    """Mtilde(tx), 2q x 2q (Remark on the V-cycle approximation in space): the
+    spatial two-grid iteration matrix on the harmonics (tx, gamma(tx)) with
+    damped point-block Jacobi D^x = 2h/3 K + 2/h M, R_x = 1 + cos, P_x = R_x / 2,
+    coarse Ahat on 2h; smoothing order S^{nu2} K S^{nu1} (nu1 = nu2 = nu_x)."""
+    q = K.shape[0]
+    F = tx.size
+    gx = _gam_arr(tx)
+    A1, A2 = _Ahat_batch(K, M, tx, h), _Ahat_batch(K, M, gx, h)
+    Dx = 2.0 * h / 3.0 * K + 2.0 / h * M
+    Dinv = np.linalg.inv(Dx)
+    S1 = np.eye(q)[None] - omega_x * (Dinv[None] @ A1)
+    S2 = np.eye(q)[None] - omega_x * (Dinv[None] @ A2)
+    At = np.zeros((F, 2 * q, 2 * q), dtype=complex)
+    St = np.zeros((F, 2 * q, 2 * q), dtype=complex)
+    At[:, :q, :q], At[:, q:, q:] = A1, A2
+    St[:, :q, :q], St[:, q:, q:] = S1, S2
+    Rx = np.concatenate([(1.0 + np.cos(tx))[:, None, None] * np.eye(q)[None],
+                         (1.0 + np.cos(gx))[:, None, None] * np.eye(q)[None]], axis=2)
+    Px = np.concatenate([(0.5 * (1.0 + np.cos(tx)))[:, None, None] * np.eye(q)[None],
+                         (0.5 * (1.0 + np.cos(gx)))[:, None, None] * np.eye(q)[None]], axis=1)
+    Ac = _Ahat_batch(K, M, 2 * tx, 2 * h)
+    Kx = np.eye(2 * q)[None] - Px @ np.linalg.solve(Ac, Rx @ At)
+    Sn = np.linalg.matrix_power(St, nu_x)
+    return Sn @ Kx @ Sn
+
+
+def two_grid_factor_inexact_batch(p_t, mu, nu, full, Nx=1024, Nt=256, omega=0.5, nu_x=2, omega_x=2.0 / 3.0):
+    """rho(Mbar_mu^{s|f}) (eq. chap4_twoGridIterationMatrixApprox): the two-grid
+    factor with the inexact smoother Sbar = I - w (I - M) D^{-1} L, M acting as
+    Mtilde(tx) on the two space harmonics of each time harmonic (mapping
+    (chap4_mappingPropertyApprox)); otherwise as two_grid_factor_batch."""
+    h = 1.0 / Nx
+    tau = mu * h ** 2
+    q = p_t + 1
+    K, M, N = dg_time.time_matrices(p_t, tau)
+    K2, M2, N2 = dg_time.time_matrices(p_t, 2 * tau)
+    R1, R2 = transfer.time_blocks(p_t, tau)
+    txs, tts = low_frequencies(Nx, Nt)
+    TX, TT = np.meshgrid(txs, tts, indexing="ij")
+    tx, tt = TX.ravel(), TT.ravel()
+    F = tx.size
+    harm = [(tx, tt), (_gam_arr(tx), tt), (tx, _gam_arr(tt)), (_gam_arr(tx), _gam_arr(tt))]
+    Lt = np.zeros((F, 4 * q, 4 * q), dtype=complex)
+    DL = np.zeros((F, 4 * q, 4 * q), dtype=complex)
+    for i, (a, b) in enumerate(harm):
+        Lab = _L_batch(K, M, N, a, b, tau, h)
+        Lt[:, i * q:(i + 1) * q, i * q:(i + 1) * q] = Lab
+        DL[:, i * q:(i + 1) * q, i * q:(i + 1) * q] = np.linalg.solve(_Ahat_batch(K, M, a, h), Lab)
+    Mx = spatial_iteration_symbol(K, M, tx, h, nu_x, omega_x)
+    Mbig = np.zeros((F, 4 * q, 4 * q), dtype=complex)
+    Mbig[:, :2 * q, :2 * q] = Mx
+    Mbig[:, 2 * q:, 2 * q:] = Mx
+    Sbar = np.eye(4 * q)[None] - omega * (np.eye(4 * q)[None] - Mbig) @ DL
+
+    def Rt(t):
+        return np.exp(-1j * t)[:, None, None] * R1[None] + R2[None]
+
+    def Pt(t):
+        return 0.5 * (np.exp(1j * t)[:, None, None] * R1.T[None] + R2.T[None])
+
+    if full:
+        Rf = np.concatenate([(1.0 + np.cos(a))[:, None, None] * Rt(b) for (a, b) in harm], axis=2)
+        Pf = np.concatenate([(0.5 * (1.0 + np.cos(a)))[:, None, None] * Pt(b) for (a, b) in harm], axis=1)
+        Lc = _L_batch(K2, M2, N2, 2 * tx, 2 * tt, 2 * tau, 2 * h)
+        Kt = np.eye(4 * q)[None] - Pf @ np.linalg.solve(Lc, Rf @ Lt)
+    else:
+        Z = np.zeros((F, q, q), dtype=complex)
+        Rs = np.concatenate([np.concatenate([Rt(tt), Z, Rt(_gam_arr(tt)), Z], axis=2),
+                             np.concatenate([Z, Rt(tt), Z, Rt(_gam_arr(tt))], axis=2)], axis=1)
+        Ps = np.concatenate([np.concatenate([Pt(tt), Z], axis=2), np.concatenate([Z, Pt(tt)], axis=2),
+                             np.concatenate([Pt(_gam_arr(tt)), Z], axis=2),
+                             np.concatenate([Z, Pt(_gam_arr(tt))], axis=2)], axis=1)
+        Lc = np.zeros((F, 2 * q, 2 * q), dtype=complex)
+        Lc[:, :q, :q] = _L_batch(K2, M2, N2, tx, 2 * tt, 2 * tau, h)
+        Lc[:, q:, q:] = _L_batch(K2, M2, N2, _gam_arr(tx), 2 * tt, 2 * tau, h)
+        Kt = np.eye(4 * q)[None] - Ps @ np.linalg.solve(Lc, Rs @ Lt)
+    Mt = np.linalg.matrix_power(Sbar, nu) @ Kt @ np.linalg.matrix_power(Sbar, nu)
+    return float(np.max(np.abs(np.linalg.eigvals(Mt))))

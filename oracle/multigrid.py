@@ -2,7 +2,8 @@
 
 * damped block-Jacobi smoother, eq. (chap4_smoother), with the exact block
   inverse D^{-1} = diag(A)^{-1} used throughout Section 3 (one sparse LU of A
-  per level, applied to all time steps);
+  per level, applied to all time steps), or the inexact D~^{-1} of the Remark
+  on the V-cycle approximation (one spatial V-cycle per time step);
 * coarse operators re-discretised on (tau_L, h_L) (Section 3.2);
 * restriction / prolongation of ``transfer`` with P = R^T (Section 2);
 * coarsest level solved exactly (Section 2): one time step with the LU of A,
@@ -15,19 +16,78 @@
   R = P^T.
 """
 import numpy as np
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import hierarchy, spacetime, transfer
 
 
+class SpatialVCycle:
+    """Inexact block inverse of the Remark on the V-cycle approximation in space
+    (eq. chap4_smootherApprox): one multigrid V-cycle in space for
+    A_{tau,h} = K_tau (x) M_h + M_tau (x) K_h with zero initial guess, damped
+    point-block Jacobi smoothing with D^x = diag{(M_h)_jj K_tau + (K_h)_jj M_tau}
+    (in 1D: 2h/3 K_tau + 2/h M_tau), nu_x pre- and post-smoothing steps,
+    restriction R_x (x) I, prolongation its transpose, coarse operators
+    A_{tau,2h} re-discretised, and an exact solve on one node."""
+
+    def __init__(self, d, n, p_t, tau, nu_x=2, omega_x=2.0 / 3.0):
+        self.nu_x, self.omega_x = nu_x, omega_x
+        self.q = p_t + 1
+        self.levels = []
+        nl = n
+        while True:
+            disc = spacetime.Discretization(d, nl, p_t, 1, tau)
+            A = disc.A.tocsr()
+            Nx = disc.Nx
+            # point blocks A[(l, j), (l', j)] of every node j, shape (Nx, q, q)
+            blocks = np.zeros((Nx, self.q, self.q))
+            for a in range(self.q):
+                for b in range(self.q):
+                    blocks[:, a, b] = A[a * Nx:(a + 1) * Nx, b * Nx:(b + 1) * Nx].diagonal()
+            lvl = {"n": nl, "Nx": Nx, "A": A, "blocks": blocks, "R": None, "lu": None}
+            self.levels.append(lvl)
+            if nl == 1:
+                lvl["lu"] = spla.splu(A.tocsc())
+                break
+            Rx = transfer.space_restriction(d, nl)
+            lvl["R"] = sp.kron(sp.identity(self.q), Rx, format="csr")
+            nl = (nl - 1) // 2
+
+    def _jacobi(self, lvl, x, b, adjoint):
+        A = lvl["A"].T if adjoint else lvl["A"]
+        blocks = np.transpose(lvl["blocks"], (0, 2, 1)) if adjoint else lvl["blocks"]
+        r = b - A @ x                                   # (q Nx, m)
+        q, Nx = self.q, lvl["Nx"]
+        rn = r.reshape(q, Nx, -1).transpose(1, 0, 2)     # (Nx, q, m)
+        dn = np.linalg.solve(blocks, rn)
+        return x + self.omega_x * dn.transpose(1, 0, 2).reshape(q * Nx, -1)
+
+    def apply(self, b, adjoint=False, i=0):
+        """Approximate A^{-1} b for the columns of b (shape (q Nx, m))."""
+        lvl = self.levels[i]
+        if lvl["lu"] is not None:
+            return (lvl["lu"].solve(b, trans="T") if adjoint else lvl["lu"].solve(b))
+        A = lvl["A"].T if adjoint else lvl["A"]
+        x = np.zeros_like(b)
+        for _ in range(self.nu_x):
+            x = self._jacobi(lvl, x, b, adjoint)
+        bc = lvl["R"] @ (b - A @ x)
+        x = x + lvl["R"].T @ self.apply(bc, adjoint, i + 1)
+        for _ in range(self.nu_x):
+            x = self._jacobi(lvl, x, b, adjoint)
+        return x
+
+
 class Level:
-    def __init__(self, d, lv, p_t):
+    def __init__(self, d, lv, p_t, smoother="exact", nu_x=2, omega_x=2.0 / 3.0):
         self.disc = spacetime.Discretization(d, lv["n"], p_t, lv["N"], lv["tau"])
         self.full = lv["full"]
         self.mu = lv["mu"]
         self.lu = spla.splu(self.disc.A.tocsc())
         self._luT = None       # LU of A^T, built on first adjoint use
         self.R = None          # restriction to the next coarser level
+        self.inexact = SpatialVCycle(d, lv["n"], p_t, lv["tau"], nu_x, omega_x) if smoother == "vcycle" else None
 
     @property
     def luT(self):
@@ -36,7 +96,14 @@ class Level:
         return self._luT
 
     def block_solve(self, r, adjoint=False):
-        """D^{-1} r: A^{-1} (or A^{-T}) applied to every time block of r."""
+        """D^{-1} r: A^{-1} (or A^{-T}) applied to every time block of r, or its
+        approximation by one spatial V-cycle when the level smoother is 'vcycle'."""
+        if self.inexact is not None:
+            return self.inexact.apply(np.ascontiguousarray(r.T), adjoint).T
+        lu = self.luT if adjoint else self.lu
+        return lu.solve(np.ascontiguousarray(r.T)).T
+
+    def exact_block_solve(self, r, adjoint=False):
         lu = self.luT if adjoint else self.lu
         return lu.solve(np.ascontiguousarray(r.T)).T
 
@@ -49,9 +116,10 @@ class Level:
 class Hierarchy:
     """Levels finest-first (index 0 is the finest, the paper's M_L)."""
 
-    def __init__(self, d, n, p_t, N, T, coarsening="auto", coarsest_steps=1):
+    def __init__(self, d, n, p_t, N, T, coarsening="auto", coarsest_steps=1, smoother="exact", nu_x=2,
+                 omega_x=2.0 / 3.0):
         self.params = hierarchy.build_levels(d, n, p_t, N, T, coarsening, coarsest_steps)
-        self.levels = [Level(d, lv, p_t) for lv in self.params]
+        self.levels = [Level(d, lv, p_t, smoother, nu_x, omega_x) for lv in self.params]
         for i in range(len(self.levels) - 1):
             self.levels[i].R = transfer.restriction(self.levels[i].disc, self.levels[i].full)
 
@@ -68,8 +136,9 @@ def smooth(level, u, f, nu, omega, adjoint=False):
 
 
 def coarsest_solve(level, f, adjoint=False):
+    """Exact solve on the coarsest level (Section 2), whatever the smoother."""
     if level.disc.N == 1:
-        return level.block_solve(f, adjoint)
+        return level.exact_block_solve(f, adjoint)
     return backward_substitution(level, f) if adjoint else forward_substitution(level, f)
 
 

@@ -148,6 +148,18 @@ struct Vecs {
   T* r = nullptr;
 };
 
+// One spatial level of the inexact block inverse: iterate x, right-hand side
+// b (not owned on the finest spatial level) and a ping-pong / residual buffer t.
+template <typename T>
+struct SpaceLvl {
+  int n = 0;
+  double h = 0;
+  int64_t Nx = 0;
+  T* x = nullptr;
+  T* b = nullptr;
+  T* t = nullptr;
+};
+
 struct Level {
   int N = 0, n = 0;
   double tau = 0, h = 0, mu = 0;
@@ -157,6 +169,8 @@ struct Level {
   Vecs<float> v32;
   Tables<double> t64;
   Tables<float> t32;
+  std::vector<SpaceLvl<double>> sp64;   // spatial hierarchy of the inexact block inverse
+  std::vector<SpaceLvl<float>> sp32;
 };
 
 }  // namespace
@@ -384,9 +398,33 @@ void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
   }
 }
 
+template <typename T>
+void make_space(st_handle* h, Level& lv, std::vector<SpaceLvl<T>>& sp) {
+  int nl = lv.n;
+  double hl = lv.h;
+  while (true) {
+    SpaceLvl<T> s;
+    s.n = nl;
+    s.h = hl;
+    s.Nx = 1;
+    for (int a = 0; a < h->d; ++a) s.Nx *= nl;
+    const int64_t cnt = (int64_t)lv.N * h->q * s.Nx;
+    s.x = dalloc<T>(h, cnt);
+    s.t = dalloc<T>(h, cnt);
+    if (!sp.empty()) s.b = dalloc<T>(h, cnt);   // the finest spatial level reads the caller's vector
+    sp.push_back(s);
+    if (nl == 1) break;
+    nl = (nl - 1) / 2;
+    hl *= 2.0;
+  }
+}
+
 template <typename T> Vecs<T>& vecs(Level& lv);
 template <> Vecs<double>& vecs<double>(Level& lv) { return lv.v64; }
 template <> Vecs<float>& vecs<float>(Level& lv) { return lv.v32; }
+template <typename T> std::vector<SpaceLvl<T>>& spaces(Level& lv);
+template <> std::vector<SpaceLvl<double>>& spaces<double>(Level& lv) { return lv.sp64; }
+template <> std::vector<SpaceLvl<float>>& spaces<float>(Level& lv) { return lv.sp32; }
 template <typename T> Tables<T>& tables(Level& lv);
 template <> Tables<double>& tables<double>(Level& lv) { return lv.t64; }
 template <> Tables<float>& tables<float>(Level& lv) { return lv.t32; }
@@ -488,6 +526,39 @@ template <typename T, int D, int Q>
 void launch_ic_grad_t(st_handle* h, const Level& lv, const T* lam, T* g) {
   auto tc = to_coef<T, Q>(h->tm);
   stmg::k_ic_gradient<T, D, Q><<<blocks_for(lv.Nx), kThreads, 0, h->stream>>>(lam, g, lv.n, (T)lv.h, tc);
+}
+
+template <typename T, int D, int Q>
+void launch_space_op_t(st_handle* h, const Level& lv, int n, double hl, int mode, bool adj, const T* x, const T* b,
+                       T* xo, double w, const double* dinv) {
+  auto tc = to_coef<T, Q>(h->tm);
+  stmg::SmallMat<T, Q> m{};
+  for (int i = 0; i < Q * Q; ++i) m.a[i] = (T)dinv[i];
+  int64_t Nx = 1;
+  for (int a = 0; a < D; ++a) Nx *= n;
+  dim3 grid(blocks_for(Nx), lv.N);
+  const T tau = (T)lv.tau, hh = (T)hl, ww = (T)w;
+#define STMG_SPACE_OP(ADJ, MODE) \
+  stmg::k_space_op<T, D, Q, ADJ, MODE><<<grid, kThreads, 0, h->stream>>>(x, b, xo, n, lv.N, tau, hh, ww, m, tc)
+  if (adj) {
+    if (mode == 0) STMG_SPACE_OP(true, 0); else if (mode == 1) STMG_SPACE_OP(true, 1); else STMG_SPACE_OP(true, 2);
+  } else {
+    if (mode == 0) STMG_SPACE_OP(false, 0); else if (mode == 1) STMG_SPACE_OP(false, 1); else STMG_SPACE_OP(false, 2);
+  }
+#undef STMG_SPACE_OP
+}
+
+template <typename T, int D, int Q>
+void launch_space_transfer_t(st_handle* h, const Level& lv, int nf, int nc, bool restrict_, const T* in, T* out) {
+  int64_t Nxf = 1, Nxc = 1;
+  for (int a = 0; a < D; ++a) {
+    Nxf *= nf;
+    Nxc *= nc;
+  }
+  if (restrict_)
+    stmg::k_restrict_space<T, D, Q><<<dim3(blocks_for(Nxc), lv.N), kThreads, 0, h->stream>>>(in, out, nf, nc, lv.N);
+  else
+    stmg::k_prolong_space<T, D, Q><<<dim3(blocks_for(Nxf), lv.N), kThreads, 0, h->stream>>>(in, out, nf, nc, lv.N);
 }
 
 #define STMG_DISPATCH(FN, ...)                                                   \
@@ -595,22 +666,41 @@ size_t dst_reg_smem() {
   return ((size_t)Lay::TAB + (size_t)rows * Lay::RS) * sizeof(T);
 }
 
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// Opt the sine-transform kernels into the dynamic shared memory they need for
+// the row lengths this hierarchy uses (only levels with d >= 2 transform).
 template <typename T>
-void dst_set_smem_limits(st_handle* h, int maxNf) {
-  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_reg_smem<T, 3, 2>()), "cudaFuncSetAttribute");
-  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_reg_smem<T, 3, 3>()), "cudaFuncSetAttribute");
-  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_reg_smem<T, 4, 3>()), "cudaFuncSetAttribute");
-  check(h, cudaFuncSetAttribute(stmg::k_dst_rows_reg<T, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_reg_smem<T, 4, 4>()), "cudaFuncSetAttribute");
-  check(h, cudaFuncSetAttribute(stmg::k_dst_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_rows_smem<T>(maxNf)), "cudaFuncSetAttribute");
-  check(h, cudaFuncSetAttribute(stmg::k_dst_cols<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_cols_smem<T, 32>(maxNf)), "cudaFuncSetAttribute");
-  check(h, cudaFuncSetAttribute(stmg::k_dst_cols<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dst_cols_smem<T, 16>(maxNf)), "cudaFuncSetAttribute");
+void dst_set_smem_limits(st_handle* h) {
+  if (h->d < 2) return;
+  int maxNf = 2;
+  for (const Level& l : h->levels) maxNf = std::max(maxNf, l.n + 1);
+  auto set = [&](const void* fn, size_t bytes) {
+    if (bytes > kMaxSmem) fail(h, ST_EINVAL, "n too large for the sine-transform kernels (n <= 511)");
+    check(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+          "cudaFuncSetAttribute");
+  };
+  for (const Level& l : h->levels) {
+    const int Nf = l.n + 1;
+    if (Nf >= 64 && Nf <= 512) {
+      if (Nf == 64) set((const void*)stmg::k_dst_rows_reg<T, 3, 2>, dst_reg_smem<T, 3, 2>());
+      if (Nf == 128) set((const void*)stmg::k_dst_rows_reg<T, 3, 3>, dst_reg_smem<T, 3, 3>());
+      if (Nf == 256) set((const void*)stmg::k_dst_rows_reg<T, 4, 3>, dst_reg_smem<T, 4, 3>());
+      if (Nf == 512) set((const void*)stmg::k_dst_rows_reg<T, 4, 4>, dst_reg_smem<T, 4, 4>());
+    } else {
+      set((const void*)stmg::k_dst_rows<T>, dst_rows_smem<T>(Nf));
+    }
+  }
+  if (h->d == 3) {   // y axis of 3D levels: column tiles of W = 16 (FP64, Nf >= 512) or 32 lines
+    int max16 = 0, max32 = 0;
+    for (const Level& l : h->levels) {
+      const int Nf = l.n + 1;
+      if (sizeof(T) == 8 && Nf >= 512) max16 = std::max(max16, Nf); else max32 = std::max(max32, Nf);
+    }
+    if (max16) set((const void*)stmg::k_dst_cols<T, 16>, dst_cols_smem<T, 16>(max16));
+    if (max32) set((const void*)stmg::k_dst_cols<T, 32>, dst_cols_smem<T, 32>(max32));
+  }
+  (void)maxNf;
 }
 
 // Algorithmic flops of one sine transform of a line of n = Nf - 1 values:
@@ -702,11 +792,123 @@ void axpy(st_handle* h, T* y, const T* x, T a, int64_t n) {
   stmg::k_axpy<T><<<std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, n);
 }
 
+// Node block D^x = (M_h)_jj K + (K_h)_jj tau Mh of a uniform Q1 grid with spacing hl
+// ((M_h)_jj = (2hl/3)^d, (K_h)_jj = d (2/hl)(2hl/3)^(d-1)), inverted; transposed
+// K for the adjoint.  On a one-node grid this block is A itself.
+void node_block_inverse(const st_handle* h, double hl, double tau, bool adj, double* out) {
+  const int q = h->q, d = h->d;
+  const double md = std::pow(2.0 * hl / 3.0, d);
+  const double kd = d * (2.0 / hl) * std::pow(2.0 * hl / 3.0, d - 1);
+  double A[kQmax * kQmax], X[kQmax * kQmax];
+  for (int k = 0; k < q; ++k)
+    for (int l = 0; l < q; ++l) {
+      A[k * q + l] = md * (adj ? h->tm.K[l * q + k] : h->tm.K[k * q + l]) + (k == l ? kd * tau * h->tm.Mh[k] : 0.0);
+      X[k * q + l] = (k == l) ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < q; ++c) {   // Gauss-Jordan with partial pivoting
+    int p = c;
+    for (int r = c + 1; r < q; ++r)
+      if (std::fabs(A[r * q + c]) > std::fabs(A[p * q + c])) p = r;
+    if (p != c)
+      for (int j = 0; j < q; ++j) {
+        std::swap(A[c * q + j], A[p * q + j]);
+        std::swap(X[c * q + j], X[p * q + j]);
+      }
+    const double dv = 1.0 / A[c * q + c];
+    for (int j = 0; j < q; ++j) {
+      A[c * q + j] *= dv;
+      X[c * q + j] *= dv;
+    }
+    for (int r = 0; r < q; ++r) {
+      if (r == c) continue;
+      const double f = A[r * q + c];
+      for (int j = 0; j < q; ++j) {
+        A[r * q + j] -= f * A[c * q + j];
+        X[r * q + j] -= f * X[c * q + j];
+      }
+    }
+  }
+  for (int i = 0; i < q * q; ++i) out[i] = X[i];
+}
+
+template <typename T>
+void space_op(st_handle* h, Level& lv, const SpaceLvl<T>& sl, int mode, bool adj, const T* x, const T* b, T* xo,
+              double w, const double* dinv) {
+  const double nodes = (double)lv.N * sl.Nx, Q = h->q;
+  Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * nodes * (mode == 2 ? 2.0 : 3.0),
+          2.0 * nodes * (mode == 2 ? Q * Q : Q * (9.0 * h->d - 3.0) + 2.0 * Q * Q + Q), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_op_t, h, lv, sl.n, sl.h, mode, adj, x, b, xo, w, dinv);
+}
+
+template <typename T>
+void space_transfer(st_handle* h, Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse, bool restrict_,
+                    const T* in, T* out) {
+  Prof pr(h, ST_K_SPACEMG, sizeof(T) * h->q * (double)lv.N * (restrict_ ? fine.Nx + coarse.Nx : 2.0 * fine.Nx + coarse.Nx),
+          0.0, 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_transfer_t, h, lv, fine.n, coarse.n, restrict_, in, out);
+}
+
+// x = D~^{-1} b on every time step of level lv: one spatial V-cycle from x = 0
+// (Remark on the V-cycle approximation in space), spatial level ell.
+template <typename T>
+void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) {
+  std::vector<SpaceLvl<T>>& sp = spaces<T>(lv);
+  const SpaceLvl<T>& sl = sp[ell];
+  double dinv[kQmax * kQmax];
+  node_block_inverse(h, sl.h, lv.tau, adj, dinv);
+  if (sl.n == 1) {   // one node: D^x = A, exact solve
+    space_op<T>(h, lv, sl, 2, adj, nullptr, b, x, 1.0, dinv);
+    return;
+  }
+  const double w = h->opt.omega_x;
+  T* cur = x;
+  T* oth = sl.t;
+  space_op<T>(h, lv, sl, 2, adj, nullptr, b, cur, w, dinv);
+  for (int i = 1; i < h->opt.nu_x; ++i) {
+    space_op<T>(h, lv, sl, 0, adj, cur, b, oth, w, dinv);
+    std::swap(cur, oth);
+  }
+  space_op<T>(h, lv, sl, 1, adj, cur, b, oth, 0.0, dinv);       // residual b - A x into oth
+  const SpaceLvl<T>& cl = sp[ell + 1];
+  space_transfer<T>(h, lv, sl, cl, true, oth, cl.b);
+  space_vcycle<T>(h, lv, ell + 1, adj, cl.x, cl.b);
+  space_transfer<T>(h, lv, sl, cl, false, cl.x, cur);
+  for (int i = 0; i < h->opt.nu_x; ++i) {
+    space_op<T>(h, lv, sl, 0, adj, cur, b, oth, w, dinv);
+    std::swap(cur, oth);
+  }
+  if (cur != x) copy<T>(h, x, cur, (int64_t)lv.N * h->q * sl.Nx);
+}
+
+// d = D~^{-1} r, the smoother's block inverse: exact, or one spatial V-cycle.
+template <typename T>
+void smoother_block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d) {
+  if (h->opt.smoother == ST_SMOOTH_VCYCLE) {
+    if (r == d) {
+      T* x = spaces<T>(lv)[0].x;
+      space_vcycle<T>(h, lv, 0, adj, x, r);
+      copy<T>(h, d, x, lv.ndof);
+    } else {
+      space_vcycle<T>(h, lv, 0, adj, d, r);
+    }
+    return;
+  }
+  block_solve<T>(h, lv, adj, r, d, 0, lv.N);
+}
+
 // One damped block-Jacobi step (eq. chap4_smoother), u <- u + w D^{-1}(f - L u),
 // evaluated as u <- (1 - w) u + w A^{-1} (f - B u_prev): the block inverse of
 // the block row removes A u_n, so only the rank-one time coupling is applied.
 template <typename T>
 void smooth_step(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
+  if (h->opt.smoother == ST_SMOOTH_VCYCLE) {
+    // inexact block inverse: u <- u + w D~^{-1} (f - L u) (eq. chap4_smootherApprox)
+    residual<T>(h, lv, adj, f, u, u0, work);
+    T* d = spaces<T>(lv)[0].x;
+    space_vcycle<T>(h, lv, 0, adj, d, work);
+    axpy<T>(h, u, d, (T)h->opt.omega, lv.ndof);
+    return;
+  }
   rhs<T>(h, lv, adj, f, u, u0, work);
   block_solve<T>(h, lv, adj, work, work, 0, lv.N);
   axpby<T>(h, u, work, (T)(1.0 - h->opt.omega), (T)h->opt.omega, lv.ndof);
@@ -880,6 +1082,9 @@ void st_default_options(st_options* o) {
   o->coarsest_steps = 1;
   o->inner_cycles = 1;
   o->max_workspace_bytes = 0;
+  o->smoother = ST_SMOOTH_EXACT;
+  o->nu_x = 2;
+  o->omega_x = 2.0 / 3.0;
 }
 
 int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt, void* cuda_stream,
@@ -898,6 +1103,9 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       fail(h, ST_EINVAL, "bad options");
     if (h->opt.precision != ST_FP64 && h->opt.precision != ST_MIXED) fail(h, ST_EINVAL, "bad precision");
     if (h->opt.coarsening < ST_AUTO || h->opt.coarsening > ST_FULL) fail(h, ST_EINVAL, "bad coarsening");
+    if (h->opt.smoother != ST_SMOOTH_EXACT && h->opt.smoother != ST_SMOOTH_VCYCLE) fail(h, ST_EINVAL, "bad smoother");
+    if (h->opt.smoother == ST_SMOOTH_VCYCLE && (h->opt.nu_x < 1 || !(h->opt.omega_x > 0.0)))
+      fail(h, ST_EINVAL, "bad spatial smoothing options");
     if (h->opt.coarsest_steps < 1) h->opt.coarsest_steps = 1;
     if (!is_pow2(h->opt.coarsest_steps) || h->opt.coarsest_steps > N) fail(h, ST_EINVAL, "bad coarsest_steps");
     h->d = mesh->dim;
@@ -948,11 +1156,13 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       }
       l.v64.r = dalloc<double>(h, l.ndof);
       make_tables<double>(h, l, l.t64);
+      if (h->opt.smoother == ST_SMOOTH_VCYCLE) make_space<double>(h, l, l.sp64);
       if (mixed) {
         l.v32.u = dalloc<float>(h, l.ndof);
         l.v32.f = dalloc<float>(h, l.ndof);
         l.v32.r = dalloc<float>(h, l.ndof);
         make_tables<float>(h, l, l.t32);
+        if (h->opt.smoother == ST_SMOOTH_VCYCLE) make_space<float>(h, l, l.sp32);
       }
     }
     if (mixed) {
@@ -962,10 +1172,8 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       h->coarse64_r = dalloc<double>(h, c.ndof);
       h->r64 = finest(h).v64.r;
     }
-    int maxNf = 2;
-    for (const Level& l : h->levels) maxNf = std::max(maxNf, l.n + 1);
-    dst_set_smem_limits<double>(h, maxNf);
-    if (mixed) dst_set_smem_limits<float>(h, maxNf);
+    dst_set_smem_limits<double>(h);
+    if (mixed) dst_set_smem_limits<float>(h);
     h->partial = dalloc<double>(h, kNormBlocks);
     h->dnorm = dalloc<double>(h, 1);
     check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");
@@ -1071,7 +1279,7 @@ int st_level_block_solve(st_handle* h, int L, int adjoint, const double* r, doub
   return guarded(h, [&]() -> int {
     if (!r || !d) fail(h, ST_EINVAL, "null pointer");
     Level& lv = h->levels[level_index(h, L)];
-    block_solve<double>(h, lv, adjoint != 0, r, d, 0, lv.N);
+    smoother_block_solve<double>(h, lv, adjoint != 0, r, d);
     after_launch(h);
     return ST_OK;
   });

@@ -21,6 +21,7 @@ ST_FP64, ST_MIXED = 0, 1
 ST_AUTO, ST_SEMI, ST_FULL = 0, 1, 2
 ST_INIT_GIVEN = 1
 ST_MAX_PT = 3
+ST_SMOOTH_EXACT, ST_SMOOTH_VCYCLE = 0, 1
 
 EXPORTS = [
     "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
@@ -31,7 +32,7 @@ EXPORTS = [
 
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
 
-KERNEL_CLASSES = ["residual", "dst", "line_solve", "restrict", "prolong", "norm", "vector", "rhs"]
+KERNEL_CLASSES = ["residual", "dst", "line_solve", "restrict", "prolong", "norm", "vector", "rhs", "space_mg"]
 
 
 class StMesh(ctypes.Structure):
@@ -42,7 +43,8 @@ class StOptions(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("coarsening", ctypes.c_int), ("coarsest_steps", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("max_workspace_bytes", ctypes.c_size_t)]
+                ("inner_cycles", ctypes.c_int), ("max_workspace_bytes", ctypes.c_size_t),
+                ("smoother", ctypes.c_int), ("nu_x", ctypes.c_int), ("omega_x", ctypes.c_double)]
 
 
 class StmgError(RuntimeError):
@@ -128,7 +130,7 @@ class Solver:
 
     def __init__(self, dim, n, p_t, N, T, *, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50,
                  precision="fp64", coarsening="auto", coarsest_steps=1, inner_cycles=1,
-                 max_workspace_bytes=0, stream=None, device=None):
+                 max_workspace_bytes=0, smoother="exact", nu_x=2, omega_x=2.0 / 3.0, stream=None, device=None):
         L = lib()
         self._lib = L
         self.dim, self.n, self.p_t, self.N, self.T = dim, n, p_t, N, float(T)
@@ -141,6 +143,9 @@ class Solver:
         opt.coarsest_steps = coarsest_steps
         opt.inner_cycles = inner_cycles
         opt.max_workspace_bytes = max_workspace_bytes
+        opt.smoother = {"exact": ST_SMOOTH_EXACT, "vcycle": ST_SMOOTH_VCYCLE}[smoother]
+        opt.nu_x = nu_x
+        opt.omega_x = omega_x
         self.options = opt
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

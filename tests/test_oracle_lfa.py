@@ -103,3 +103,14 @@ def test_two_grid_contraction_agrees_with_lfa(p):
     meas = measured_two_grid(p, 0.01, True)
     th = lfa.two_grid_factor(p, 0.01, 2, True, Nx=128, Nt=32)
     assert meas > 0.5 and th > 0.5
+
+
+@pytest.mark.parametrize("p", [0, 1])
+@pytest.mark.parametrize("full", [False, True])
+def test_batched_two_grid_factor_equals_loop(p, full):
+    """The vectorised LFA used for the paper-size comparison equals the
+    frequency-by-frequency evaluation of Theorems 5-6."""
+    for mu in [0.01, hierarchy.mu_star(p), 30.0]:
+        a = lfa.two_grid_factor(p, mu, 2, full, Nx=64, Nt=16)
+        b = lfa.two_grid_factor_batch(p, mu, 2, full, Nx=64, Nt=16)
+        assert abs(a - b) < 1e-12
