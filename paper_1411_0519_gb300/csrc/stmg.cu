@@ -445,10 +445,10 @@ void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, cons
       grid.z = std::min(65535, ns - c);
       if (adj)
         stmg::k_residual2d<T, Q, true><<<grid, block, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c, (T)lv.tau,
-                                                                       (T)lv.h, tc);
+                                                                       (T)lv.h, (T)(1.0 / lv.h), tc);
       else
         stmg::k_residual2d<T, Q, false><<<grid, block, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c, (T)lv.tau,
-                                                                        (T)lv.h, tc);
+                                                                        (T)lv.h, (T)(1.0 / lv.h), tc);
     }
     return;
   }
@@ -457,10 +457,10 @@ void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, cons
     grid.y = std::min(65535, ns - c);
     if (adj)
       stmg::k_residual<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c,
-                                                                         (T)lv.tau, (T)lv.h, tc);
+                                                                         (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), tc);
     else
       stmg::k_residual<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, lv.N, s0 + c,
-                                                                          (T)lv.tau, (T)lv.h, tc);
+                                                                          (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), tc);
   }
 }
 
@@ -537,9 +537,9 @@ void launch_space_op_t(st_handle* h, const Level& lv, int n, double hl, int mode
   int64_t Nx = 1;
   for (int a = 0; a < D; ++a) Nx *= n;
   dim3 grid(blocks_for(Nx), lv.N);
-  const T tau = (T)lv.tau, hh = (T)hl, ww = (T)w;
+  const T tau = (T)lv.tau, hh = (T)hl, hinv = (T)(1.0 / hl), ww = (T)w;
 #define STMG_SPACE_OP(ADJ, MODE) \
-  stmg::k_space_op<T, D, Q, ADJ, MODE><<<grid, kThreads, 0, h->stream>>>(x, b, xo, n, lv.N, tau, hh, ww, m, tc)
+  stmg::k_space_op<T, D, Q, ADJ, MODE><<<grid, kThreads, 0, h->stream>>>(x, b, xo, n, lv.N, tau, hh, hinv, ww, m, tc)
   if (adj) {
     if (mode == 0) STMG_SPACE_OP(true, 0); else if (mode == 1) STMG_SPACE_OP(true, 1); else STMG_SPACE_OP(true, 2);
   } else {

@@ -29,13 +29,16 @@ struct TimeCoef {
 // K_h = sum_a K_1 (axis a) (x)_{b != a} M_1.  Nodes outside [0, n) are zero
 // (homogeneous Dirichlet).
 // ---------------------------------------------------------------------------
+// The weights are formed from h and 1/h (both passed by the host, exact since
+// h = 1/(n+1) is a power of two) without a division on the device: an FP64
+// division costs as much as a dozen FMAs on the FP64 pipe.
 template <typename T, int D>
 struct Stencil {
   // weights for offset o in {-1,0,1}: index o + 1
   T m1[3], k1[3];
-  __device__ __forceinline__ Stencil(T h) {
-    m1[0] = h / T(6); m1[1] = T(4) * h / T(6); m1[2] = h / T(6);
-    k1[0] = T(-1) / h; k1[1] = T(2) / h; k1[2] = T(-1) / h;
+  __device__ __forceinline__ Stencil(T h, T hinv) {
+    m1[0] = h * T(1.0 / 6.0); m1[1] = h * T(2.0 / 3.0); m1[2] = m1[0];
+    k1[0] = -hinv; k1[1] = T(2) * hinv; k1[2] = -hinv;
   }
 };
 
@@ -104,8 +107,27 @@ __device__ __forceinline__ void apply_mk(const Stencil<T, D>& S, int n, int ix, 
 // Only M_h (for the time-coupling trace term and the initial value).
 template <typename T, int D, typename Get>
 __device__ __forceinline__ T apply_m(const Stencil<T, D>& S, int n, int ix, int iy, int iz, Get get) {
-  T mu, ku;
-  apply_mk<T, D>(S, n, ix, iy, iz, get, mu, ku);
+  T mu = T(0);
+#pragma unroll
+  for (int oz = (D >= 3 ? -1 : 0); oz <= (D >= 3 ? 1 : 0); ++oz) {
+    const int z = iz + oz;
+    if (z < 0 || z >= (D >= 3 ? n : 1)) continue;
+    T am = T(0);
+#pragma unroll
+    for (int oy = (D >= 2 ? -1 : 0); oy <= (D >= 2 ? 1 : 0); ++oy) {
+      const int y = iy + oy;
+      if (y < 0 || y >= (D >= 2 ? n : 1)) continue;
+      T a = T(0);
+#pragma unroll
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int x = ix + ox;
+        if (x < 0 || x >= n) continue;
+        a += S.m1[ox + 1] * get(((int64_t)z * n + y) * n + x);
+      }
+      am += (D >= 2 ? S.m1[oy + 1] : T(1)) * a;
+    }
+    mu += (D >= 3 ? S.m1[oz + 1] : T(1)) * am;
+  }
   return mu;
 }
 
@@ -128,14 +150,14 @@ __device__ __forceinline__ void node_coords(int64_t j, int n, int D, int& ix, in
 template <typename T, int D, int Q, bool ADJ>
 __global__ void k_residual(const T* __restrict__ f, const T* __restrict__ u,
                            const T* __restrict__ u0, T* __restrict__ r,
-                           int n, int N, int s0, T tau, T h, TimeCoef<T, Q> tc) {
+                           int n, int N, int s0, T tau, T h, T hinv, TimeCoef<T, Q> tc) {
   const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = s0 + blockIdx.y;
   if (j >= Nx || s >= N) return;
   int ix, iy, iz;
   node_coords(j, n, D, ix, iy, iz);
-  Stencil<T, D> S(h);
+  Stencil<T, D> S(h, hinv);
   T mu[Q], ku[Q];
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
@@ -191,7 +213,7 @@ constexpr int kResTY = 8;
 template <typename T, int Q, bool ADJ>
 __global__ void __launch_bounds__(kResTX * kResTY) k_residual2d(const T* __restrict__ f, const T* __restrict__ u,
                                                                 const T* __restrict__ u0, T* __restrict__ r,
-                                                                int n, int N, int s0, T tau, T h,
+                                                                int n, int N, int s0, T tau, T h, T hinv,
                                                                 TimeCoef<T, Q> tc) {
   constexpr int HX = kResTX + 2, HY = kResTY + 2;
   __shared__ T su[Q + 1][HY][HX];        // fields 0..Q-1: u_s; field Q: coupling trace
@@ -225,8 +247,8 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_residual2d(const T* __restr
     su[Q][hy][hx] = t;
   }
   __syncthreads();
-  const T m0 = h / T(6), m1 = T(4) * h / T(6);
-  const T k0 = T(-1) / h, k1 = T(2) / h;
+  const T m0 = h * T(1.0 / 6.0), m1 = h * T(2.0 / 3.0);
+  const T k0 = -hinv, k1 = T(2) * hinv;
   // x passes on every staged row
   for (int i = tid; i < HY * kResTX; i += kResTX * kResTY) {
     const int hy = i / kResTX, tx = i - hy * kResTX;
@@ -788,7 +810,7 @@ __global__ void k_rhs(const T* __restrict__ f, const T* __restrict__ u, const T*
   if (j >= Nx || s >= N) return;
   int ix, iy, iz;
   node_coords(j, n, D, ix, iy, iz);
-  Stencil<T, D> S(h);
+  Stencil<T, D> S(h, T(0));   // M_h only
   T mt = T(0);
   const T* nb = nullptr;
   if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
@@ -847,7 +869,7 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_rhs2d(const T* __restrict__
     }
   }
   __syncthreads();
-  const T m0 = h / T(6), m1 = T(4) * h / T(6);
+  const T m0 = h * T(1.0 / 6.0), m1 = h * T(2.0 / 3.0);
   if (any) {
     for (int i = tid; i < HY * kResTX; i += kResTX * kResTY) {
       const int hy = i / kResTX, tx = i - hy * kResTX;
@@ -1008,7 +1030,7 @@ __global__ void k_ic_gradient(const T* __restrict__ lam, T* __restrict__ g, int 
   if (j >= Nx) return;
   int ix, iy, iz;
   node_coords(j, n, D, ix, iy, iz);
-  Stencil<T, D> S(h);
+  Stencil<T, D> S(h, T(0));   // M_h only
   g[j] = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) {
     T t = T(0);
 #pragma unroll
@@ -1036,7 +1058,7 @@ struct SmallMat {
 
 template <typename T, int D, int Q, bool ADJ, int MODE>
 __global__ void k_space_op(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ xo, int n,
-                           int nsteps, T tau, T h, T w, SmallMat<T, Q> Dinv, TimeCoef<T, Q> tc) {
+                           int nsteps, T tau, T h, T hinv, T w, SmallMat<T, Q> Dinv, TimeCoef<T, Q> tc) {
   const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
@@ -1047,7 +1069,7 @@ __global__ void k_space_op(const T* __restrict__ x, const T* __restrict__ b, T* 
   if (MODE != 2) {
     int ix, iy, iz;
     node_coords(j, n, D, ix, iy, iz);
-    Stencil<T, D> S(h);
+    Stencil<T, D> S(h, hinv);
     T mu[Q], ku[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
