@@ -280,8 +280,9 @@ void upload(st_handle* h, T* dst, const std::vector<double>& src) {
 }
 
 // Host FP64 block-LU factors of the per-mode line systems (see k_line_solve):
-// fac[((j*2 + w)*q*q + e)*nmodes + mode] (w = 0: L_j, w = 1: W_j^{-1}),
-// ecoef[e*nmodes + mode].
+// fac[((j*2 + w)*q*q + e)*nmodes + mode] (w = 0: L_j, w = 1: s W_j^{-1}),
+// ecoef[e*nmodes + mode] = E / s, with s = (2/Nf)^(d-1) the inverse sine-transform
+// normalisation: the backward sweep then produces s x directly.
 void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool adj, std::vector<double>& fac,
                   std::vector<double>& ecoef) {
   const int q = tm.q, qq = q * q;
@@ -294,6 +295,7 @@ void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool a
     m1[k - 1] = h / 3.0 * (2.0 + c);
     k1[k - 1] = 2.0 / h * (1.0 - c);
   }
+  const double sc = std::pow(2.0 / Nf, D - 1);
   fac.assign((size_t)n * 2 * qq * nmodes, 0.0);
   ecoef.assign((size_t)qq * nmodes, 0.0);
   std::vector<double> K(qq), Dg(qq), E(qq), W(qq), Wi(qq), L(qq), tmp(qq);
@@ -344,7 +346,7 @@ void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool a
         Dg[k * q + l] = lamM * (4.0 * h / 6.0) * K[k * q + l] + mt * (lamM * 2.0 / h + lamK * 4.0 * h / 6.0);
         E[k * q + l] = lamM * (h / 6.0) * K[k * q + l] + mt * (-lamM / h + lamK * h / 6.0);
       }
-    for (int e = 0; e < qq; ++e) ecoef[(size_t)e * nmodes + mode] = E[e];
+    for (int e = 0; e < qq; ++e) ecoef[(size_t)e * nmodes + mode] = E[e] / sc;
     W = Dg;
     for (int j = 0; j < n; ++j) {
       if (j > 0) {
@@ -367,7 +369,7 @@ void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool a
       inv(W, Wi);
       for (int e = 0; e < qq; ++e) {
         fac[(((size_t)j * 2 + 0) * qq + e) * nmodes + mode] = L[e];
-        fac[(((size_t)j * 2 + 1) * qq + e) * nmodes + mode] = Wi[e];
+        fac[(((size_t)j * 2 + 1) * qq + e) * nmodes + mode] = sc * Wi[e];
       }
     }
   }
@@ -465,14 +467,14 @@ void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, cons
 }
 
 template <typename T, int D, int Q>
-void launch_line_solve_t(st_handle* h, Level& lv, bool adj, T* data, int ns, T scale) {
+void launch_line_solve_t(st_handle* h, Level& lv, bool adj, T* data, int ns) {
   Tables<T>& tb = tables<T>(lv);
   const int64_t nmodes = lv.Nx / lv.n;
   dim3 grid(blocks_for(nmodes, 128), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
     stmg::k_line_solve<T, Q><<<grid, 128, 0, h->stream>>>(data + (int64_t)c * Q * lv.Nx, lv.n, nmodes, grid.y,
-                                                          tb.fac[adj ? 1 : 0], tb.ecoef[adj ? 1 : 0], scale);
+                                                          tb.fac[adj ? 1 : 0], tb.ecoef[adj ? 1 : 0]);
   }
 }
 
@@ -595,12 +597,12 @@ void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T
 }
 
 template <typename T>
-void line_solve(st_handle* h, Level& lv, bool adj, T* data, int ns, T scale) {
+void line_solve(st_handle* h, Level& lv, bool adj, T* data, int ns) {
   const double nodes = (double)ns * lv.Nx;
   const double Q = h->q;
   // per node: forward Q^2 FMA, backward 2 Q^2 FMA; bytes: read + write (one pass each)
   Prof pr(h, ST_K_LINESOLVE, sizeof(T) * 2.0 * nodes * Q, nodes * 6.0 * Q * Q, 1, level_of(h, lv));
-  STMG_DISPATCH(launch_line_solve_t, h, lv, adj, data, ns, scale);
+  STMG_DISPATCH(launch_line_solve_t, h, lv, adj, data, ns);
 }
 
 template <typename T>
@@ -775,8 +777,7 @@ void block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d, int s0, in
   const int64_t cnt = (int64_t)ns * h->q * lv.Nx;
   if (r != d) copy<T>(h, d + off, r + off, cnt);
   dst_axes<T>(h, lv, d + off, ns, h->d - 1);
-  const T scale = (T)std::pow(2.0 / (lv.n + 1), h->d - 1);
-  line_solve<T>(h, lv, adj, d + off, ns, scale);
+  line_solve<T>(h, lv, adj, d + off, ns);   // includes the inverse-transform scale (2/Nf)^(d-1)
   dst_axes<T>(h, lv, d + off, ns, h->d - 1);
 }
 

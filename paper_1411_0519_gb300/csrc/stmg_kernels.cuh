@@ -494,7 +494,7 @@ struct DstRegLayout {
   static constexpr int NEED = (H + H / P) > (P * (G + 1)) ? (H + H / P) : (P * (G + 1));
   static constexpr int BS = ((NEED + 31) / 32) * 32 + 16;
   static constexpr int RS = ((2 * BS + 31) / 32) * 32 + G;
-  static constexpr int TAB = 2 * H + 4 * H + NF;   // sin e/o, two twiddle tables (re, im), cos/sin half
+  static constexpr int TAB = 4 * H + 4 * H + NF;   // sin +- 1/2 e/o, two twiddle tables (re, im), cos/sin half
 };
 
 // Per-CTA tables of the register sine transform (see DstRegLayout).
@@ -502,25 +502,30 @@ template <typename T, int LP, int LG>
 __device__ __forceinline__ void dst_reg_stage_tables(T* sm, DstTables<T> tb) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int P = Lay::P, G = Lay::G, H = Lay::H, NF = Lay::NF;
-  T* se = sm;
-  T* so = se + H;
-  T* t1r = so + H;
+  T* sep = sm;                // sin(2m pi / Nf) + 1/2
+  T* sem = sep + H;           // sin(2m pi / Nf) - 1/2
+  T* sop = sem + H;           // sin((2m+1) pi / Nf) + 1/2
+  T* som = sop + H;           // sin((2m+1) pi / Nf) - 1/2
+  T* t1r = som + H;
   T* t1i = t1r + H;
-  T* t3r = t1i + H;
+  T* t3r = t1i + H;           // W_Nf^{g P + c} / 2 at c G + g (the split's factor 1/2 folded in)
   T* t3i = t3r + H;
   T* wc = t3i + H;
   T* ws = wc + NF / 2;
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
-    se[i] = tb.sinp[2 * i];
-    so[i] = tb.sinp[2 * i + 1];
+    const T s0 = tb.sinp[2 * i], s1 = tb.sinp[2 * i + 1];
+    sep[i] = s0 + T(0.5);
+    sem[i] = s0 - T(0.5);
+    sop[i] = s1 + T(0.5);
+    som[i] = s1 - T(0.5);
     const int k1 = i / G, gg = i - k1 * G;                 // t1 entry (k1, g)
     const int j1 = (2 * gg * k1) & (NF - 1);               // W_H^{g k1} = e^{-2 pi i (2 g k1) / Nf}
     t1r[i] = tb.twc[j1];
     t1i[i] = -tb.tws[j1];
-    const int c = i / G, g3 = i - c * G;                   // t3 entry (c, g): W_Nf^{g P + c}
+    const int c = i / G, g3 = i - c * G;                   // t3 entry (c, g): W_Nf^{g P + c} / 2
     const int j3 = g3 * P + c;
-    t3r[i] = tb.twc[j3];
-    t3i[i] = -tb.tws[j3];
+    t3r[i] = T(0.5) * tb.twc[j3];
+    t3i[i] = T(-0.5) * tb.tws[j3];
   }
   for (int i = threadIdx.x; i < NF / 2; i += blockDim.x) {
     wc[i] = tb.twc[i];
@@ -531,14 +536,19 @@ __device__ __forceinline__ void dst_reg_stage_tables(T* sm, DstTables<T> tb) {
 // Sine transform of one row by the G threads of a group (g = rank in the
 // group).  On entry bre[k] = x_{2k}, bim[k] = x_{2k+1} (x_0 = 0); on exit
 // bre[k] = X_{2k}, bim[k] = X_{2k+1}.  Only __syncwarp is used: a group never
-// spans two warps.
+// spans two warps.  The pre-processing is written as
+// y_j = x_j (s_j + 1/2) + x_{Nf-j} (s_j - 1/2) and the even/odd split as
+// Y_k = 1/2 [A + (w_i - i w_r) B], A = Z_k + conj Z_{H-k}, B = Z_k - conj Z_{H-k},
+// W^k = w_r + i w_i, to save FP64 instructions.
 template <typename T, int LP, int LG>
 __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int P = Lay::P, G = Lay::G, H = Lay::H, NF = Lay::NF, LNF = LP + LG + 1;
-  const T* se = sm;
-  const T* so = se + H;
-  const T* t1r = so + H;
+  const T* sep = sm;
+  const T* sem = sep + H;
+  const T* sop = sem + H;
+  const T* som = sop + H;
+  const T* t1r = som + H;
   const T* t1i = t1r + H;
   const T* t3r = t1i + H;
   const T* t3i = t3r + H;
@@ -551,19 +561,24 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
     const int m = g + G * p;
     const T a0 = bre[m], b0 = bre[(H - m) & (H - 1)];      // x_{2m}, x_{Nf - 2m}
     const T a1 = bim[m], b1 = bim[H - 1 - m];              // x_{2m+1}, x_{Nf - 2m - 1}
-    re[p] = (m == 0) ? T(0) : se[m] * (a0 + b0) + T(0.5) * (a0 - b0);
-    im[p] = so[m] * (a1 + b1) + T(0.5) * (a1 - b1);
+    re[p] = (m == 0) ? T(0) : a0 * sep[m] + b0 * sem[m];
+    im[p] = a1 * sop[m] + b1 * som[m];
   }
   __syncwarp();
   // 2. P-point DFTs over p
   fft_dif_reg<T, P>(re, im, wc, ws, LNF);
-  // 3. twiddle and exchange at k1 (G + 1) + g
+  // 3. twiddle and exchange at k1 (G + 1) + g (k1 = 0 has the twiddle 1)
 #pragma unroll
   for (int pos = 0; pos < P; ++pos) {
     const int k1 = brevc(pos, LP);
-    const T c = t1r[k1 * G + g], sn = t1i[k1 * G + g];     // W = c + i sn
-    bre[k1 * (G + 1) + g] = re[pos] * c - im[pos] * sn;
-    bim[k1 * (G + 1) + g] = re[pos] * sn + im[pos] * c;
+    if (k1 == 0) {
+      bre[g] = re[pos];
+      bim[g] = im[pos];
+    } else {
+      const T c = t1r[k1 * G + g], sn = t1i[k1 * G + g];   // W = c + i sn
+      bre[k1 * (G + 1) + g] = re[pos] * c - im[pos] * sn;
+      bim[k1 * (G + 1) + g] = re[pos] * sn + im[pos] * c;
+    }
   }
   __syncwarp();
   // 4. G-point DFTs over g for k1 = g + G i (results kept in registers)
@@ -604,12 +619,12 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
     const int k = g * P + c;
     const int kc = (H - k) & (H - 1);
     const T zkr = bre[k + (k >> LP)], zki = bim[k + (k >> LP)];
-    const T zcr = bre[kc + (kc >> LP)], zci = -bim[kc + (kc >> LP)];
-    const T er = T(0.5) * (zkr + zcr), ei = T(0.5) * (zki + zci);
-    const T orr = T(0.5) * (zki - zci), oi = T(-0.5) * (zkr - zcr);
-    const T wr = t3r[c * G + g], wi = t3i[c * G + g];     // W_Nf^k = wr + i wi
-    Rk[c] = er + (wr * orr - wi * oi);
-    Ik[c] = -(ei + (wr * oi + wi * orr));
+    const T zcr = bre[kc + (kc >> LP)], zcm = bim[kc + (kc >> LP)];   // Z_{H-k} = zcr + i zcm
+    const T ar = zkr + zcr, ai = zki - zcm;                          // A = Z_k + conj Z_{H-k}
+    const T br = zkr - zcr, bi = zki + zcm;                          // B = Z_k - conj Z_{H-k}
+    const T hr = t3r[c * G + g], hi = t3i[c * G + g];                // W^k / 2
+    Rk[c] = T(0.5) * ar + (hi * br + hr * bi);                       // Re Y_k
+    Ik[c] = (hr * br - hi * bi) - T(0.5) * ai;                       // -Im Y_k
   }
   __syncwarp();
   T loc = T(0);
@@ -662,12 +677,14 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int 
   const int rr = tid >> LG, g = tid & (Lay::G - 1);
   dst_reg_row<T, LP, LG>(rows + rr * RS, rows + rr * RS + BS, g, sm);   // rows >= rcount are not stored
   __syncthreads();
+  const bool unit = scale == T(1);
   for (int r = warp; r < rcount; r += nw) {
     T* dst = data + (r0 + r) * n;
     const T* br = rows + r * RS;
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
-      dst[c] = scale * br[(j & 1) * BS + (j >> 1)];
+      const T v = br[(j & 1) * BS + (j >> 1)];
+      dst[c] = unit ? v : scale * v;
     }
   }
 }
@@ -729,11 +746,12 @@ __global__ void __launch_bounds__(256) k_dst_cols(T* __restrict__ data, int n, i
 // so every access along the sweep is coalesced.  Table layout:
 //   fac[((j * 2 + w) * Q*Q + e) * nmodes + mode], w = 0: L_j, w = 1: W_j^{-1}
 //   ecoef[e * nmodes + mode]
-// The result is multiplied by `scale` (inverse sine-transform normalisation).
+// The tables carry the inverse sine-transform normalisation s: fac holds
+// s W_j^{-1} and ecoef E / s, so the sweep returns s x without a multiply.
 // ---------------------------------------------------------------------------
 template <typename T, int Q>
 __global__ void k_line_solve(T* __restrict__ data, int n, int64_t nmodes, int nsteps,
-                             const T* __restrict__ fac, const T* __restrict__ ecoef, T scale) {
+                             const T* __restrict__ fac, const T* __restrict__ ecoef) {
   const int64_t mode = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   if (mode >= nmodes || s >= nsteps) return;
@@ -765,7 +783,7 @@ __global__ void k_line_solve(T* __restrict__ data, int n, int64_t nmodes, int ns
   T E[QQ];
 #pragma unroll
   for (int e = 0; e < QQ; ++e) E[e] = ecoef[(int64_t)e * nmodes + mode];
-  // backward substitution; x_{j+1} kept unscaled in registers
+  // backward substitution (on s x)
   T xn[Q];
   for (int j = n - 1; j >= 0; --j) {
     T t[Q];
@@ -789,7 +807,7 @@ __global__ void k_line_solve(T* __restrict__ data, int n, int64_t nmodes, int ns
       xn[k] = acc;
     }
 #pragma unroll
-    for (int l = 0; l < Q; ++l) base[(int64_t)l * Nx + (int64_t)j * nmodes] = scale * xn[l];
+    for (int l = 0; l < Q; ++l) base[(int64_t)l * Nx + (int64_t)j * nmodes] = xn[l];
   }
 }
 
