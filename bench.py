@@ -160,10 +160,11 @@ def time_solves(torch, solver, f, u0, u, steps, warmup, barrier):
 
 
 def traffic_table():
-    """DRAM bytes per row of the finest-level sine-transform kernels, from the
-    ncu captures summarised in profiles/ (measured on heat2d_255_n256 and scaled
-    by rows; the captures name the kernel they were taken on)."""
-    path = os.path.join(ROOT, "profiles", "traffic_per_row.json")
+    """Measured DRAM bytes per unknown of finest-level kernels, from the ncu
+    captures summarised in profiles/ (taken on a smaller case of the same
+    kernel and scaled by unknowns; each entry names the kernel, the case and
+    the summary it comes from)."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_dof.json")
     if not os.path.exists(path):
         return {}
     with open(path) as fh:
@@ -194,14 +195,11 @@ def roofline(solver, prof, fp32, pk, w):
         rf = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
               "frac": round(f_hbm, 4), "peak_src": pk["src"] + " (MEASURED_PEAKS.json hbm_gbs)"}
     launches = max(1, v["launches"])
-    rows = w["N"] * (w["p_t"] + 1) * w["n"] ** (w["d"] - 1)
-    name = None
-    traffic = None
-    if dom == "dst" and w["d"] == 2 and w["n"] + 1 == 256:
-        name = "k_dst_rows_reg<%s,4,3>" % ("float" if fp32 else "double")
-        t = traffic_table().get(name)
-        if t is not None:
-            traffic = t["bytes_per_row"] * rows
+    ndof = w["N"] * (w["p_t"] + 1) * w["n"] ** w["d"]
+    key = "%s/%s/d%d_n%d_q%d" % (dom, "fp32" if fp32 else "fp64", w["d"], w["n"], w["p_t"] + 1)
+    t = traffic_table().get(key)
+    name = t["kernel"] if t else None
+    traffic = t["bytes_per_dof"] * ndof if t else None
     rf.update({"kernel": name or dom, "level": "finest", "launches": v["launches"],
                "avg_launch_ms": round(v["ms"] / launches, 4), "share_of_class_total": round(
                    classes[dom]["ms"] / total_ms, 3),

@@ -120,7 +120,11 @@ int st_residual(st_handle* h, const double* f, const double* u0_ic, const double
 
 /* One V-cycle (gamma = 1, Section 2) on L u = f + IC for the finest level, in
  * place on u.  With ST_MIXED this is one refinement step: FP64 residual,
- * inner_cycles FP32 V-cycles on the scaled residual, FP64 update. */
+ * inner_cycles FP32 V-cycles on the scaled residual, FP64 update.
+ * With ST_SMOOTH_EXACT the cycle runs in the basis that diagonalises the
+ * spatial matrices along the first dim-1 axes (sine transform, Section 3.1):
+ * f, u0_ic and u are transformed on entry and u is transformed back; the
+ * iterates are the same as on nodes up to rounding. */
 int st_vcycle(st_handle* h, double* u, const double* f, const double* u0_ic);
 
 /* Solve L u = f + IC to ||r|| <= rtol ||r_0|| by repeated V-cycles (Section 2).
@@ -139,7 +143,10 @@ int st_adjoint_solve(st_handle* h, const double* g, double* lambda, double* grad
 
 /* ---- step-level entry points (one step of the cycle on one level) ----
  * adjoint != 0 selects the transposed operator.  Vectors have the level's
- * layout (N_L, q, n_L^d). */
+ * layout (N_L, q, n_L^d), on nodes.  With ST_SMOOTH_EXACT each call
+ * transforms its inputs to the basis of the cycle, runs the same kernels as
+ * st_solve and transforms the result back; it uses the level's internal
+ * buffers as scratch (calls on one handle must not overlap). */
 
 /* r = f - L_L u (no IC term) or f - L_L^T u. */
 int st_level_residual(st_handle* h, int L, int adjoint, const double* f, const double* u, double* r);
@@ -169,12 +176,14 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
  * Kernel classes for st_profile_stop: */
 #define ST_K_RESIDUAL   0   /* residual (forward / transposed) */
 #define ST_K_DST        1   /* batched sine transform along one axis */
-#define ST_K_LINESOLVE  2   /* block-tridiagonal line solve per sine mode */
+#define ST_K_LINESOLVE  2   /* fused smoothing step: coupling term, block-tridiagonal
+                               line solve per sine mode, damping */
 #define ST_K_RESTRICT   3
 #define ST_K_PROLONG    4
 #define ST_K_NORM       5   /* both reduction stages */
 #define ST_K_VECTOR     6   /* axpy, casts, copies, memsets */
-#define ST_K_RHS        7   /* smoother right-hand side f - B u_prev */
+#define ST_K_RHS        7   /* separate smoother right-hand side (no longer launched:
+                               fused into ST_K_LINESOLVE; the value is kept) */
 #define ST_K_SPACEMG    8   /* spatial V-cycle of the inexact block inverse */
 #define ST_K_COUNT      9
 

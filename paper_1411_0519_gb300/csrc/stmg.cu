@@ -14,6 +14,7 @@
 
 #include "stmg.h"
 #include "stmg_kernels.cuh"
+#include "stmg_modal.cuh"
 
 using stmg::TimeCoef;
 
@@ -139,6 +140,10 @@ struct Tables {
   T* tws = nullptr;   // sin(2 pi k / Nf)
   T* fac[2] = {nullptr, nullptr};    // line-solve LU factors (forward, adjoint)
   T* ecoef[2] = {nullptr, nullptr};  // off-diagonal blocks E per mode
+  T* alpha = nullptr;  // per mode: product of the 1D mass eigenvalues over the transformed axes
+  T* beta = nullptr;   // per mode: the matching stiffness combination
+  T* ra = nullptr;     // full-coarsening pair weights to level L-1: (1 + c_k) / 2
+  T* rb = nullptr;     //                                             -(1 - c_k) / 2
 };
 
 template <typename T>
@@ -191,6 +196,7 @@ struct st_handle {
   double* coarse64_f = nullptr;
   double* coarse64_r = nullptr;
   double* r64 = nullptr;         // mixed precision: finest FP64 residual
+  double* u0m = nullptr;         // transformed initial value (mixed basis)
   std::string err;
   // kernel timing
   bool prof = false;
@@ -279,12 +285,12 @@ void upload(st_handle* h, T* dst, const std::vector<double>& src) {
   check(h, cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice), "upload table");
 }
 
-// Host FP64 block-LU factors of the per-mode line systems (see k_line_solve):
-// fac[((j*2 + w)*q*q + e)*nmodes + mode] (w = 0: L_j, w = 1: s W_j^{-1}),
-// ecoef[e*nmodes + mode] = E / s, with s = (2/Nf)^(d-1) the inverse sine-transform
-// normalisation: the backward sweep then produces s x directly.
+// Host FP64 block-LU factors of the per-mode line systems (see k_msmooth):
+// fac[((j*2 + w)*q*q + e)*nmodes + mode] (w = 0: L_j, w = 1: W_j^{-1}),
+// ecoef[e*nmodes + mode] = E; lamM / lamK receive the per-mode coefficients
+// alpha_i, beta_i of M_h and K_h in the mixed basis.
 void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool adj, std::vector<double>& fac,
-                  std::vector<double>& ecoef) {
+                  std::vector<double>& ecoef, std::vector<double>& lamMv, std::vector<double>& lamKv) {
   const int q = tm.q, qq = q * q;
   const int Nf = n + 1;
   int64_t nmodes = 1;
@@ -295,9 +301,10 @@ void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool a
     m1[k - 1] = h / 3.0 * (2.0 + c);
     k1[k - 1] = 2.0 / h * (1.0 - c);
   }
-  const double sc = std::pow(2.0 / Nf, D - 1);
   fac.assign((size_t)n * 2 * qq * nmodes, 0.0);
   ecoef.assign((size_t)qq * nmodes, 0.0);
+  lamMv.assign((size_t)nmodes, 1.0);
+  lamKv.assign((size_t)nmodes, 0.0);
   std::vector<double> K(qq), Dg(qq), E(qq), W(qq), Wi(qq), L(qq), tmp(qq);
   for (int k = 0; k < q; ++k)
     for (int l = 0; l < q; ++l) K[k * q + l] = adj ? tm.K[l * q + k] : tm.K[k * q + l];
@@ -340,13 +347,15 @@ void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool a
       lamM = m1[ix] * m1[iy];
       lamK = k1[ix] * m1[iy] + m1[ix] * k1[iy];
     }
+    lamMv[mode] = lamM;
+    lamKv[mode] = lamK;
     for (int k = 0; k < q; ++k)
       for (int l = 0; l < q; ++l) {
         const double mt = (k == l) ? tau * tm.Mh[k] : 0.0;
         Dg[k * q + l] = lamM * (4.0 * h / 6.0) * K[k * q + l] + mt * (lamM * 2.0 / h + lamK * 4.0 * h / 6.0);
         E[k * q + l] = lamM * (h / 6.0) * K[k * q + l] + mt * (-lamM / h + lamK * h / 6.0);
       }
-    for (int e = 0; e < qq; ++e) ecoef[(size_t)e * nmodes + mode] = E[e] / sc;
+    for (int e = 0; e < qq; ++e) ecoef[(size_t)e * nmodes + mode] = E[e];
     W = Dg;
     for (int j = 0; j < n; ++j) {
       if (j > 0) {
@@ -369,7 +378,7 @@ void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool a
       inv(W, Wi);
       for (int e = 0; e < qq; ++e) {
         fac[(((size_t)j * 2 + 0) * qq + e) * nmodes + mode] = L[e];
-        fac[(((size_t)j * 2 + 1) * qq + e) * nmodes + mode] = sc * Wi[e];
+        fac[(((size_t)j * 2 + 1) * qq + e) * nmodes + mode] = Wi[e];
       }
     }
   }
@@ -391,12 +400,32 @@ void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
   upload(h, tb.twc, tc);
   upload(h, tb.tws, ts);
   for (int adj = 0; adj < 2; ++adj) {
-    std::vector<double> fac, ec;
-    line_factors(h->tm, h->d, n, lv.h, lv.tau, adj != 0, fac, ec);
+    std::vector<double> fac, ec, lm, lk;
+    line_factors(h->tm, h->d, n, lv.h, lv.tau, adj != 0, fac, ec, lm, lk);
     tb.fac[adj] = dalloc<T>(h, fac.size());
     tb.ecoef[adj] = dalloc<T>(h, ec.size());
     upload(h, tb.fac[adj], fac);
     upload(h, tb.ecoef[adj], ec);
+    if (adj == 0) {
+      tb.alpha = dalloc<T>(h, lm.size());
+      tb.beta = dalloc<T>(h, lk.size());
+      upload(h, tb.alpha, lm);
+      upload(h, tb.beta, lk);
+    }
+  }
+  if (lv.coarsen_full) {
+    // coarse mode k (k = 1..nc) pairs with fine modes k and Nf - k, c_k = cos(k pi / Nf)
+    const int nc = (n - 1) / 2;
+    std::vector<double> a(std::max(nc, 1)), b(std::max(nc, 1));
+    for (int k = 1; k <= nc; ++k) {
+      const double c = std::cos(k * M_PI / Nf);
+      a[k - 1] = 0.5 * (1.0 + c);
+      b[k - 1] = -0.5 * (1.0 - c);
+    }
+    tb.ra = dalloc<T>(h, a.size());
+    tb.rb = dalloc<T>(h, b.size());
+    upload(h, tb.ra, a);
+    upload(h, tb.rb, b);
   }
 }
 
@@ -467,61 +496,77 @@ void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, cons
 }
 
 template <typename T, int D, int Q>
-void launch_line_solve_t(st_handle* h, Level& lv, bool adj, T* data, int ns) {
-  Tables<T>& tb = tables<T>(lv);
-  const int64_t nmodes = lv.Nx / lv.n;
-  dim3 grid(blocks_for(nmodes, 128), 1);
-  for (int c = 0; c < ns; c += 65535) {
-    grid.y = std::min(65535, ns - c);
-    stmg::k_line_solve<T, Q><<<grid, 128, 0, h->stream>>>(data + (int64_t)c * Q * lv.Nx, lv.n, nmodes, grid.y,
-                                                          tb.fac[adj ? 1 : 0], tb.ecoef[adj ? 1 : 0]);
-  }
-}
-
-template <typename T, int D, int Q>
-void launch_rhs_t(st_handle* h, const Level& lv, bool adj, const T* f, const T* u, const T* u0, T* g, int s0,
-                  int ns) {
+void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0,
+                        int ns) {
   auto tc = to_coef<T, Q>(h->tm);
-  if (D == 2) {
-    dim3 block(stmg::kResTX, stmg::kResTY);
-    dim3 grid((lv.n + stmg::kResTX - 1) / stmg::kResTX, (lv.n + stmg::kResTY - 1) / stmg::kResTY, 1);
-    for (int c = 0; c < ns; c += 65535) {
-      grid.z = std::min(65535, ns - c);
-      if (adj)
-        stmg::k_rhs2d<T, Q, true><<<grid, block, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
-      else
-        stmg::k_rhs2d<T, Q, false><<<grid, block, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
-    }
-    return;
-  }
-  dim3 grid(blocks_for(lv.Nx), 1);
+  Tables<T>& tb = tables<T>(lv);
+  const int nm = (int)(lv.Nx / lv.n);
+  const int nch = (lv.n + stmg::kMResChunk - 1) / stmg::kMResChunk;
+  dim3 grid(blocks_for((int64_t)nm * nch), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
     if (adj)
-      stmg::k_rhs<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
+      stmg::k_mresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(
+          f, u, u0, r, lv.n, nm, lv.N, s0 + c, (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), tb.alpha, tb.beta, tc);
     else
-      stmg::k_rhs<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, g, lv.n, lv.N, s0 + c, (T)lv.h, tc);
+      stmg::k_mresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(
+          f, u, u0, r, lv.n, nm, lv.N, s0 + c, (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), tb.alpha, tb.beta, tc);
   }
 }
 
+constexpr int kSmoothThreads = 128;
+
 template <typename T, int D, int Q>
-void launch_restrict_t(st_handle* h, const Level& fine, const Level& coarse, const T* r, T* fc) {
+void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out,
+                      int s0, int ns) {
+  auto tc = to_coef<T, Q>(h->tm);
+  Tables<T>& tb = tables<T>(lv);
+  const int nm = (int)(lv.Nx / lv.n);
+  const T* fac = tb.fac[adj ? 1 : 0];
+  const T* ec = tb.ecoef[adj ? 1 : 0];
+  const T w = (T)h->opt.omega;
+  dim3 grid(blocks_for(nm, kSmoothThreads), 1);
+  for (int c = 0; c < ns; c += 65535) {
+    grid.y = std::min(65535, ns - c);
+#define STMG_MSMOOTH(ADJ, DAMP)                                                                                  \
+  stmg::k_msmooth<T, Q, ADJ, DAMP><<<grid, kSmoothThreads, 0, h->stream>>>(f, u, u0, out, lv.n, nm, lv.N, s0 + c, \
+                                                                           (T)lv.h, w, tb.alpha, fac, ec, tc)
+    if (adj) {
+      if (damp) STMG_MSMOOTH(true, true); else STMG_MSMOOTH(true, false);
+    } else {
+      if (damp) STMG_MSMOOTH(false, true); else STMG_MSMOOTH(false, false);
+    }
+#undef STMG_MSMOOTH
+  }
+}
+
+// Restriction / prolongation between levels L and L-1.  modal: vectors in the
+// mixed basis (full coarsening pairs sine modes); otherwise on nodes.  Semi
+// coarsening is the identity in space and the same kernel serves both.
+template <typename T, int D, int Q>
+void launch_restrict_t(st_handle* h, Level& fine, const Level& coarse, bool modal, const T* r, T* fc) {
   auto tc = to_coef<T, Q>(h->tm);
   dim3 grid(blocks_for(coarse.Nx), coarse.N);
-  if (fine.coarsen_full)
-    stmg::k_restrict<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
-  else
+  if (!fine.coarsen_full)
     stmg::k_restrict<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
+  else if (modal)
+    stmg::k_mrestrict<T, D, Q><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N,
+                                                                  tables<T>(fine).ra, tables<T>(fine).rb, tc);
+  else
+    stmg::k_restrict<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
 }
 
 template <typename T, int D, int Q>
-void launch_prolong_t(st_handle* h, const Level& fine, const Level& coarse, const T* ec, T* uf) {
+void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, bool modal, const T* ec, T* uf) {
   auto tc = to_coef<T, Q>(h->tm);
   dim3 grid(blocks_for(fine.Nx), fine.N);
-  if (fine.coarsen_full)
-    stmg::k_prolong<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
-  else
+  if (!fine.coarsen_full)
     stmg::k_prolong<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
+  else if (modal)
+    stmg::k_mprolong<T, D, Q><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N,
+                                                                 tables<T>(fine).ra, tables<T>(fine).rb, tc);
+  else
+    stmg::k_prolong<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
 }
 
 template <typename T, int D, int Q>
@@ -596,42 +641,51 @@ void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T
   STMG_DISPATCH(launch_residual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
+// Residual in the mixed basis (exact block inverse), steps [s0, s0 + ns).
 template <typename T>
-void line_solve(st_handle* h, Level& lv, bool adj, T* data, int ns) {
-  const double nodes = (double)ns * lv.Nx;
-  const double Q = h->q;
-  // per node: forward Q^2 FMA, backward 2 Q^2 FMA; bytes: read + write (one pass each)
-  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * 2.0 * nodes * Q, nodes * 6.0 * Q * Q, 1, level_of(h, lv));
-  STMG_DISPATCH(launch_line_solve_t, h, lv, adj, data, ns);
+void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0 = 0,
+               int ns = -1) {
+  if (ns < 0) ns = lv.N;
+  const double Q = h->q, nodes = (double)ns * lv.Nx;
+  // per node: Q neighbour sums, 2 Q^2 stencil FMA, trace Q FMA + M_1 (4), Q coupling FMA
+  Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)),
+          nodes * (4.0 * Q * Q + 5.0 * Q + 4.0), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
+}
+
+// Fused damped block-Jacobi step with the exact block inverse in the mixed
+// basis (k_msmooth): out = (1 - w) u + w A^{-1}(f - B u_prev) (damp), or
+// out = A^{-1}(f - B u_prev) (no damping), steps [s0, s0 + ns); u may be null.
+template <typename T>
+void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out, int s0 = 0,
+             int ns = -1) {
+  if (ns < 0) ns = lv.N;
+  const double Q = h->q, nodes = (double)ns * lv.Nx;
+  const double passes = 2.0 + ((damp && u) ? 1.0 : 0.0);   // read f (and u), write out
+  // per node: trace 2Q + 4, coupling 2Q, forward 2Q^2, backward 4Q^2, damping 3Q
+  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * (6.0 * Q * Q + 7.0 * Q + 4.0), 1,
+          level_of(h, lv));
+  STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, f, u, u0, out, s0, ns);
 }
 
 template <typename T>
-void rhs(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* g) {
-  const double nodes = (double)lv.N * lv.Nx;
-  const int D = h->d, Q = h->q;
-  // per node: trace Q FMA, M_h stencil 3D FMA, output Q FMA; bytes: read f, u (neighbour step), write g
-  Prof pr(h, ST_K_RHS, sizeof(T) * 3.0 * nodes * Q, 2.0 * nodes * (2.0 * Q + 3.0 * D), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_rhs_t, h, lv, adj, f, u, u0, g, 0, lv.N);
-}
-
-template <typename T>
-void restrict_to(st_handle* h, int L, const T* r, T* fc) {
+void restrict_to(st_handle* h, int L, bool modal, const T* r, T* fc) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
-  Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_),
-          2.0 * cn * (2.0 * (fine.coarsen_full ? std::pow(3.0, h->d) : 1.0) + 2.0 * h->q), 1, L);
-  STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
+  const double ns = fine.coarsen_full ? (modal ? std::pow(2.0, h->d - 1) * 3.0 : std::pow(3.0, h->d)) : 1.0;
+  Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * h->q), 1, L);
+  STMG_DISPATCH(launch_restrict_t, h, fine, coarse, modal, r, fc);
 }
 
 template <typename T>
-void prolong_add(st_handle* h, int L, const T* ec, T* uf) {
+void prolong_add(st_handle* h, int L, bool modal, const T* ec, T* uf) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
-  Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_),
-          2.0 * fn_ * ((fine.coarsen_full ? std::pow(2.0, h->d) : 1.0) + h->q), 1, L);
-  STMG_DISPATCH(launch_prolong_t, h, fine, coarse, ec, uf);
+  const double ns = fine.coarsen_full ? (modal ? 2.0 : std::pow(2.0, h->d)) : 1.0;
+  Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + h->q), 1, L);
+  STMG_DISPATCH(launch_prolong_t, h, fine, coarse, modal, ec, uf);
 }
 
 template <typename T>
@@ -716,20 +770,21 @@ double dst_line_flops(int n) {
   return 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
 }
 
-// DST-I along spatial axes 0..naxes-1 of `ns` time steps of data (in place).
+// scale * DST-I along the first d-1 spatial axes of `slabs` consecutive
+// spatial fields of level lv (in place; `scale` is applied once per axis).
 template <typename T>
-void dst_axes(st_handle* h, Level& lv, T* data, int ns, int naxes) {
+void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale) {
   const int n = lv.n, Nf = n + 1;
+  const int naxes = h->d - 1;
   int logh = 0;
   while ((1 << (logh + 1)) <= Nf / 2) ++logh;
   Tables<T>& tb = tables<T>(lv);
   stmg::DstTables<T> dt{tb.sinp, tb.twc, tb.tws};
-  const int64_t slabs = (int64_t)ns * h->q;
   const int64_t nlines = slabs * lv.Nx / n;
   const double line_flops = dst_line_flops(n);
   int64_t inner = 1;
   for (int a = 0; a < naxes; ++a) {
-    const T scale = T(1);
+    const T scale = (T)axis_scale;
     Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines, 1, level_of(h, lv));
     if (a == 0 && Nf >= 64 && Nf <= 512) {
       const int thr = dst_reg_threads<T>();
@@ -767,18 +822,28 @@ void dst_axes(st_handle* h, Level& lv, T* data, int ns, int naxes) {
   }
 }
 
-// d = D^{-1} r on time steps [s0, s0 + ns) (exact block inverse, Section 3.1):
-// sine transform along the first D-1 axes, block-tridiagonal line solve along
-// the last axis per mode (with the inverse-transform scale (2/Nf)^{D-1}),
-// inverse sine transform.  r and d may be the same buffer.
+// Change of basis of `slabs` spatial fields of level lv: nodes -> mixed basis
+// (S, the unnormalised DST-I along the first d-1 axes) and back (S^{-1} =
+// (2/Nf)^{d-1} S).  No-ops in 1D.
 template <typename T>
-void block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d, int s0, int ns) {
+void to_modal(st_handle* h, Level& lv, T* data, int64_t slabs) {
+  if (h->d > 1) dst_axes<T>(h, lv, data, slabs, 1.0);
+}
+template <typename T>
+void from_modal(st_handle* h, Level& lv, T* data, int64_t slabs) {
+  if (h->d > 1) dst_axes<T>(h, lv, data, slabs, 2.0 / (lv.n + 1));
+}
+
+// d = A^{-1} r on nodes, time steps [s0, s0 + ns) (exact block inverse,
+// Section 3.1): sine transform along the first d-1 axes, one block-tridiagonal
+// solve per mode along the last axis, inverse transform.  r is overwritten
+// (transformed); r and d must differ.
+template <typename T>
+void block_solve(st_handle* h, Level& lv, bool adj, T* r, T* d, int s0, int ns) {
   const int64_t off = (int64_t)s0 * h->q * lv.Nx;
-  const int64_t cnt = (int64_t)ns * h->q * lv.Nx;
-  if (r != d) copy<T>(h, d + off, r + off, cnt);
-  dst_axes<T>(h, lv, d + off, ns, h->d - 1);
-  line_solve<T>(h, lv, adj, d + off, ns);   // includes the inverse-transform scale (2/Nf)^(d-1)
-  dst_axes<T>(h, lv, d + off, ns, h->d - 1);
+  to_modal<T>(h, lv, r + off, (int64_t)ns * h->q);
+  msmooth<T>(h, lv, adj, false, r, (const T*)nullptr, (const T*)nullptr, d, s0, ns);
+  from_modal<T>(h, lv, d + off, (int64_t)ns * h->q);
 }
 
 template <typename T>
@@ -881,10 +946,15 @@ void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) 
   if (cur != x) copy<T>(h, x, cur, (int64_t)lv.N * h->q * sl.Nx);
 }
 
-// d = D~^{-1} r, the smoother's block inverse: exact, or one spatial V-cycle.
+// The exact block inverse runs the whole cycle in the mixed basis; the
+// inexact one (spatial V-cycle per step) works on nodes.
+bool modal(const st_handle* h) { return h->opt.smoother == ST_SMOOTH_EXACT; }
+
+// d = D~^{-1} r on nodes, the smoother's block inverse: exact, or one spatial
+// V-cycle.  r and d may be the same buffer.
 template <typename T>
 void smoother_block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d) {
-  if (h->opt.smoother == ST_SMOOTH_VCYCLE) {
+  if (!modal(h)) {
     if (r == d) {
       T* x = spaces<T>(lv)[0].x;
       space_vcycle<T>(h, lv, 0, adj, x, r);
@@ -894,87 +964,136 @@ void smoother_block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d) {
     }
     return;
   }
-  block_solve<T>(h, lv, adj, r, d, 0, lv.N);
+  T* tmp = vecs<T>(lv).f;
+  copy<T>(h, tmp, r, lv.ndof);
+  block_solve<T>(h, lv, adj, tmp, d, 0, lv.N);
 }
 
-// One damped block-Jacobi step (eq. chap4_smoother), u <- u + w D^{-1}(f - L u),
-// evaluated as u <- (1 - w) u + w A^{-1} (f - B u_prev): the block inverse of
-// the block row removes A u_n, so only the rank-one time coupling is applied.
+// One damped block-Jacobi step with the inexact block inverse on nodes
+// (eq. chap4_smootherApprox): u <- u + w D~^{-1} (f - L u).
 template <typename T>
-void smooth_step(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
-  if (h->opt.smoother == ST_SMOOTH_VCYCLE) {
-    // inexact block inverse: u <- u + w D~^{-1} (f - L u) (eq. chap4_smootherApprox)
-    residual<T>(h, lv, adj, f, u, u0, work);
-    T* d = spaces<T>(lv)[0].x;
-    space_vcycle<T>(h, lv, 0, adj, d, work);
-    axpy<T>(h, u, d, (T)h->opt.omega, lv.ndof);
+void smooth_step_nodes(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
+  residual<T>(h, lv, adj, f, u, u0, work);
+  T* d = spaces<T>(lv)[0].x;
+  space_vcycle<T>(h, lv, 0, adj, d, work);
+  axpy<T>(h, u, d, (T)h->opt.omega, lv.ndof);
+}
+
+// nu damped block-Jacobi steps (eq. chap4_smoother) with the exact block
+// inverse in the mixed basis, u <- (1 - w) u + w A^{-1} (f - B u_prev) (the
+// block inverse of the block row removes A u, so only the rank-one time
+// coupling is applied).  Each step reads one buffer and writes the other
+// (Jacobi in time); the first destination is chosen so that the last step
+// lands in u.  u_zero: u holds zero on entry and is not read.
+template <typename T>
+void smooth_modal(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* tmp, int nu, bool u_zero) {
+  if (nu <= 0) {
+    if (u_zero) zero<T>(h, u, lv.ndof);
     return;
   }
-  rhs<T>(h, lv, adj, f, u, u0, work);
-  block_solve<T>(h, lv, adj, work, work, 0, lv.N);
-  axpby<T>(h, u, work, (T)(1.0 - h->opt.omega), (T)h->opt.omega, lv.ndof);
+  T* buf[2] = {u, tmp};
+  int cur = u_zero ? -1 : 0;
+  int dst = u_zero ? ((nu & 1) ? 0 : 1) : 1;
+  for (int i = 0; i < nu; ++i) {
+    msmooth<T>(h, lv, adj, true, f, cur < 0 ? (const T*)nullptr : buf[cur], u0, buf[dst]);
+    cur = dst;
+    dst = 1 - dst;
+  }
+  if (cur != 0) copy<T>(h, u, tmp, lv.ndof);
 }
 
-// Exact coarsest solve (Section 2): one step via the block inverse, several by
-// forward (adjoint: backward) substitution, in the vector's own precision.
+// Exact coarsest solve (Section 2) by forward (adjoint: backward) substitution,
+// one block inverse per step with the coupling to the step solved before.
+// Mixed basis: one fused launch per step.
 template <typename T>
-void coarsest_solve_t(st_handle* h, bool adj, T* u, const T* f, T* work) {
+void coarsest_modal(st_handle* h, bool adj, T* u, const T* f, const T* u0) {
   Level& lv = h->levels[0];
-  if (lv.N == 1) {
-    block_solve<T>(h, lv, adj, f, u, 0, 1);
-    return;
+  for (int i = 0; i < lv.N; ++i) {
+    const int s = adj ? lv.N - 1 - i : i;
+    msmooth<T>(h, lv, adj, false, f, u, u0, u, s, 1);
   }
+}
+
+// The same on nodes: residual of step s with u_s = 0, then the block inverse.
+template <typename T>
+void coarsest_nodes(st_handle* h, bool adj, T* u, const T* f, const T* u0, T* work) {
+  Level& lv = h->levels[0];
   zero<T>(h, u, lv.ndof);
   for (int i = 0; i < lv.N; ++i) {
     const int s = adj ? lv.N - 1 - i : i;
-    residual<T>(h, lv, adj, f, u, (const T*)nullptr, work, s, 1);
+    residual<T>(h, lv, adj, f, u, u0, work, s, 1);
     block_solve<T>(h, lv, adj, work, u, s, 1);
   }
 }
 
-void coarsest_solve_mixed(st_handle* h, bool adj, float* u, const float* f, float* work) {
-  (void)work;
+void coarsest_fp64(st_handle* h, bool adj, double* u, const double* f, const double* u0) {
+  if (modal(h)) coarsest_modal<double>(h, adj, u, f, u0);
+  else coarsest_nodes<double>(h, adj, u, f, u0, h->levels[0].v64.r);
+}
+
+// Mixed precision: the coarsest level is solved in FP64.
+void coarsest_mixed(st_handle* h, bool adj, float* u, const float* f) {
   Level& lv = h->levels[0];
   const int64_t n = lv.ndof;
   {
     Prof pr(h, ST_K_VECTOR, 12.0 * (double)n, 0.0);
     stmg::k_cast_up<<<blocks_for(n), kThreads, 0, h->stream>>>(h->coarse64_f, f, n);
   }
-  coarsest_solve_t<double>(h, adj, h->coarse64_u, h->coarse64_f, h->coarse64_r);
+  if (modal(h)) coarsest_modal<double>(h, adj, h->coarse64_u, h->coarse64_f, (const double*)nullptr);
+  else coarsest_nodes<double>(h, adj, h->coarse64_u, h->coarse64_f, (const double*)nullptr, h->coarse64_r);
   Prof pr(h, ST_K_VECTOR, 12.0 * (double)n, 0.0);
   stmg::k_cast_down<<<blocks_for(n), kThreads, 0, h->stream>>>(u, h->coarse64_u, 1.0, n);
 }
 
 template <typename T>
-void coarsest_solve(st_handle* h, bool adj, T* u, const T* f, T* work);
+void coarsest_solve(st_handle* h, bool adj, T* u, const T* f, const T* u0);
 template <>
-void coarsest_solve<double>(st_handle* h, bool adj, double* u, const double* f, double* work) {
-  coarsest_solve_t<double>(h, adj, u, f, work);
+void coarsest_solve<double>(st_handle* h, bool adj, double* u, const double* f, const double* u0) {
+  coarsest_fp64(h, adj, u, f, u0);
 }
 template <>
-void coarsest_solve<float>(st_handle* h, bool adj, float* u, const float* f, float* work) {
-  coarsest_solve_mixed(h, adj, u, f, work);
+void coarsest_solve<float>(st_handle* h, bool adj, float* u, const float* f, const float* u0) {
+  (void)u0;   // inner cycles of the mixed form carry no initial value
+  coarsest_mixed(h, adj, u, f);
 }
 
 // V-cycle (gamma = 1) on level L for L u = f (+ the initial-value term u0 on
-// the finest level), Section 2.
+// the finest level), Section 2.  With the exact block inverse every vector is
+// in the mixed basis.  u_zero: u holds zero on entry (coarse-grid corrections).
 template <typename T>
-void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0) {
+void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u_zero) {
   Level& lv = h->levels[L];
   T* work = vecs<T>(lv).r;
   if (L == 0) {
-    coarsest_solve<T>(h, adj, u, f, work);
+    coarsest_solve<T>(h, adj, u, f, u0);
     return;
   }
-  for (int i = 0; i < h->opt.nu1; ++i) smooth_step<T>(h, lv, adj, u, f, u0, work);
-  residual<T>(h, lv, adj, f, u, u0, work);
+  const bool md = modal(h);
+  if (md) {
+    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu1, u_zero);
+    mresidual<T>(h, lv, adj, f, u, u0, work);
+  } else {
+    if (u_zero) zero<T>(h, u, lv.ndof);
+    for (int i = 0; i < h->opt.nu1; ++i) smooth_step_nodes<T>(h, lv, adj, u, f, u0, work);
+    residual<T>(h, lv, adj, f, u, u0, work);
+  }
   Level& cl = h->levels[L - 1];
   Vecs<T>& cv = vecs<T>(cl);
-  restrict_to<T>(h, L, work, cv.f);
-  zero<T>(h, cv.u, cl.ndof);
-  vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr);
-  prolong_add<T>(h, L, cv.u, u);
-  for (int i = 0; i < h->opt.nu2; ++i) smooth_step<T>(h, lv, adj, u, f, u0, work);
+  restrict_to<T>(h, L, md, work, cv.f);
+  vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, true);
+  prolong_add<T>(h, L, md, cv.u, u);
+  if (md) {
+    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false);
+  } else {
+    for (int i = 0; i < h->opt.nu2; ++i) smooth_step_nodes<T>(h, lv, adj, u, f, u0, work);
+  }
+}
+
+// Residual of the finest level in the basis of the cycle.
+template <typename T>
+void cycle_residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r) {
+  if (modal(h)) mresidual<T>(h, lv, adj, f, u, u0, r);
+  else residual<T>(h, lv, adj, f, u, u0, r);
 }
 
 template <typename T>
@@ -993,7 +1112,7 @@ Level& finest(st_handle* h) { return h->levels.back(); }
 
 // One FP64 refinement step of the mixed-precision form: given the FP64 residual
 // r (norm s), solve L e = r / s approximately with FP32 V-cycles and update
-// u += s e in FP64.
+// u += s e in FP64 (all in the basis of the cycle).
 void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
@@ -1003,19 +1122,50 @@ void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
     stmg::k_cast_down<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(
         v.f, r, 1.0 / s, lv.ndof);
   }
-  zero<float>(h, v.u, lv.ndof);
-  for (int c = 0; c < std::max(1, h->opt.inner_cycles); ++c) vcycle<float>(h, L, adj, v.u, v.f, (const float*)nullptr);
+  for (int c = 0; c < std::max(1, h->opt.inner_cycles); ++c)
+    vcycle<float>(h, L, adj, v.u, v.f, (const float*)nullptr, c == 0);
   Prof pr(h, ST_K_VECTOR, 20.0 * (double)lv.ndof, 2.0 * (double)lv.ndof);
   stmg::k_axpy_up<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(u, v.u, s, lv.ndof);
+}
+
+// Inputs of a finest-level cycle in its basis: with the exact block inverse f
+// and u0 are transformed into handle buffers (u in place); otherwise as given.
+struct CycleInputs {
+  const double* f;
+  const double* u0;
+};
+
+CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, double* u, bool u_given) {
+  Level& lv = finest(h);
+  if (!modal(h)) return {f, u0};
+  copy<double>(h, lv.v64.f, f, lv.ndof);
+  to_modal<double>(h, lv, lv.v64.f, (int64_t)lv.N * h->q);
+  const double* u0m = nullptr;
+  if (u0) {
+    copy<double>(h, h->u0m, u0, lv.Nx);
+    to_modal<double>(h, lv, h->u0m, 1);
+    u0m = h->u0m;
+  }
+  if (u_given) to_modal<double>(h, lv, u, (int64_t)lv.N * h->q);
+  return {lv.v64.f, u0m};
+}
+
+void leave_cycle_basis(st_handle* h, double* u) {
+  Level& lv = finest(h);
+  if (modal(h)) from_modal<double>(h, lv, u, (int64_t)lv.N * h->q);
 }
 
 int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double* u, int flags, int* iters,
                double* relres) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
-  if (!(flags & ST_INIT_GIVEN)) zero<double>(h, u, lv.ndof);
+  const bool given = (flags & ST_INIT_GIVEN) != 0;
+  const CycleInputs in = enter_cycle_basis(h, f, u0, u, given);
+  if (!given) zero<double>(h, u, lv.ndof);
   double* r = (h->opt.precision == ST_MIXED) ? h->r64 : lv.v64.r;
-  residual<double>(h, lv, adj, f, u, u0, r);
+  cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
+  // the sine transform is orthogonal up to a constant factor, so the relative
+  // residual is the same in both bases
   const double r0 = norm2<double>(h, r, lv.ndof);
   double rn = r0;
   int it = 0;
@@ -1026,14 +1176,15 @@ int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double
     if (h->opt.precision == ST_MIXED) {
       mixed_step(h, adj, u, r, rn);
     } else {
-      vcycle<double>(h, L, adj, u, f, u0);
+      vcycle<double>(h, L, adj, u, in.f, in.u0, false);
     }
     ++it;
-    residual<double>(h, lv, adj, f, u, u0, r);
+    cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
     rn = norm2<double>(h, r, lv.ndof);
     if (!std::isfinite(rn)) { status = ST_ENAN; h->err = "residual norm is not finite"; break; }
     if (rn > 1e6 * r0) { status = ST_ENOTCONV; h->err = "residual grew by 1e6"; break; }
   }
+  leave_cycle_basis(h, u);
   if (iters) *iters = it;
   if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
   return status;
@@ -1151,10 +1302,8 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
     const bool mixed = h->opt.precision == ST_MIXED;
     for (int L = 0; L < nlev; ++L) {
       Level& l = h->levels[L];
-      if (L < nlev - 1) {
-        l.v64.u = dalloc<double>(h, l.ndof);
-        l.v64.f = dalloc<double>(h, l.ndof);
-      }
+      if (L < nlev - 1) l.v64.u = dalloc<double>(h, l.ndof);
+      l.v64.f = dalloc<double>(h, l.ndof);   // finest level: the transformed right-hand side
       l.v64.r = dalloc<double>(h, l.ndof);
       make_tables<double>(h, l, l.t64);
       if (h->opt.smoother == ST_SMOOTH_VCYCLE) make_space<double>(h, l, l.sp64);
@@ -1173,6 +1322,7 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       h->coarse64_r = dalloc<double>(h, c.ndof);
       h->r64 = finest(h).v64.r;
     }
+    h->u0m = dalloc<double>(h, finest(h).Nx);
     dst_set_smem_limits<double>(h);
     if (mixed) dst_set_smem_limits<float>(h);
     h->partial = dalloc<double>(h, kNormBlocks);
@@ -1231,15 +1381,17 @@ int st_vcycle(st_handle* h, double* u, const double* f, const double* u0_ic) {
   return guarded(h, [&]() -> int {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
     const int L = (int)h->levels.size() - 1;
+    Level& lv = finest(h);
+    const CycleInputs in = enter_cycle_basis(h, f, u0_ic, u, true);
     if (h->opt.precision == ST_MIXED) {
-      Level& lv = finest(h);
-      residual<double>(h, lv, false, f, u, u0_ic, h->r64);
+      cycle_residual<double>(h, lv, false, in.f, u, in.u0, h->r64);
       const double s = norm2<double>(h, h->r64, lv.ndof);
       if (!std::isfinite(s)) fail(h, ST_ENAN, "residual norm is not finite");
       if (s > 0.0) mixed_step(h, false, u, h->r64, s);
     } else {
-      vcycle<double>(h, L, false, u, f, u0_ic);
+      vcycle<double>(h, L, false, u, in.f, in.u0, false);
     }
+    leave_cycle_basis(h, u);
     after_launch(h);
     return ST_OK;
   });
@@ -1270,7 +1422,18 @@ int st_adjoint_solve(st_handle* h, const double* g, double* lambda, double* grad
 int st_level_residual(st_handle* h, int L, int adjoint, const double* f, const double* u, double* r) {
   return guarded(h, [&]() -> int {
     if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
-    residual<double>(h, h->levels[level_index(h, L)], adjoint != 0, f, u, (const double*)nullptr, r);
+    Level& lv = h->levels[level_index(h, L)];
+    if (modal(h)) {
+      const int64_t slabs = (int64_t)lv.N * h->q;
+      copy<double>(h, lv.v64.f, f, lv.ndof);
+      to_modal<double>(h, lv, lv.v64.f, slabs);
+      copy<double>(h, lv.v64.r, u, lv.ndof);
+      to_modal<double>(h, lv, lv.v64.r, slabs);
+      mresidual<double>(h, lv, adjoint != 0, lv.v64.f, lv.v64.r, (const double*)nullptr, r);
+      from_modal<double>(h, lv, r, slabs);
+    } else {
+      residual<double>(h, lv, adjoint != 0, f, u, (const double*)nullptr, r);
+    }
     after_launch(h);
     return ST_OK;
   });
@@ -1290,7 +1453,17 @@ int st_level_smooth(st_handle* h, int L, int adjoint, int nu, const double* f, d
   return guarded(h, [&]() -> int {
     if (!f || !u || nu < 0) fail(h, ST_EINVAL, "bad argument");
     Level& lv = h->levels[level_index(h, L)];
-    for (int i = 0; i < nu; ++i) smooth_step<double>(h, lv, adjoint != 0, u, f, (const double*)nullptr, lv.v64.r);
+    if (modal(h)) {
+      const int64_t slabs = (int64_t)lv.N * h->q;
+      copy<double>(h, lv.v64.f, f, lv.ndof);
+      to_modal<double>(h, lv, lv.v64.f, slabs);
+      to_modal<double>(h, lv, u, slabs);
+      smooth_modal<double>(h, lv, adjoint != 0, u, lv.v64.f, (const double*)nullptr, lv.v64.r, nu, false);
+      from_modal<double>(h, lv, u, slabs);
+    } else {
+      for (int i = 0; i < nu; ++i)
+        smooth_step_nodes<double>(h, lv, adjoint != 0, u, f, (const double*)nullptr, lv.v64.r);
+    }
     after_launch(h);
     return ST_OK;
   });
@@ -1299,7 +1472,16 @@ int st_level_smooth(st_handle* h, int L, int adjoint, int nu, const double* f, d
 int st_level_restrict(st_handle* h, int L, const double* r_fine, double* f_coarse) {
   return guarded(h, [&]() -> int {
     if (!r_fine || !f_coarse || level_index(h, L) < 1) fail(h, ST_EINVAL, "bad argument");
-    restrict_to<double>(h, L, r_fine, f_coarse);
+    if (modal(h)) {
+      Level& fine = h->levels[L];
+      Level& coarse = h->levels[L - 1];
+      copy<double>(h, fine.v64.r, r_fine, fine.ndof);
+      to_modal<double>(h, fine, fine.v64.r, (int64_t)fine.N * h->q);
+      restrict_to<double>(h, L, true, fine.v64.r, f_coarse);
+      from_modal<double>(h, coarse, f_coarse, (int64_t)coarse.N * h->q);
+    } else {
+      restrict_to<double>(h, L, false, r_fine, f_coarse);
+    }
     after_launch(h);
     return ST_OK;
   });
@@ -1308,7 +1490,17 @@ int st_level_restrict(st_handle* h, int L, const double* r_fine, double* f_coars
 int st_level_prolong(st_handle* h, int L, const double* e_coarse, double* u_fine) {
   return guarded(h, [&]() -> int {
     if (!e_coarse || !u_fine || level_index(h, L) < 1) fail(h, ST_EINVAL, "bad argument");
-    prolong_add<double>(h, L, e_coarse, u_fine);
+    if (modal(h)) {
+      Level& fine = h->levels[L];
+      Level& coarse = h->levels[L - 1];
+      copy<double>(h, coarse.v64.r, e_coarse, coarse.ndof);
+      to_modal<double>(h, coarse, coarse.v64.r, (int64_t)coarse.N * h->q);
+      to_modal<double>(h, fine, u_fine, (int64_t)fine.N * h->q);
+      prolong_add<double>(h, L, true, coarse.v64.r, u_fine);
+      from_modal<double>(h, fine, u_fine, (int64_t)fine.N * h->q);
+    } else {
+      prolong_add<double>(h, L, false, e_coarse, u_fine);
+    }
     after_launch(h);
     return ST_OK;
   });
@@ -1317,7 +1509,16 @@ int st_level_prolong(st_handle* h, int L, const double* e_coarse, double* u_fine
 int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u) {
   return guarded(h, [&]() -> int {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
-    coarsest_solve_t<double>(h, adjoint != 0, u, f, h->levels[0].v64.r);
+    Level& c = h->levels[0];
+    if (modal(h)) {
+      const int64_t slabs = (int64_t)c.N * h->q;
+      copy<double>(h, c.v64.f, f, c.ndof);
+      to_modal<double>(h, c, c.v64.f, slabs);
+      coarsest_modal<double>(h, adjoint != 0, u, c.v64.f, (const double*)nullptr);
+      from_modal<double>(h, c, u, slabs);
+    } else {
+      coarsest_nodes<double>(h, adjoint != 0, u, f, (const double*)nullptr, c.v64.r);
+    }
     after_launch(h);
     return ST_OK;
   });

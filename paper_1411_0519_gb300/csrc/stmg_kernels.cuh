@@ -729,185 +729,6 @@ __global__ void __launch_bounds__(256) k_dst_cols(T* __restrict__ data, int n, i
 }
 
 // ---------------------------------------------------------------------------
-// Line solve of the exact block inverse (Section 3.1).  After the sine
-// transform along the first D-1 axes, A = K_tau (x) M_h + M_tau (x) K_h
-// decouples into one block-tridiagonal system per mode i of those axes along
-// the last axis:
-//     A_i = tridiag(E_i, Dg_i, E_i),
-//     Dg_i = lamM (4h/6) K + tau Mh (lamM (2/h) + lamK (4h/6)),
-//     E_i  = lamM ( h/6) K + tau Mh (-lamM / h  + lamK ( h/6)),
-// with lamM, lamK the products / sums of the 1D eigenvalues m_k = h/3 (2 + cos),
-// kappa_k = 2/h (1 - cos) over the transformed axes (lamM = 1, lamK = 0 in 1D),
-// K = K_tau (adjoint: K_tau^T).  Block LU without pivoting, factors precomputed
-// on the host in FP64: W_0 = Dg, L_j = E W_{j-1}^{-1}, W_j = Dg - L_j E.
-//   forward  z_j = g_j - L_j z_{j-1}
-//   backward x_j = W_j^{-1} (z_j - E x_{j+1})
-// One thread per (time step, mode); consecutive threads take consecutive modes
-// so every access along the sweep is coalesced.  Table layout:
-//   fac[((j * 2 + w) * Q*Q + e) * nmodes + mode], w = 0: L_j, w = 1: W_j^{-1}
-//   ecoef[e * nmodes + mode]
-// The tables carry the inverse sine-transform normalisation s: fac holds
-// s W_j^{-1} and ecoef E / s, so the sweep returns s x without a multiply.
-// ---------------------------------------------------------------------------
-template <typename T, int Q>
-__global__ void k_line_solve(T* __restrict__ data, int n, int64_t nmodes, int nsteps,
-                             const T* __restrict__ fac, const T* __restrict__ ecoef) {
-  const int64_t mode = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (mode >= nmodes || s >= nsteps) return;
-  const int64_t Nx = nmodes * n;
-  T* base = data + (int64_t)s * Q * Nx + mode;
-  constexpr int QQ = Q * Q;
-  T z[Q];
-  // forward elimination, z_j stored in place
-  for (int j = 0; j < n; ++j) {
-    T g[Q];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) g[l] = base[(int64_t)l * Nx + (int64_t)j * nmodes];
-    if (j > 0) {
-      const T* Lj = fac + ((int64_t)(j * 2 + 0) * QQ) * nmodes + mode;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        T acc = g[k];
-#pragma unroll
-        for (int l = 0; l < Q; ++l) acc -= Lj[(int64_t)(k * Q + l) * nmodes] * z[l];
-        g[k] = acc;
-      }
-    }
-#pragma unroll
-    for (int l = 0; l < Q; ++l) {
-      z[l] = g[l];
-      base[(int64_t)l * Nx + (int64_t)j * nmodes] = g[l];
-    }
-  }
-  T E[QQ];
-#pragma unroll
-  for (int e = 0; e < QQ; ++e) E[e] = ecoef[(int64_t)e * nmodes + mode];
-  // backward substitution (on s x)
-  T xn[Q];
-  for (int j = n - 1; j >= 0; --j) {
-    T t[Q];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) t[l] = (j == n - 1) ? z[l] : base[(int64_t)l * Nx + (int64_t)j * nmodes];
-    if (j < n - 1) {
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        T acc = t[k];
-#pragma unroll
-        for (int l = 0; l < Q; ++l) acc -= E[k * Q + l] * xn[l];
-        t[k] = acc;
-      }
-    }
-    const T* Wi = fac + ((int64_t)(j * 2 + 1) * QQ) * nmodes + mode;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      T acc = T(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) acc += Wi[(int64_t)(k * Q + l) * nmodes] * t[l];
-      xn[k] = acc;
-    }
-#pragma unroll
-    for (int l = 0; l < Q; ++l) base[(int64_t)l * Nx + (int64_t)j * nmodes] = xn[l];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Right-hand side of one damped block-Jacobi step written without A u:
-//     u + w D^{-1} (f - A u_n - B u_{n-1}) = (1 - w) u + w A^{-1} (f_n - B u_{n-1}),
-// so the step needs g = f - B u_prev only (B = -N_tau (x) M_h, rank one in time):
-//   forward  g_{s,k} = f_{s,k} + st[k] M_h (sum_l en[l] u_{s-1,l})   (s = 0: M_h u0)
-//   adjoint  g_{s,k} = f_{s,k} + en[k] M_h (sum_l st[l] u_{s+1,l})
-// One thread per (spatial node, time step).
-// ---------------------------------------------------------------------------
-template <typename T, int D, int Q, bool ADJ>
-__global__ void k_rhs(const T* __restrict__ f, const T* __restrict__ u, const T* __restrict__ u0,
-                      T* __restrict__ g, int n, int N, int s0, T h, TimeCoef<T, Q> tc) {
-  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = s0 + blockIdx.y;
-  if (j >= Nx || s >= N) return;
-  int ix, iy, iz;
-  node_coords(j, n, D, ix, iy, iz);
-  Stencil<T, D> S(h, T(0));   // M_h only
-  T mt = T(0);
-  const T* nb = nullptr;
-  if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
-  if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
-  if (nb != nullptr) {
-    mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) {
-      T t = T(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) t += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + q];
-      return t;
-    });
-  } else if (!ADJ && s == 0 && u0 != nullptr) {
-    mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t q) { return u0[q]; });
-  }
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
-    g[idx] = f[idx] + (ADJ ? tc.en[k] : tc.st[k]) * mt;
-  }
-}
-
-// 2D smoother right-hand side with a shared-memory tile (same result as
-// k_rhs<T, 2, Q, ADJ>): the coupling trace of the neighbouring step is formed
-// once per staged node, M_1 along x once per staged row, M_1 along y per node.
-template <typename T, int Q, bool ADJ>
-__global__ void __launch_bounds__(kResTX * kResTY) k_rhs2d(const T* __restrict__ f, const T* __restrict__ u,
-                                                           const T* __restrict__ u0, T* __restrict__ g, int n,
-                                                           int N, int s0, T h, TimeCoef<T, Q> tc) {
-  constexpr int HX = kResTX + 2, HY = kResTY + 2;
-  __shared__ T st[HY][HX];        // trace of the neighbouring step on tile + halo
-  __shared__ T sa[HY][kResTX];    // M_1 along x
-  const int s = s0 + blockIdx.z;
-  const int x0 = blockIdx.x * kResTX, y0 = blockIdx.y * kResTY;
-  const int tid = threadIdx.y * kResTX + threadIdx.x;
-  const int64_t Nx = (int64_t)n * n;
-  const T* nb = nullptr;
-  if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
-  if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
-  const bool use_u0 = !ADJ && s == 0 && u0 != nullptr;
-  const bool any = nb != nullptr || use_u0;
-  if (any) {
-    for (int i = tid; i < HX * HY; i += kResTX * kResTY) {
-      const int hy = i / HX, hx = i - hy * HX;
-      const int x = x0 + hx - 1, y = y0 + hy - 1;
-      T t = T(0);
-      if (x >= 0 && x < n && y >= 0 && y < n) {
-        const int64_t j = (int64_t)y * n + x;
-        if (nb != nullptr) {
-#pragma unroll
-          for (int l = 0; l < Q; ++l) t += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + j];
-        } else {
-          t = u0[j];
-        }
-      }
-      st[hy][hx] = t;
-    }
-  }
-  __syncthreads();
-  const T m0 = h * T(1.0 / 6.0), m1 = h * T(2.0 / 3.0);
-  if (any) {
-    for (int i = tid; i < HY * kResTX; i += kResTX * kResTY) {
-      const int hy = i / kResTX, tx = i - hy * kResTX;
-      sa[hy][tx] = m0 * (st[hy][tx] + st[hy][tx + 2]) + m1 * st[hy][tx + 1];
-    }
-  }
-  __syncthreads();
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = x0 + tx, y = y0 + ty;
-  if (x >= n || y >= n || s >= N) return;
-  const T mt = any ? m0 * (sa[ty][tx] + sa[ty + 2][tx]) + m1 * sa[ty + 1][tx] : T(0);
-  const int64_t j = (int64_t)y * n + x;
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
-    g[idx] = f[idx] + (ADJ ? tc.en[k] : tc.st[k]) * mt;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Restriction (eqs. chap4_restrictionTime, chap4_spaceRestrictionProlongation):
 // fc[m, k, J] = sum_l R1[k,l] (Rx r)[2m, l, J] + R2[k,l] (Rx r)[2m+1, l, J],
 // Rx = identity (semi) or (x)_a (1/2)[1 2 1] at fine nodes 2J, 2J+1, 2J+2 (0-based,
