@@ -140,8 +140,9 @@ struct Tables {
   T* tws = nullptr;   // sin(2 pi k / Nf)
   T* fac[2] = {nullptr, nullptr};    // line-solve LU factors (forward, adjoint)
   T* ecoef[2] = {nullptr, nullptr};  // off-diagonal blocks E per mode
-  T* alpha = nullptr;  // per mode: product of the 1D mass eigenvalues over the transformed axes
-  T* beta = nullptr;   // per mode: the matching stiffness combination
+  T* facw[2] = {nullptr, nullptr};   // damped smoother: L_j and w W_j^{-1}
+  T* ecoefw[2] = {nullptr, nullptr}; // damped smoother: E / w
+  T* rw[2] = {nullptr, nullptr};     // residual stencil weights per mode (see k_mresidual)
   T* ra = nullptr;     // full-coarsening pair weights to level L-1: (1 + c_k) / 2
   T* rb = nullptr;     //                                             -(1 - c_k) / 2
 };
@@ -406,12 +407,43 @@ void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
     tb.ecoef[adj] = dalloc<T>(h, ec.size());
     upload(h, tb.fac[adj], fac);
     upload(h, tb.ecoef[adj], ec);
-    if (adj == 0) {
-      tb.alpha = dalloc<T>(h, lm.size());
-      tb.beta = dalloc<T>(h, lk.size());
-      upload(h, tb.alpha, lm);
-      upload(h, tb.beta, lk);
+    // damped tables: w W^{-1} and E / w, so the backward sweep yields w x
+    const double w = h->opt.omega;
+    const int qq = h->q * h->q;
+    const int64_t nm = (int64_t)lm.size();
+    std::vector<double> facw(fac), ecw(ec);
+    for (int j = 0; j < n; ++j)
+      for (int64_t e = 0; e < (int64_t)qq * nm; ++e) facw[((size_t)j * 2 + 1) * qq * nm + e] *= w;
+    for (double& x : ecw) x /= w;
+    tb.facw[adj] = dalloc<T>(h, facw.size());
+    tb.ecoefw[adj] = dalloc<T>(h, ecw.size());
+    upload(h, tb.facw[adj], facw);
+    upload(h, tb.ecoefw[adj], ecw);
+    // residual weights per mode: row k, column l of
+    // a K[k,l] M_1 + delta_kl tau Mh[k] (a K_1 + b M_1) as (neighbour w0, centre w1),
+    // then the coupling weights a h/6, a 2h/3
+    const int q = h->q;
+    const double hl = lv.h, m0 = hl / 6.0, m1 = 2.0 * hl / 3.0;
+    std::vector<double> rw((size_t)(2 * qq + 2) * nm);
+    for (int64_t i = 0; i < nm; ++i) {
+      const double a = lm[i], b = lk[i];
+      for (int k = 0; k < q; ++k)
+        for (int l = 0; l < q; ++l) {
+          const double cK = a * (adj ? h->tm.K[l * q + k] : h->tm.K[k * q + l]);
+          double w0 = cK * m0, w1 = cK * m1;
+          if (k == l) {
+            const double d = lv.tau * h->tm.Mh[k];
+            w0 += d * (b * m0 - a / hl);
+            w1 += d * (2.0 * a / hl + b * m1);
+          }
+          rw[(size_t)(k * q + l) * nm + i] = w0;
+          rw[(size_t)(qq + k * q + l) * nm + i] = w1;
+        }
+      rw[(size_t)(2 * qq) * nm + i] = a * m0;
+      rw[(size_t)(2 * qq + 1) * nm + i] = a * m1;
     }
+    tb.rw[adj] = dalloc<T>(h, rw.size());
+    upload(h, tb.rw[adj], rw);
   }
   if (lv.coarsen_full) {
     // coarse mode k (k = 1..nc) pairs with fine modes k and Nf - k, c_k = cos(k pi / Nf)
@@ -498,7 +530,6 @@ void launch_residual_t(st_handle* h, const Level& lv, bool adj, const T* f, cons
 template <typename T, int D, int Q>
 void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0,
                         int ns) {
-  auto tc = to_coef<T, Q>(h->tm);
   Tables<T>& tb = tables<T>(lv);
   const int nm = (int)(lv.Nx / lv.n);
   const int nch = (lv.n + stmg::kMResChunk - 1) / stmg::kMResChunk;
@@ -506,11 +537,11 @@ void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* 
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
     if (adj)
-      stmg::k_mresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(
-          f, u, u0, r, lv.n, nm, lv.N, s0 + c, (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), tb.alpha, tb.beta, tc);
+      stmg::k_mresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, nm, lv.N, s0 + c,
+                                                                      tb.rw[1]);
     else
-      stmg::k_mresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(
-          f, u, u0, r, lv.n, nm, lv.N, s0 + c, (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), tb.alpha, tb.beta, tc);
+      stmg::k_mresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, nm, lv.N, s0 + c,
+                                                                       tb.rw[0]);
   }
 }
 
@@ -519,18 +550,18 @@ constexpr int kSmoothThreads = 128;
 template <typename T, int D, int Q>
 void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out,
                       int s0, int ns) {
-  auto tc = to_coef<T, Q>(h->tm);
   Tables<T>& tb = tables<T>(lv);
   const int nm = (int)(lv.Nx / lv.n);
-  const T* fac = tb.fac[adj ? 1 : 0];
-  const T* ec = tb.ecoef[adj ? 1 : 0];
-  const T w = (T)h->opt.omega;
+  const int a = adj ? 1 : 0;
+  const T* fac = damp ? tb.facw[a] : tb.fac[a];
+  const T* ec = damp ? tb.ecoefw[a] : tb.ecoef[a];
+  const T wc = (T)(1.0 - h->opt.omega);
   dim3 grid(blocks_for(nm, kSmoothThreads), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
 #define STMG_MSMOOTH(ADJ, DAMP)                                                                                  \
   stmg::k_msmooth<T, Q, ADJ, DAMP><<<grid, kSmoothThreads, 0, h->stream>>>(f, u, u0, out, lv.n, nm, lv.N, s0 + c, \
-                                                                           (T)lv.h, w, tb.alpha, fac, ec, tc)
+                                                                           wc, fac, ec, tb.rw[a])
     if (adj) {
       if (damp) STMG_MSMOOTH(true, true); else STMG_MSMOOTH(true, false);
     } else {
@@ -562,9 +593,15 @@ void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, bool modal
   dim3 grid(blocks_for(fine.Nx), fine.N);
   if (!fine.coarsen_full)
     stmg::k_prolong<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
-  else if (modal)
+  else if (modal) {
+    // pair weights of the prolongation are 2 ra, 2 rb per transformed axis: fold 2^(D-1) into R^T
+    for (int i = 0; i < Q * Q; ++i) {
+      tc.R1[i] *= (T)(1 << (D - 1));
+      tc.R2[i] *= (T)(1 << (D - 1));
+    }
     stmg::k_mprolong<T, D, Q><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N,
                                                                  tables<T>(fine).ra, tables<T>(fine).rb, tc);
+  }
   else
     stmg::k_prolong<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
 }

@@ -29,26 +29,50 @@
 
 namespace stmg {
 
+// Time traces of a step with the Legendre slab basis (Section 1), whose end
+// values are psi_k(t_{n-1}^+) = (-1)^k and psi_k(t_n^-) = 1: the coupling of
+// step s to s-1 (forward) uses sum_l u_{s-1,l} and enters row k with sign
+// (-1)^k; the transposed coupling to s+1 uses sum_l (-1)^l u_{s+1,l} and
+// enters every row with sign +1.  Additions only, no multiplies.
+template <typename T, int Q, bool ADJ>
+__device__ __forceinline__ T step_trace(const T* __restrict__ nb, int64_t Nx, int64_t o) {
+  T v = nb[o];
+#pragma unroll
+  for (int l = 1; l < Q; ++l) {
+    const T x = nb[(int64_t)l * Nx + o];
+    v = (ADJ && (l & 1)) ? v - x : v + x;
+  }
+  return v;
+}
+
+template <typename T, bool ADJ>
+__device__ __forceinline__ T couple(int k, T g, T mt) {
+  return (!ADJ && (k & 1)) ? g - mt : g + mt;
+}
+
 // ---------------------------------------------------------------------------
 // Residual r^ = f^ - L^ u^ (forward) or f^ - L^T u^ (adjoint) in the mixed basis;
 // the operator is that of k_residual with M_h, K_h replaced by their mode-wise
 // line forms.  Row k of the block row of step s:
 //   sum_l [a K[k,l] M_1 + delta_kl tau Mh[k] (a K_1 + b M_1)] u_{s,l}
 // is a three-point stencil per (k, l) with weights w0 (neighbours) and w1
-// (centre), formed once per thread.  The time coupling adds st[k] a M_1 t,
-// t = sum_l en[l] u_{s-1,l} (adjoint: en[k] a M_1 sum_l st[l] u_{s+1,l}); at
-// s = 0 of the forward problem t is the transformed initial value u0^ (or 0).
+// (centre), tabulated per mode on the host.  The time coupling adds
+// (-1)^k a M_1 t, t = sum_l u_{s-1,l} (adjoint: a M_1 sum_l (-1)^l u_{s+1,l});
+// at s = 0 of the forward problem t is the transformed initial value u0^ (or 0).
 // One thread per (mode, chunk of kMResChunk line positions, time step); the
 // three-point window slides along the chunk in registers.
 // ---------------------------------------------------------------------------
-constexpr int kMResChunk = 8;
+constexpr int kMResChunk = 16;
 
+// Per-mode residual weights (host table, FP64 formed then rounded to T):
+// rw[(e) * nm + i] = w0 for e = k*Q + l, rw[(Q*Q + e) * nm + i] = w1,
+// rw[(2*Q*Q) * nm + i] = a m0, rw[(2*Q*Q + 1) * nm + i] = a m1 (M_1 weights
+// of the coupling term times alpha_i).
 template <typename T, int Q, bool ADJ>
 __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, const T* __restrict__ u,
                                                    const T* __restrict__ u0, T* __restrict__ r, int n, int nm,
-                                                   int N, int s0, T tau, T h, T hinv,
-                                                   const T* __restrict__ alpha, const T* __restrict__ beta,
-                                                   TimeCoef<T, Q> tc) {
+                                                   int N, int s0, const T* __restrict__ rw) {
+  constexpr int QQ = Q * Q;
   const int nch = (n + kMResChunk - 1) / kMResChunk;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = s0 + blockIdx.y;
@@ -56,22 +80,13 @@ __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, cons
   const int i = (int)(t % nm), c = (int)(t / nm);
   const int p0 = c * kMResChunk, p1 = min(p0 + kMResChunk, n);
   const int64_t Nx = (int64_t)nm * n;
-  const T a = alpha[i], b = beta[i];
-  const T m0 = h * T(1.0 / 6.0), m1 = h * T(2.0 / 3.0), k1 = T(2) * hinv;
-  T w0[Q][Q], w1[Q][Q], cT[Q];
+  T w0[QQ], w1[QQ];
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-#pragma unroll
-    for (int l = 0; l < Q; ++l) {
-      const T cK = a * (ADJ ? tc.K[l * Q + k] : tc.K[k * Q + l]);
-      w0[k][l] = cK * m0;
-      w1[k][l] = cK * m1;
-    }
-    const T d = tau * tc.Mh[k];
-    w0[k][k] += d * (b * m0 - a * hinv);
-    w1[k][k] += d * (a * k1 + b * m1);
-    cT[k] = (ADJ ? tc.en[k] : tc.st[k]) * a;
+  for (int e = 0; e < QQ; ++e) {
+    w0[e] = rw[(int64_t)e * nm + i];
+    w1[e] = rw[(int64_t)(QQ + e) * nm + i];
   }
+  const T am0 = rw[(int64_t)(2 * QQ) * nm + i], am1 = rw[(int64_t)(2 * QQ + 1) * nm + i];
   const T* nb = nullptr;
   if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
   if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
@@ -79,12 +94,7 @@ __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, cons
   auto trace = [&](int p) -> T {
     if (p < 0 || p >= n) return T(0);
     const int64_t o = (int64_t)p * nm + i;
-    if (nb != nullptr) {
-      T v = T(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) v += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + o];
-      return v;
-    }
+    if (nb != nullptr) return step_trace<T, Q, ADJ>(nb, Nx, o);
     return use_u0 ? u0[o] : T(0);
   };
   const T* us = u + (int64_t)s * Q * Nx + i;
@@ -96,17 +106,20 @@ __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, cons
   }
   T tp = trace(p0 - 1), tcur = trace(p0);
   for (int p = p0; p < p1; ++p) {
-    T un[Q];
+    T un[Q], sg[Q];
 #pragma unroll
-    for (int l = 0; l < Q; ++l) un[l] = (p + 1 < n) ? us[(int64_t)l * Nx + (int64_t)(p + 1) * nm] : T(0);
+    for (int l = 0; l < Q; ++l) {
+      un[l] = (p + 1 < n) ? us[(int64_t)l * Nx + (int64_t)(p + 1) * nm] : T(0);
+      sg[l] = up[l] + un[l];
+    }
     const T tn = trace(p + 1);
-    const T mt = m0 * (tp + tn) + m1 * tcur;
+    const T mt = am0 * (tp + tn) + am1 * tcur;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int64_t idx = ((int64_t)s * Q + k) * Nx + (int64_t)p * nm + i;
-      T acc = f[idx] + cT[k] * mt;
+      T acc = couple<T, ADJ>(k, f[idx], mt);
 #pragma unroll
-      for (int l = 0; l < Q; ++l) acc -= w0[k][l] * (up[l] + un[l]) + w1[k][l] * uc[l];
+      for (int l = 0; l < Q; ++l) acc -= w0[k * Q + l] * sg[l] + w1[k * Q + l] * uc[l];
       r[idx] = acc;
     }
 #pragma unroll
@@ -131,28 +144,28 @@ __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, cons
 // W_0 = Dg, L_p = E W_{p-1}^{-1}, W_p = Dg - L_p E;
 //   forward  z_p = g_p - L_p z_{p-1}   (g = f - B u_prev, formed on the fly)
 //   backward x_p = W_p^{-1} (z_p - E x_{p+1}).
-// z is kept in `out` between the sweeps.  DAMP = false writes x (w = 1) and
-// never reads u at step s, so `out` may be `u` itself (forward substitution of
-// the coarsest solve, one step per launch).  u == nullptr means a zero iterate
-// (no coupling term, no damping term).  f and out must not alias.
-// Tables: fac[((p * 2 + w) * Q*Q + e) * nm + i] (w = 0: L_p, w = 1: W_p^{-1}),
-// ecoef[e * nm + i].  One thread per (mode, time step in [s0, s0 + gridDim.y)).
+// DAMP: the host passes the damped tables w W_p^{-1} and E / w, so the backward
+// sweep yields y = w x directly and out = y + wc u with wc = 1 - w.  Without
+// DAMP the tables are unscaled and out = x; u at step s is then never read, so
+// `out` may be `u` itself (forward substitution of the coarsest solve, one
+// step per launch).  u == nullptr means a zero iterate (no coupling term, no
+// damping term).  f and out must not alias.  z is kept in `out` between the
+// sweeps.  Tables: fac[((p * 2 + w) * Q*Q + e) * nm + i] (w = 0: L_p, w = 1:
+// the inverse block), ecoef[e * nm + i], and the coupling weights a m0, a m1
+// of the residual table rw.  One thread per (mode, time step in
+// [s0, s0 + gridDim.y)).
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ, bool DAMP>
 __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const T* u, const T* __restrict__ u0,
-                                                 T* out, int n, int nm, int N, int s0, T h, T w,
-                                                 const T* __restrict__ alpha, const T* __restrict__ fac,
-                                                 const T* __restrict__ ecoef, TimeCoef<T, Q> tc) {
+                                                 T* out, int n, int nm, int N, int s0, T wc,
+                                                 const T* __restrict__ fac, const T* __restrict__ ecoef,
+                                                 const T* __restrict__ rw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = s0 + blockIdx.y;
   if (i >= nm || s >= N) return;
   const int64_t Nx = (int64_t)nm * n;
   constexpr int QQ = Q * Q;
-  const T m0 = h * T(1.0 / 6.0), m1 = h * T(2.0 / 3.0);
-  const T a = alpha[i];
-  T cT[Q];
-#pragma unroll
-  for (int k = 0; k < Q; ++k) cT[k] = (ADJ ? tc.en[k] : tc.st[k]) * a;
+  const T am0 = rw[(int64_t)(2 * QQ) * nm + i], am1 = rw[(int64_t)(2 * QQ + 1) * nm + i];
   const T* nb = nullptr;
   if (u != nullptr) {
     if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
@@ -163,12 +176,7 @@ __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const 
   auto trace = [&](int p) -> T {
     if (p >= n) return T(0);
     const int64_t o = (int64_t)p * nm + i;
-    if (nb != nullptr) {
-      T v = T(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) v += (ADJ ? tc.st[l] : tc.en[l]) * nb[(int64_t)l * Nx + o];
-      return v;
-    }
+    if (nb != nullptr) return step_trace<T, Q, ADJ>(nb, Nx, o);
     return u0[o];
   };
   const T* fs = f + (int64_t)s * Q * Nx + i;
@@ -181,9 +189,9 @@ __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const 
     for (int k = 0; k < Q; ++k) g[k] = fs[(int64_t)k * Nx + (int64_t)p * nm];
     if (any) {
       const T tn = trace(p + 1);
-      const T mt = m0 * (tp + tn) + m1 * tcur;
+      const T mt = am0 * (tp + tn) + am1 * tcur;
 #pragma unroll
-      for (int k = 0; k < Q; ++k) g[k] += cT[k] * mt;
+      for (int k = 0; k < Q; ++k) g[k] = couple<T, ADJ>(k, g[k], mt);
       tp = tcur;
       tcur = tn;
     }
@@ -205,7 +213,6 @@ __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const 
 #pragma unroll
   for (int e = 0; e < QQ; ++e) E[e] = ecoef[(int64_t)e * nm + i];
   const T* us = (DAMP && u != nullptr) ? u + (int64_t)s * Q * Nx + i : nullptr;
-  const T wc = T(1) - w;
   T xn[Q];
   for (int p = n - 1; p >= 0; --p) {
     T t[Q];
@@ -221,18 +228,15 @@ __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const 
     const T* Wi = fac + (int64_t)(p * 2 + 1) * QQ * nm + i;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      T acc = T(0);
+      T acc = Wi[(int64_t)(k * Q) * nm] * t[0];
 #pragma unroll
-      for (int l = 0; l < Q; ++l) acc += Wi[(int64_t)(k * Q + l) * nm] * t[l];
+      for (int l = 1; l < Q; ++l) acc += Wi[(int64_t)(k * Q + l) * nm] * t[l];
       xn[k] = acc;
     }
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       T v = xn[l];
-      if (DAMP) {
-        v = w * v;
-        if (us != nullptr) v += wc * us[(int64_t)l * Nx + (int64_t)p * nm];
-      }
+      if (us != nullptr) v += wc * us[(int64_t)l * Nx + (int64_t)p * nm];
       os[(int64_t)l * Nx + (int64_t)p * nm] = v;
     }
   }
@@ -308,21 +312,24 @@ __global__ void k_mrestrict(const T* __restrict__ r, T* __restrict__ fc, int nf,
 // Full-coarsening prolongation and correction u^_f += (P e)^ in the mixed
 // basis: per transformed axis fine mode i < nc takes 2 ra_i e^_i, fine mode
 // i > nc takes 2 rb_j e^_j (j = nf - 1 - i), mode nc takes nothing; along the
-// last axis linear interpolation; in time R_sl^T.  One thread per fine
-// (mode, position, step).
+// last axis linear interpolation (odd fine positions coincide with a coarse
+// node, even ones average their two neighbours); in time R_sl^T.  The host
+// passes the time blocks pre-multiplied by 2^(D-1), so the pair weights are ra,
+// rb themselves.  One thread per fine (mode, position, step).
 template <typename T>
-__device__ __forceinline__ void mode_source(int i, int nf, int nc, const T* __restrict__ ra,
+__device__ __forceinline__ bool mode_source(int i, int nf, int nc, const T* __restrict__ ra,
                                             const T* __restrict__ rb, int& src, T& wgt) {
   if (i < nc) {
     src = i;
-    wgt = T(2) * ra[i];
-  } else if (i > nc) {
-    src = nf - 1 - i;
-    wgt = T(2) * rb[src];
-  } else {
-    src = 0;
-    wgt = T(0);
+    wgt = ra[i];
+    return true;
   }
+  if (i > nc) {
+    src = nf - 1 - i;
+    wgt = rb[src];
+    return true;
+  }
+  return false;
 }
 
 template <typename T, int D, int Q>
@@ -339,39 +346,49 @@ __global__ void k_mprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
   const int pf = (int)(I / nmf);
   int64_t ic = 0;
   T wmode = T(1);
+  bool has = true;
   if (D == 2) {
     int c;
-    mode_source<T>((int)i_f, nf, nc, ra, rb, c, wmode);
+    has = mode_source<T>((int)i_f, nf, nc, ra, rb, c, wmode);
     ic = c;
   } else if (D == 3) {
     int cx, cy;
     T wx, wy;
-    mode_source<T>((int)(i_f % nf), nf, nc, ra, rb, cx, wx);
-    mode_source<T>((int)(i_f / nf), nf, nc, ra, rb, cy, wy);
-    ic = (int64_t)cy * nc + cx;
-    wmode = wx * wy;
+    has = mode_source<T>((int)(i_f % nf), nf, nc, ra, rb, cx, wx) &&
+          mode_source<T>((int)(i_f / nf), nf, nc, ra, rb, cy, wy);
+    if (has) {
+      ic = (int64_t)cy * nc + cx;
+      wmode = wx * wy;
+    }
   }
+  if (!has) return;   // the unpaired fine mode receives no correction
   T e[Q];
-  if (wmode == T(0)) {
+  const T* e0 = ec + (int64_t)m * Q * Nxc + ic;
+  if (pf & 1) {
+    const int64_t o = (int64_t)(pf >> 1) * nmc;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) e[k] = T(0);
+    for (int k = 0; k < Q; ++k) e[k] = wmode * e0[(int64_t)k * Nxc + o];
   } else {
-    int c0, c1;
-    float w0, w1;
-    interp_pair(pf, nc, c0, c1, w0, w1);
+    const int jl = (pf >> 1) - 1, jr = pf >> 1;
+    const T wh = T(0.5) * wmode;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      const T* ek = ec + ((int64_t)m * Q + k) * Nxc + ic;
-      e[k] = wmode * (T(w0) * ek[(int64_t)c0 * nmc] + T(w1) * ek[(int64_t)c1 * nmc]);
+      const T* ek = e0 + (int64_t)k * Nxc;
+      T v;
+      if (jl < 0) v = ek[(int64_t)jr * nmc];
+      else if (jr >= nc) v = ek[(int64_t)jl * nmc];
+      else v = ek[(int64_t)jl * nmc] + ek[(int64_t)jr * nmc];
+      e[k] = wh * v;
     }
   }
   const T* Rb = sl ? tc.R2 : tc.R1;
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
-    T acc = T(0);
+    T* dst = uf + ((int64_t)s * Q + l) * Nxf + I;
+    T acc = *dst;
 #pragma unroll
     for (int k = 0; k < Q; ++k) acc += Rb[k * Q + l] * e[k];
-    uf[((int64_t)s * Q + l) * Nxf + I] += acc;
+    *dst = acc;
   }
 }
 
