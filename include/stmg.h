@@ -81,6 +81,7 @@ typedef struct st_options {
   int smoother;          /* ST_SMOOTH_EXACT (default) or ST_SMOOTH_VCYCLE */
   int nu_x;              /* ST_SMOOTH_VCYCLE: spatial pre-/post-smoothing steps, default 2 (Section 4) */
   double omega_x;        /* ST_SMOOTH_VCYCLE: spatial Jacobi damping, default 2/3 (Section 4) */
+  int gamma;             /* cycle index (Section 2): 1 = V-cycle (default), 2 = W-cycle */
 } st_options;
 
 typedef struct st_handle st_handle;

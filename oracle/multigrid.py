@@ -166,8 +166,12 @@ def backward_substitution(level, g):
     return lam
 
 
-def vcycle(H, i, u, f, nu1=2, nu2=2, omega=0.5, adjoint=False):
-    """One V-cycle on level i (0 = finest) for L u = f (or L^T u = f)."""
+def vcycle(H, i, u, f, nu1=2, nu2=2, omega=0.5, adjoint=False, gamma=1):
+    """One multigrid cycle on level i (0 = finest) for L u = f (or L^T u = f),
+    Section 2: pre-smoothing, restriction of the residual, gamma applications of
+    the cycle on the coarse level to the correction equation (from zero; gamma = 1
+    V-cycle, 2 W-cycle; the coarsest level is solved exactly), prolongation of
+    the correction, post-smoothing."""
     lv = H.levels[i]
     if i == len(H.levels) - 1:
         return coarsest_solve(lv, f, adjoint)
@@ -175,14 +179,16 @@ def vcycle(H, i, u, f, nu1=2, nu2=2, omega=0.5, adjoint=False):
     r = lv.residual(u, f, adjoint)
     coarse = H.levels[i + 1]
     fc = (lv.R @ r.reshape(-1)).reshape(coarse.disc.shape())
-    ec = vcycle(H, i + 1, np.zeros_like(fc), fc, nu1, nu2, omega, adjoint)
+    ec = np.zeros_like(fc)
+    for _ in range(gamma):
+        ec = vcycle(H, i + 1, ec, fc, nu1, nu2, omega, adjoint, gamma)
     u = u + (lv.R.T @ ec.reshape(-1)).reshape(lv.disc.shape())
     u = smooth(lv, u, f, nu2, omega, adjoint)
     return u
 
 
-def solve(H, f, u=None, rtol=1e-8, maxit=100, nu1=2, nu2=2, omega=0.5, adjoint=False):
-    """Repeat V-cycles until ||f - L u||_2 <= rtol ||f - L u^0||_2.
+def solve(H, f, u=None, rtol=1e-8, maxit=100, nu1=2, nu2=2, omega=0.5, adjoint=False, gamma=1):
+    """Repeat cycles (gamma = 1: V, 2: W) until ||f - L u||_2 <= rtol ||f - L u^0||_2.
 
     Returns (u, iterations, history of residual norms)."""
     lv = H.finest
@@ -192,7 +198,7 @@ def solve(H, f, u=None, rtol=1e-8, maxit=100, nu1=2, nu2=2, omega=0.5, adjoint=F
     hist = [r0]
     it = 0
     while hist[-1] > rtol * r0 and it < maxit and r0 > 0:
-        u = vcycle(H, 0, u, f, nu1, nu2, omega, adjoint)
+        u = vcycle(H, 0, u, f, nu1, nu2, omega, adjoint, gamma)
         it += 1
         hist.append(np.linalg.norm(lv.residual(u, f, adjoint)))
     return u, it, hist

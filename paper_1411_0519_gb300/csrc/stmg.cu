@@ -532,7 +532,7 @@ void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* 
                         int ns) {
   Tables<T>& tb = tables<T>(lv);
   const int nm = (int)(lv.Nx / lv.n);
-  const int nch = (lv.n + stmg::kMResChunk - 1) / stmg::kMResChunk;
+  const int nch = (lv.n + stmg::mres_chunk<T>() - 1) / stmg::mres_chunk<T>();
   dim3 grid(blocks_for((int64_t)nm * nch), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
@@ -1094,8 +1094,10 @@ void coarsest_solve<float>(st_handle* h, bool adj, float* u, const float* f, con
   coarsest_mixed(h, adj, u, f);
 }
 
-// V-cycle (gamma = 1) on level L for L u = f (+ the initial-value term u0 on
-// the finest level), Section 2.  With the exact block inverse every vector is
+// Multigrid cycle on level L for L u = f (+ the initial-value term u0 on the
+// finest level), Section 2: the coarse correction equation is treated by gamma
+// cycles on level L-1 (1: V-cycle, 2: W-cycle; once when L-1 is the coarsest
+// level, whose solve is exact).  With the exact block inverse every vector is
 // in the mixed basis.  u_zero: u holds zero on entry (coarse-grid corrections).
 template <typename T>
 void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u_zero) {
@@ -1117,7 +1119,8 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u
   Level& cl = h->levels[L - 1];
   Vecs<T>& cv = vecs<T>(cl);
   restrict_to<T>(h, L, md, work, cv.f);
-  vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, true);
+  const int reps = (L - 1 == 0) ? 1 : h->opt.gamma;
+  for (int g = 0; g < reps; ++g) vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, g == 0);
   prolong_add<T>(h, L, md, cv.u, u);
   if (md) {
     smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false);
@@ -1274,6 +1277,7 @@ void st_default_options(st_options* o) {
   o->smoother = ST_SMOOTH_EXACT;
   o->nu_x = 2;
   o->omega_x = 2.0 / 3.0;
+  o->gamma = 1;
 }
 
 int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt, void* cuda_stream,
@@ -1295,6 +1299,7 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
     if (h->opt.smoother != ST_SMOOTH_EXACT && h->opt.smoother != ST_SMOOTH_VCYCLE) fail(h, ST_EINVAL, "bad smoother");
     if (h->opt.smoother == ST_SMOOTH_VCYCLE && (h->opt.nu_x < 1 || !(h->opt.omega_x > 0.0)))
       fail(h, ST_EINVAL, "bad spatial smoothing options");
+    if (h->opt.gamma < 1 || h->opt.gamma > 2) fail(h, ST_EINVAL, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
     if (h->opt.coarsest_steps < 1) h->opt.coarsest_steps = 1;
     if (!is_pow2(h->opt.coarsest_steps) || h->opt.coarsest_steps > N) fail(h, ST_EINVAL, "bad coarsest_steps");
     h->d = mesh->dim;

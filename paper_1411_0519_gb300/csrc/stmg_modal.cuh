@@ -50,6 +50,17 @@ __device__ __forceinline__ T couple(int k, T g, T mt) {
   return (!ADJ && (k & 1)) ? g - mt : g + mt;
 }
 
+// Pointer type with or without __restrict__ (kernels whose buffers may alias
+// in one use and not in another).
+template <typename P, bool RESTRICT>
+struct PtrSel {
+  typedef P* type;
+};
+template <typename P>
+struct PtrSel<P, true> {
+  typedef P* __restrict__ type;
+};
+
 // ---------------------------------------------------------------------------
 // Residual r^ = f^ - L^ u^ (forward) or f^ - L^T u^ (adjoint) in the mixed basis;
 // the operator is that of k_residual with M_h, K_h replaced by their mode-wise
@@ -59,10 +70,13 @@ __device__ __forceinline__ T couple(int k, T g, T mt) {
 // (centre), tabulated per mode on the host.  The time coupling adds
 // (-1)^k a M_1 t, t = sum_l u_{s-1,l} (adjoint: a M_1 sum_l (-1)^l u_{s+1,l});
 // at s = 0 of the forward problem t is the transformed initial value u0^ (or 0).
-// One thread per (mode, chunk of kMResChunk line positions, time step); the
+// One thread per (mode, chunk of mres_chunk<T>() line positions, time step); the
 // three-point window slides along the chunk in registers.
 // ---------------------------------------------------------------------------
-constexpr int kMResChunk = 16;
+// Line positions per thread: FP64 amortises the per-thread table loads over
+// more points; FP32 is bound by memory latency and wants more threads.
+template <typename T>
+__host__ __device__ constexpr int mres_chunk() { return sizeof(T) == 8 ? 16 : 8; }
 
 // Per-mode residual weights (host table, FP64 formed then rounded to T):
 // rw[(e) * nm + i] = w0 for e = k*Q + l, rw[(Q*Q + e) * nm + i] = w1,
@@ -73,12 +87,13 @@ __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, cons
                                                    const T* __restrict__ u0, T* __restrict__ r, int n, int nm,
                                                    int N, int s0, const T* __restrict__ rw) {
   constexpr int QQ = Q * Q;
-  const int nch = (n + kMResChunk - 1) / kMResChunk;
+  constexpr int CH = mres_chunk<T>();
+  const int nch = (n + CH - 1) / CH;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = s0 + blockIdx.y;
   if (t >= (int64_t)nm * nch || s >= N) return;
   const int i = (int)(t % nm), c = (int)(t / nm);
-  const int p0 = c * kMResChunk, p1 = min(p0 + kMResChunk, n);
+  const int p0 = c * CH, p1 = min(p0 + CH, n);
   const int64_t Nx = (int64_t)nm * n;
   T w0[QQ], w1[QQ];
 #pragma unroll
@@ -149,15 +164,16 @@ __global__ void __launch_bounds__(256) k_mresidual(const T* __restrict__ f, cons
 // DAMP the tables are unscaled and out = x; u at step s is then never read, so
 // `out` may be `u` itself (forward substitution of the coarsest solve, one
 // step per launch).  u == nullptr means a zero iterate (no coupling term, no
-// damping term).  f and out must not alias.  z is kept in `out` between the
-// sweeps.  Tables: fac[((p * 2 + w) * Q*Q + e) * nm + i] (w = 0: L_p, w = 1:
+// damping term).  f and out must not alias; with DAMP, u and out must not
+// either (both are then __restrict__).  z is kept in `out` between the sweeps.  Tables: fac[((p * 2 + w) * Q*Q + e) * nm + i] (w = 0: L_p, w = 1:
 // the inverse block), ecoef[e * nm + i], and the coupling weights a m0, a m1
 // of the residual table rw.  One thread per (mode, time step in
 // [s0, s0 + gridDim.y)).
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ, bool DAMP>
-__global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const T* u, const T* __restrict__ u0,
-                                                 T* out, int n, int nm, int N, int s0, T wc,
+__global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, typename PtrSel<const T, DAMP>::type u,
+                                                 const T* __restrict__ u0, typename PtrSel<T, DAMP>::type out,
+                                                 int n, int nm, int N, int s0, T wc,
                                                  const T* __restrict__ fac, const T* __restrict__ ecoef,
                                                  const T* __restrict__ rw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -183,6 +199,7 @@ __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const 
   T* os = out + (int64_t)s * Q * Nx + i;
   T z[Q];
   T tp = T(0), tcur = any ? trace(0) : T(0);
+#pragma unroll 2
   for (int p = 0; p < n; ++p) {
     T g[Q];
 #pragma unroll
@@ -214,6 +231,7 @@ __global__ void __launch_bounds__(128) k_msmooth(const T* __restrict__ f, const 
   for (int e = 0; e < QQ; ++e) E[e] = ecoef[(int64_t)e * nm + i];
   const T* us = (DAMP && u != nullptr) ? u + (int64_t)s * Q * Nx + i : nullptr;
   T xn[Q];
+#pragma unroll 2
   for (int p = n - 1; p >= 0; --p) {
     T t[Q];
 #pragma unroll

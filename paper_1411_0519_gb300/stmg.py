@@ -44,7 +44,8 @@ class StOptions(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("coarsening", ctypes.c_int), ("coarsest_steps", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("max_workspace_bytes", ctypes.c_size_t),
-                ("smoother", ctypes.c_int), ("nu_x", ctypes.c_int), ("omega_x", ctypes.c_double)]
+                ("smoother", ctypes.c_int), ("nu_x", ctypes.c_int), ("omega_x", ctypes.c_double),
+                ("gamma", ctypes.c_int)]
 
 
 class StmgError(RuntimeError):
@@ -130,7 +131,8 @@ class Solver:
 
     def __init__(self, dim, n, p_t, N, T, *, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50,
                  precision="fp64", coarsening="auto", coarsest_steps=1, inner_cycles=1,
-                 max_workspace_bytes=0, smoother="exact", nu_x=2, omega_x=2.0 / 3.0, stream=None, device=None):
+                 max_workspace_bytes=0, smoother="exact", nu_x=2, omega_x=2.0 / 3.0, gamma=1, stream=None,
+                 device=None):
         L = lib()
         self._lib = L
         self.dim, self.n, self.p_t, self.N, self.T = dim, n, p_t, N, float(T)
@@ -146,6 +148,7 @@ class Solver:
         opt.smoother = {"exact": ST_SMOOTH_EXACT, "vcycle": ST_SMOOTH_VCYCLE}[smoother]
         opt.nu_x = nu_x
         opt.omega_x = omega_x
+        opt.gamma = gamma
         self.options = opt
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

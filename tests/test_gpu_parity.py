@@ -165,6 +165,25 @@ def test_adjoint_solve_parity(case):
     assert rel_err(to_np(gu0), go) < 1e-10
 
 
+def test_wcycle_step_and_solve_parity(case):
+    """Cycle index gamma = 2 (W-cycle, Section 2): one cycle from the same
+    iterate, and a solve, against the oracle's W-cycle."""
+    from paper_1411_0519_gb300 import stmg
+    disc = case.H.finest.disc
+    s2 = stmg.Solver(case.d, case.n, case.p_t, case.N, case.T, rtol=1e-10, maxit=60, gamma=2)
+    try:
+        u, f = rand(disc.shape(), 72), rand(disc.shape(), 73)
+        ug = to_gpu(u)
+        s2.vcycle(ug, to_gpu(f))
+        assert rel_err(to_np(ug), multigrid.vcycle(case.H, 0, u, f, gamma=2)) < 1e-10
+        uw, it, rr = s2.solve(to_gpu(f))
+        uo, ito, _ = multigrid.solve(case.H, f, rtol=1e-10, maxit=60, gamma=2)
+        assert abs(it - ito) <= 1, (it, ito)
+        assert rr <= 1e-10 and rel_err(to_np(uw), uo) < 1e-10
+    finally:
+        s2.close()
+
+
 @pytest.mark.parametrize("coarsening,coarsest_steps", [("semi", 1), ("full", 1), ("auto", 4)])
 def test_coarsening_options_and_coarsest_substitution(coarsening, coarsest_steps):
     require_gpu()
