@@ -184,6 +184,7 @@ def roofline(solver, prof, fp32, pk, w):
     sec = v["ms"] / 1e3
     gbs = v["bytes"] / sec / 1e9
     tfl = v["flops"] / sec / 1e12
+    fp32 = fp32 and dom != "dst"   # the change of basis runs in FP64 in both forms
     alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     f_hbm = gbs / pk["hbm_gbs"]
     f_alu = tfl / alu_peak

@@ -14,7 +14,7 @@
 
 #include "stmg.h"
 #include "stmg_kernels.cuh"
-#include "stmg_modal.cuh"
+#include "stmg_sine.cuh"
 
 using stmg::TimeCoef;
 
@@ -138,11 +138,11 @@ struct Tables {
   T* sinp = nullptr;  // sin(j pi / Nf), j = 0..Nf-1
   T* twc = nullptr;   // cos(2 pi k / Nf), k = 0..Nf-1
   T* tws = nullptr;   // sin(2 pi k / Nf)
-  T* fac[2] = {nullptr, nullptr};    // line-solve LU factors (forward, adjoint)
-  T* ecoef[2] = {nullptr, nullptr};  // off-diagonal blocks E per mode
-  T* facw[2] = {nullptr, nullptr};   // damped smoother: L_j and w W_j^{-1}
-  T* ecoefw[2] = {nullptr, nullptr}; // damped smoother: E / w
-  T* rw[2] = {nullptr, nullptr};     // residual stencil weights per mode (see k_mresidual)
+  // per spatial mode (sine basis), tab[e * Nx + j], e = k * q + l; [0] forward, [1] transposed
+  T* amat[2] = {nullptr, nullptr};   // A_i = lamM_i K_tau + lamK_i M_tau
+  T* ainv[2] = {nullptr, nullptr};   // A_i^{-1}
+  T* ainvw[2] = {nullptr, nullptr};  // w A_i^{-1} (damped smoother)
+  T* lamM = nullptr;                 // lamM_i (coupling B_i = -lamM_i N_tau)
   T* ra = nullptr;     // full-coarsening pair weights to level L-1: (1 + c_k) / 2
   T* rb = nullptr;     //                                             -(1 - c_k) / 2
 };
@@ -286,101 +286,77 @@ void upload(st_handle* h, T* dst, const std::vector<double>& src) {
   check(h, cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice), "upload table");
 }
 
-// Host FP64 block-LU factors of the per-mode line systems (see k_msmooth):
-// fac[((j*2 + w)*q*q + e)*nmodes + mode] (w = 0: L_j, w = 1: W_j^{-1}),
-// ecoef[e*nmodes + mode] = E; lamM / lamK receive the per-mode coefficients
-// alpha_i, beta_i of M_h and K_h in the mixed basis.
-void line_factors(const HostTime& tm, int D, int n, double h, double tau, bool adj, std::vector<double>& fac,
-                  std::vector<double>& ecoef, std::vector<double>& lamMv, std::vector<double>& lamKv) {
+// Host FP64 per-mode time blocks of the sine basis: for spatial mode j with
+// lamM_j = prod_a m(k_a), lamK_j = sum_a kappa(k_a) prod_{b != a} m(k_b)
+// (m(k) = h/3 (2 + cos(k pi / Nf)), kappa(k) = 2/h (1 - cos(k pi / Nf)), the
+// eigenvalues of the 1D mass and stiffness matrices), A_j = lamM_j K + lamK_j M_tau
+// (K = K_tau, transposed for the adjoint) and its inverse (Gauss-Jordan with
+// partial pivoting), laid out tab[e * Nx + j].
+void mode_blocks(const HostTime& tm, int D, int n, double h, double tau, bool adj, std::vector<double>& amat,
+                 std::vector<double>& ainv, std::vector<double>& lamMv) {
   const int q = tm.q, qq = q * q;
   const int Nf = n + 1;
-  int64_t nmodes = 1;
-  for (int a = 0; a < D - 1; ++a) nmodes *= n;
+  int64_t Nx = 1;
+  for (int a = 0; a < D; ++a) Nx *= n;
   std::vector<double> m1(n), k1(n);
   for (int k = 1; k <= n; ++k) {
     const double c = std::cos(k * M_PI / Nf);
     m1[k - 1] = h / 3.0 * (2.0 + c);
     k1[k - 1] = 2.0 / h * (1.0 - c);
   }
-  fac.assign((size_t)n * 2 * qq * nmodes, 0.0);
-  ecoef.assign((size_t)qq * nmodes, 0.0);
-  lamMv.assign((size_t)nmodes, 1.0);
-  lamKv.assign((size_t)nmodes, 0.0);
-  std::vector<double> K(qq), Dg(qq), E(qq), W(qq), Wi(qq), L(qq), tmp(qq);
-  for (int k = 0; k < q; ++k)
-    for (int l = 0; l < q; ++l) K[k * q + l] = adj ? tm.K[l * q + k] : tm.K[k * q + l];
-  auto inv = [q](const std::vector<double>& A, std::vector<double>& X) {
+  amat.assign((size_t)qq * Nx, 0.0);
+  ainv.assign((size_t)qq * Nx, 0.0);
+  lamMv.assign((size_t)Nx, 0.0);
+  std::vector<double> A(qq), X(qq), M(qq);
+  for (int64_t j = 0; j < Nx; ++j) {
+    int idx[3] = {0, 0, 0};
+    int64_t rest = j;
+    for (int a = 0; a < D; ++a) {
+      idx[a] = (int)(rest % n);
+      rest /= n;
+    }
+    double lamM = 1.0, lamK = 0.0;
+    for (int a = 0; a < D; ++a) {
+      double prod = k1[idx[a]];
+      for (int b = 0; b < D; ++b)
+        if (b != a) prod *= m1[idx[b]];
+      lamK += prod;
+      lamM *= m1[idx[a]];
+    }
+    lamMv[j] = lamM;
+    for (int k = 0; k < q; ++k)
+      for (int l = 0; l < q; ++l)
+        A[k * q + l] = lamM * (adj ? tm.K[l * q + k] : tm.K[k * q + l]) + (k == l ? lamK * tau * tm.Mh[k] : 0.0);
     // Gauss-Jordan with partial pivoting on a q x q matrix
-    std::vector<double> M(A);
+    M = A;
     for (int i = 0; i < q; ++i)
-      for (int j = 0; j < q; ++j) X[i * q + j] = (i == j) ? 1.0 : 0.0;
+      for (int c = 0; c < q; ++c) X[i * q + c] = (i == c) ? 1.0 : 0.0;
     for (int c = 0; c < q; ++c) {
       int p = c;
       for (int r = c + 1; r < q; ++r)
         if (std::fabs(M[r * q + c]) > std::fabs(M[p * q + c])) p = r;
       if (p != c)
-        for (int j = 0; j < q; ++j) {
-          std::swap(M[c * q + j], M[p * q + j]);
-          std::swap(X[c * q + j], X[p * q + j]);
+        for (int i = 0; i < q; ++i) {
+          std::swap(M[c * q + i], M[p * q + i]);
+          std::swap(X[c * q + i], X[p * q + i]);
         }
-      const double d = 1.0 / M[c * q + c];
-      for (int j = 0; j < q; ++j) {
-        M[c * q + j] *= d;
-        X[c * q + j] *= d;
+      const double dv = 1.0 / M[c * q + c];
+      for (int i = 0; i < q; ++i) {
+        M[c * q + i] *= dv;
+        X[c * q + i] *= dv;
       }
       for (int r = 0; r < q; ++r) {
         if (r == c) continue;
-        const double f = M[r * q + c];
-        for (int j = 0; j < q; ++j) {
-          M[r * q + j] -= f * M[c * q + j];
-          X[r * q + j] -= f * X[c * q + j];
+        const double fct = M[r * q + c];
+        for (int i = 0; i < q; ++i) {
+          M[r * q + i] -= fct * M[c * q + i];
+          X[r * q + i] -= fct * X[c * q + i];
         }
       }
     }
-  };
-  for (int64_t mode = 0; mode < nmodes; ++mode) {
-    double lamM = 1.0, lamK = 0.0;
-    if (D == 2) {
-      lamM = m1[mode];
-      lamK = k1[mode];
-    } else if (D == 3) {
-      const int ix = (int)(mode % n), iy = (int)(mode / n);
-      lamM = m1[ix] * m1[iy];
-      lamK = k1[ix] * m1[iy] + m1[ix] * k1[iy];
-    }
-    lamMv[mode] = lamM;
-    lamKv[mode] = lamK;
-    for (int k = 0; k < q; ++k)
-      for (int l = 0; l < q; ++l) {
-        const double mt = (k == l) ? tau * tm.Mh[k] : 0.0;
-        Dg[k * q + l] = lamM * (4.0 * h / 6.0) * K[k * q + l] + mt * (lamM * 2.0 / h + lamK * 4.0 * h / 6.0);
-        E[k * q + l] = lamM * (h / 6.0) * K[k * q + l] + mt * (-lamM / h + lamK * h / 6.0);
-      }
-    for (int e = 0; e < qq; ++e) ecoef[(size_t)e * nmodes + mode] = E[e];
-    W = Dg;
-    for (int j = 0; j < n; ++j) {
-      if (j > 0) {
-        // L_j = E W_{j-1}^{-1};  W_j = Dg - L_j E
-        for (int a = 0; a < q; ++a)
-          for (int b = 0; b < q; ++b) {
-            double acc = 0.0;
-            for (int c = 0; c < q; ++c) acc += E[a * q + c] * Wi[c * q + b];
-            L[a * q + b] = acc;
-          }
-        for (int a = 0; a < q; ++a)
-          for (int b = 0; b < q; ++b) {
-            double acc = Dg[a * q + b];
-            for (int c = 0; c < q; ++c) acc -= L[a * q + c] * E[c * q + b];
-            W[a * q + b] = acc;
-          }
-      } else {
-        std::fill(L.begin(), L.end(), 0.0);
-      }
-      inv(W, Wi);
-      for (int e = 0; e < qq; ++e) {
-        fac[(((size_t)j * 2 + 0) * qq + e) * nmodes + mode] = L[e];
-        fac[(((size_t)j * 2 + 1) * qq + e) * nmodes + mode] = Wi[e];
-      }
+    for (int e = 0; e < qq; ++e) {
+      amat[(size_t)e * Nx + j] = A[e];
+      ainv[(size_t)e * Nx + j] = X[e];
     }
   }
 }
@@ -401,49 +377,20 @@ void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
   upload(h, tb.twc, tc);
   upload(h, tb.tws, ts);
   for (int adj = 0; adj < 2; ++adj) {
-    std::vector<double> fac, ec, lm, lk;
-    line_factors(h->tm, h->d, n, lv.h, lv.tau, adj != 0, fac, ec, lm, lk);
-    tb.fac[adj] = dalloc<T>(h, fac.size());
-    tb.ecoef[adj] = dalloc<T>(h, ec.size());
-    upload(h, tb.fac[adj], fac);
-    upload(h, tb.ecoef[adj], ec);
-    // damped tables: w W^{-1} and E / w, so the backward sweep yields w x
-    const double w = h->opt.omega;
-    const int qq = h->q * h->q;
-    const int64_t nm = (int64_t)lm.size();
-    std::vector<double> facw(fac), ecw(ec);
-    for (int j = 0; j < n; ++j)
-      for (int64_t e = 0; e < (int64_t)qq * nm; ++e) facw[((size_t)j * 2 + 1) * qq * nm + e] *= w;
-    for (double& x : ecw) x /= w;
-    tb.facw[adj] = dalloc<T>(h, facw.size());
-    tb.ecoefw[adj] = dalloc<T>(h, ecw.size());
-    upload(h, tb.facw[adj], facw);
-    upload(h, tb.ecoefw[adj], ecw);
-    // residual weights per mode: row k, column l of
-    // a K[k,l] M_1 + delta_kl tau Mh[k] (a K_1 + b M_1) as (neighbour w0, centre w1),
-    // then the coupling weights a h/6, a 2h/3
-    const int q = h->q;
-    const double hl = lv.h, m0 = hl / 6.0, m1 = 2.0 * hl / 3.0;
-    std::vector<double> rw((size_t)(2 * qq + 2) * nm);
-    for (int64_t i = 0; i < nm; ++i) {
-      const double a = lm[i], b = lk[i];
-      for (int k = 0; k < q; ++k)
-        for (int l = 0; l < q; ++l) {
-          const double cK = a * (adj ? h->tm.K[l * q + k] : h->tm.K[k * q + l]);
-          double w0 = cK * m0, w1 = cK * m1;
-          if (k == l) {
-            const double d = lv.tau * h->tm.Mh[k];
-            w0 += d * (b * m0 - a / hl);
-            w1 += d * (2.0 * a / hl + b * m1);
-          }
-          rw[(size_t)(k * q + l) * nm + i] = w0;
-          rw[(size_t)(qq + k * q + l) * nm + i] = w1;
-        }
-      rw[(size_t)(2 * qq) * nm + i] = a * m0;
-      rw[(size_t)(2 * qq + 1) * nm + i] = a * m1;
+    std::vector<double> am, ai, lm;
+    mode_blocks(h->tm, h->d, n, lv.h, lv.tau, adj != 0, am, ai, lm);
+    std::vector<double> aw(ai);
+    for (double& x : aw) x *= h->opt.omega;
+    tb.amat[adj] = dalloc<T>(h, am.size());
+    tb.ainv[adj] = dalloc<T>(h, ai.size());
+    tb.ainvw[adj] = dalloc<T>(h, aw.size());
+    upload(h, tb.amat[adj], am);
+    upload(h, tb.ainv[adj], ai);
+    upload(h, tb.ainvw[adj], aw);
+    if (adj == 0) {
+      tb.lamM = dalloc<T>(h, lm.size());
+      upload(h, tb.lamM, lm);
     }
-    tb.rw[adj] = dalloc<T>(h, rw.size());
-    upload(h, tb.rw[adj], rw);
   }
   if (lv.coarsen_full) {
     // coarse mode k (k = 1..nc) pairs with fine modes k and Nf - k, c_k = cos(k pi / Nf)
@@ -531,43 +478,37 @@ template <typename T, int D, int Q>
 void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0,
                         int ns) {
   Tables<T>& tb = tables<T>(lv);
-  const int nm = (int)(lv.Nx / lv.n);
-  const int nch = (lv.n + stmg::mres_chunk<T>() - 1) / stmg::mres_chunk<T>();
-  dim3 grid(blocks_for((int64_t)nm * nch), 1);
+  dim3 grid(blocks_for(lv.Nx), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
     if (adj)
-      stmg::k_mresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, nm, lv.N, s0 + c,
-                                                                      tb.rw[1]);
+      stmg::k_fresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c,
+                                                                      tb.amat[1], tb.lamM);
     else
-      stmg::k_mresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.n, nm, lv.N, s0 + c,
-                                                                       tb.rw[0]);
+      stmg::k_fresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c,
+                                                                       tb.amat[0], tb.lamM);
   }
 }
-
-constexpr int kSmoothThreads = 128;
 
 template <typename T, int D, int Q>
 void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out,
                       int s0, int ns) {
   Tables<T>& tb = tables<T>(lv);
-  const int nm = (int)(lv.Nx / lv.n);
   const int a = adj ? 1 : 0;
-  const T* fac = damp ? tb.facw[a] : tb.fac[a];
-  const T* ec = damp ? tb.ecoefw[a] : tb.ecoef[a];
+  const T* ai = damp ? tb.ainvw[a] : tb.ainv[a];
   const T wc = (T)(1.0 - h->opt.omega);
-  dim3 grid(blocks_for(nm, kSmoothThreads), 1);
+  dim3 grid(blocks_for(lv.Nx), 1);
   for (int c = 0; c < ns; c += 65535) {
     grid.y = std::min(65535, ns - c);
-#define STMG_MSMOOTH(ADJ, DAMP)                                                                                  \
-  stmg::k_msmooth<T, Q, ADJ, DAMP><<<grid, kSmoothThreads, 0, h->stream>>>(f, u, u0, out, lv.n, nm, lv.N, s0 + c, \
-                                                                           wc, fac, ec, tb.rw[a])
+#define STMG_FSMOOTH(ADJ, DAMP)                                                                              \
+  stmg::k_fsmooth<T, Q, ADJ, DAMP><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c, wc, ai, \
+                                                                     tb.lamM)
     if (adj) {
-      if (damp) STMG_MSMOOTH(true, true); else STMG_MSMOOTH(true, false);
+      if (damp) STMG_FSMOOTH(true, true); else STMG_FSMOOTH(true, false);
     } else {
-      if (damp) STMG_MSMOOTH(false, true); else STMG_MSMOOTH(false, false);
+      if (damp) STMG_FSMOOTH(false, true); else STMG_FSMOOTH(false, false);
     }
-#undef STMG_MSMOOTH
+#undef STMG_FSMOOTH
   }
 }
 
@@ -581,7 +522,7 @@ void launch_restrict_t(st_handle* h, Level& fine, const Level& coarse, bool moda
   if (!fine.coarsen_full)
     stmg::k_restrict<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
   else if (modal)
-    stmg::k_mrestrict<T, D, Q><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N,
+    stmg::k_frestrict<T, D, Q><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N,
                                                                   tables<T>(fine).ra, tables<T>(fine).rb, tc);
   else
     stmg::k_restrict<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
@@ -594,12 +535,12 @@ void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, bool modal
   if (!fine.coarsen_full)
     stmg::k_prolong<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
   else if (modal) {
-    // pair weights of the prolongation are 2 ra, 2 rb per transformed axis: fold 2^(D-1) into R^T
+    // pair weights of the prolongation are 2 ra, 2 rb per axis: fold 2^D into R^T
     for (int i = 0; i < Q * Q; ++i) {
-      tc.R1[i] *= (T)(1 << (D - 1));
-      tc.R2[i] *= (T)(1 << (D - 1));
+      tc.R1[i] *= (T)(1 << D);
+      tc.R2[i] *= (T)(1 << D);
     }
-    stmg::k_mprolong<T, D, Q><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N,
+    stmg::k_fprolong<T, D, Q><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N,
                                                                  tables<T>(fine).ra, tables<T>(fine).rb, tc);
   }
   else
@@ -684,9 +625,10 @@ void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const 
                int ns = -1) {
   if (ns < 0) ns = lv.N;
   const double Q = h->q, nodes = (double)ns * lv.Nx;
-  // per node: Q neighbour sums, 2 Q^2 stencil FMA, trace Q FMA + M_1 (4), Q coupling FMA
+  // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i u Q^2 FMA;
+  // bytes: read u, f, write r (+ u0)
   Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)),
-          nodes * (4.0 * Q * Q + 5.0 * Q + 4.0), 1, level_of(h, lv));
+          nodes * (2.0 * Q * Q + 2.0 * Q), 1, level_of(h, lv));
   STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
@@ -699,9 +641,8 @@ void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* 
   if (ns < 0) ns = lv.N;
   const double Q = h->q, nodes = (double)ns * lv.Nx;
   const double passes = 2.0 + ((damp && u) ? 1.0 : 0.0);   // read f (and u), write out
-  // per node: trace 2Q + 4, coupling 2Q, forward 2Q^2, backward 4Q^2, damping 3Q
-  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * (6.0 * Q * Q + 7.0 * Q + 4.0), 1,
-          level_of(h, lv));
+  // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i^{-1} g Q^2 FMA, damping Q FMA
+  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * (2.0 * Q * Q + 4.0 * Q), 1, level_of(h, lv));
   STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, f, u, u0, out, s0, ns);
 }
 
@@ -710,7 +651,7 @@ void restrict_to(st_handle* h, int L, bool modal, const T* r, T* fc) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
-  const double ns = fine.coarsen_full ? (modal ? std::pow(2.0, h->d - 1) * 3.0 : std::pow(3.0, h->d)) : 1.0;
+  const double ns = fine.coarsen_full ? std::pow(modal ? 2.0 : 3.0, h->d) : 1.0;
   Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * h->q), 1, L);
   STMG_DISPATCH(launch_restrict_t, h, fine, coarse, modal, r, fc);
 }
@@ -720,7 +661,7 @@ void prolong_add(st_handle* h, int L, bool modal, const T* ec, T* uf) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
-  const double ns = fine.coarsen_full ? (modal ? 2.0 : std::pow(2.0, h->d)) : 1.0;
+  const double ns = fine.coarsen_full ? (modal ? 1.0 : std::pow(2.0, h->d)) : 1.0;
   Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + h->q), 1, L);
   STMG_DISPATCH(launch_prolong_t, h, fine, coarse, modal, ec, uf);
 }
@@ -758,18 +699,23 @@ size_t dst_reg_smem() {
   const int rows = dst_reg_threads<T>() / Lay::G;
   return ((size_t)Lay::TAB + (size_t)rows * Lay::RS) * sizeof(T);
 }
+// k_dst_cols_reg: the same plus one int64 line base per line.
+template <typename T, int LP, int LG>
+size_t dst_cols_reg_smem() {
+  using Lay = stmg::DstRegLayout<LP, LG>;
+  return dst_reg_smem<T, LP, LG>() + (size_t)(dst_reg_threads<T>() / Lay::G) * sizeof(int64_t);
+}
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
 // Opt the sine-transform kernels into the dynamic shared memory they need for
-// the row lengths this hierarchy uses (only levels with d >= 2 transform).
+// the line lengths this hierarchy uses (every level transforms along every axis).
 template <typename T>
 void dst_set_smem_limits(st_handle* h) {
-  if (h->d < 2) return;
   int maxNf = 2;
   for (const Level& l : h->levels) maxNf = std::max(maxNf, l.n + 1);
   auto set = [&](const void* fn, size_t bytes) {
-    if (bytes > kMaxSmem) fail(h, ST_EINVAL, "n too large for the sine-transform kernels (n <= 511)");
+    if (bytes > kMaxSmem) fail(h, ST_EINVAL, "n too large for the sine-transform kernels");
     check(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
           "cudaFuncSetAttribute");
   };
@@ -784,10 +730,17 @@ void dst_set_smem_limits(st_handle* h) {
       set((const void*)stmg::k_dst_rows<T>, dst_rows_smem<T>(Nf));
     }
   }
-  if (h->d == 3) {   // y axis of 3D levels: column tiles of W = 16 (FP64, Nf >= 512) or 32 lines
+  if (h->d >= 2) {   // y (and z) axes: register transform for 64 <= Nf <= 512, else column tiles
     int max16 = 0, max32 = 0;
     for (const Level& l : h->levels) {
       const int Nf = l.n + 1;
+      if (Nf >= 64 && Nf <= 512) {
+        if (Nf == 64) set((const void*)stmg::k_dst_cols_reg<T, 3, 2>, dst_cols_reg_smem<T, 3, 2>());
+        if (Nf == 128) set((const void*)stmg::k_dst_cols_reg<T, 3, 3>, dst_cols_reg_smem<T, 3, 3>());
+        if (Nf == 256) set((const void*)stmg::k_dst_cols_reg<T, 4, 3>, dst_cols_reg_smem<T, 4, 3>());
+        if (Nf == 512) set((const void*)stmg::k_dst_cols_reg<T, 4, 4>, dst_cols_reg_smem<T, 4, 4>());
+        continue;
+      }
       if (sizeof(T) == 8 && Nf >= 512) max16 = std::max(max16, Nf); else max32 = std::max(max32, Nf);
     }
     if (max16) set((const void*)stmg::k_dst_cols<T, 16>, dst_cols_smem<T, 16>(max16));
@@ -807,12 +760,12 @@ double dst_line_flops(int n) {
   return 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
 }
 
-// scale * DST-I along the first d-1 spatial axes of `slabs` consecutive
+// scale * DST-I along every spatial axis of `slabs` consecutive
 // spatial fields of level lv (in place; `scale` is applied once per axis).
 template <typename T>
 void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale) {
   const int n = lv.n, Nf = n + 1;
-  const int naxes = h->d - 1;
+  const int naxes = h->d;
   int logh = 0;
   while ((1 << (logh + 1)) <= Nf / 2) ++logh;
   Tables<T>& tb = tables<T>(lv);
@@ -846,6 +799,29 @@ void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale
       const unsigned grid = (unsigned)((nlines + kDstRowsPerCta - 1) / kDstRowsPerCta);
       stmg::k_dst_rows<T><<<grid, kDstWarps * 32, dst_rows_smem<T>(Nf), h->stream>>>(data, n, logh, nlines,
                                                                                      kDstRowsPerCta, scale, dt);
+    } else if (Nf >= 64 && Nf <= 512) {
+      const int thr = dst_reg_threads<T>();
+      const int G = (Nf == 64) ? 4 : (Nf == 512) ? 16 : 8;
+      const int rows = thr / G;
+      const unsigned grid = (unsigned)((nlines + rows - 1) / rows);
+      switch (Nf) {
+        case 64:
+          stmg::k_dst_cols_reg<T, 3, 2><<<grid, thr, dst_cols_reg_smem<T, 3, 2>(), h->stream>>>(data, n, nlines, inner,
+                                                                                               scale, dt);
+          break;
+        case 128:
+          stmg::k_dst_cols_reg<T, 3, 3><<<grid, thr, dst_cols_reg_smem<T, 3, 3>(), h->stream>>>(data, n, nlines, inner,
+                                                                                               scale, dt);
+          break;
+        case 256:
+          stmg::k_dst_cols_reg<T, 4, 3><<<grid, thr, dst_cols_reg_smem<T, 4, 3>(), h->stream>>>(data, n, nlines, inner,
+                                                                                               scale, dt);
+          break;
+        default:
+          stmg::k_dst_cols_reg<T, 4, 4><<<grid, thr, dst_cols_reg_smem<T, 4, 4>(), h->stream>>>(data, n, nlines, inner,
+                                                                                               scale, dt);
+          break;
+      }
     } else if (sizeof(T) == 8 && Nf >= 512) {
       const unsigned grid = (unsigned)((nlines + 15) / 16);
       stmg::k_dst_cols<T, 16><<<grid, kDstWarps * 32, dst_cols_smem<T, 16>(Nf), h->stream>>>(data, n, logh, nlines,
@@ -859,22 +835,20 @@ void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale
   }
 }
 
-// Change of basis of `slabs` spatial fields of level lv: nodes -> mixed basis
-// (S, the unnormalised DST-I along the first d-1 axes) and back (S^{-1} =
-// (2/Nf)^{d-1} S).  No-ops in 1D.
+// Change of basis of `slabs` spatial fields of level lv: nodes -> sine basis
+// (S, the unnormalised DST-I along every axis) and back (S^{-1} = (2/Nf)^d S).
 template <typename T>
 void to_modal(st_handle* h, Level& lv, T* data, int64_t slabs) {
-  if (h->d > 1) dst_axes<T>(h, lv, data, slabs, 1.0);
+  dst_axes<T>(h, lv, data, slabs, 1.0);
 }
 template <typename T>
 void from_modal(st_handle* h, Level& lv, T* data, int64_t slabs) {
-  if (h->d > 1) dst_axes<T>(h, lv, data, slabs, 2.0 / (lv.n + 1));
+  dst_axes<T>(h, lv, data, slabs, 2.0 / (lv.n + 1));
 }
 
 // d = A^{-1} r on nodes, time steps [s0, s0 + ns) (exact block inverse,
-// Section 3.1): sine transform along the first d-1 axes, one block-tridiagonal
-// solve per mode along the last axis, inverse transform.  r is overwritten
-// (transformed); r and d must differ.
+// Section 3.1): sine transform along every axis, one q x q solve per mode,
+// inverse transform.  r is overwritten (transformed); r and d must differ.
 template <typename T>
 void block_solve(st_handle* h, Level& lv, bool adj, T* r, T* d, int s0, int ns) {
   const int64_t off = (int64_t)s0 * h->q * lv.Nx;

@@ -689,6 +689,56 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int 
   }
 }
 
+// y / z axis with the register transform: line g = (outer, in), in < inner,
+// starts at outer * inner * n + in and has stride inner.  A CTA takes the
+// threads / G consecutive lines g (consecutive x positions, so each load and
+// store of a line position is one contiguous segment), de-interleaves them into
+// the per-line buffers of k_dst_rows_reg, transforms each line with a group of
+// G threads and writes them back.  Shared memory: the k_dst_rows_reg layout
+// followed by one int64 line base per line.
+template <typename T, int LP, int LG>
+__global__ void __launch_bounds__(256) k_dst_cols_reg(T* __restrict__ data, int n, int64_t nlines, int64_t inner,
+                                                      T scale, DstTables<T> tb) {
+  using Lay = DstRegLayout<LP, LG>;
+  constexpr int BS = Lay::BS, RS = Lay::RS;
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* rows = sm + Lay::TAB;
+  const int tid = threadIdx.x;
+  const int rpc = blockDim.x >> LG;
+  int64_t* base = reinterpret_cast<int64_t*>(rows + (int64_t)rpc * RS);
+  dst_reg_stage_tables<T, LP, LG>(sm, tb);
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const int rcount = (int)((nlines - r0) < rpc ? (nlines - r0) : rpc);
+  if (tid < rcount) {
+    const int64_t g = r0 + tid;
+    const int64_t outer = g / inner, in = g - outer * inner;
+    base[tid] = outer * inner * n + in;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < rpc * n; idx += blockDim.x) {   // consecutive threads: consecutive lines
+    const int r = idx % rpc, c = idx / rpc;
+    if (r < rcount) {
+      const int j = c + 1;
+      rows[r * RS + (j & 1) * BS + (j >> 1)] = data[base[r] + (int64_t)c * inner];
+    }
+  }
+  if (tid < rpc) rows[tid * RS] = T(0);
+  __syncthreads();
+  const int rr = tid >> LG, g = tid & (Lay::G - 1);
+  dst_reg_row<T, LP, LG>(rows + rr * RS, rows + rr * RS + BS, g, sm);   // lines >= rcount are not stored
+  __syncthreads();
+  const bool unit = scale == T(1);
+  for (int idx = tid; idx < rpc * n; idx += blockDim.x) {
+    const int r = idx % rpc, c = idx / rpc;
+    if (r < rcount) {
+      const int j = c + 1;
+      const T v = rows[r * RS + (j & 1) * BS + (j >> 1)];
+      data[base[r] + (int64_t)c * inner] = unit ? v : scale * v;
+    }
+  }
+}
+
 // y / z axis: line g = (outer, in), in < inner, starts at outer * inner * n + in
 // and has stride inner.  Each CTA stages W consecutive lines.
 // Shared memory: 2 Nf (tables) + W int64 bases + W (Nf + 1) tile + nwarps Nf.

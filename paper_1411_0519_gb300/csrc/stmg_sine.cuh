@@ -1,0 +1,272 @@
+// Kernels of the cycle with the exact block inverse, in the sine basis.
+//
+// The sine vectors diagonalise M_1 and K_1 (Section 3.1).  With v^ = S v
+// (S = DST-I along every spatial axis, unnormalised), M_h and K_h act on
+// spatial mode i = (k_1, .., k_d) as the scalars
+//   lamM_i = prod_a m(k_a),  lamK_i = sum_a kappa(k_a) prod_{b != a} m(k_b),
+// m(k) = h/3 (2 + cos(k pi / Nf)), kappa(k) = 2/h (1 - cos(k pi / Nf)).  So the
+// space-time system decouples into one time problem per mode: the block rows
+//   A_i u_s + B_i u_{s-1} = f_s,  A_i = lamM_i K_tau + lamK_i M_tau,  B_i = -lamM_i N_tau
+// (q x q blocks, q = p_t + 1), and the smoother's exact block inverse is one
+// q x q solve per (mode, step).  The full-coarsening transfer pairs modes along
+// every axis: for linear interpolation P,
+//   P phi^c_k = (1+c_k)/2 phi^f_k - (1-c_k)/2 phi^f_{Nf-k},  c_k = cos(k pi / Nf),
+// so with R = P^T a coarse mode takes ra_k r^_k + rb_k r^_{Nf-k} per axis
+// (ra = (1+c)/2, rb = -(1-c)/2), prolongation the same weights doubled (S P S^{-1}),
+// and mode Nf/2 of each axis has no coarse partner.  The iterates of the cycle
+// are the images under S of those of the same cycle written on nodes: one
+// forward transform of the data and one inverse transform of the result per solve.
+//
+// Layout: index ((s * Q + l) * Nx + j): time step s, time dof l, spatial mode j
+// (first axis fastest, Nx = n^d modes).  One thread per (mode, step), consecutive
+// threads on consecutive modes, so every access is coalesced; the per-mode q x q
+// blocks are tabulated on the host as tab[e * Nx + j], e = k * Q + l.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "stmg_kernels.cuh"
+
+namespace stmg {
+
+// Time traces of a step with the Legendre slab basis (Section 1), whose end
+// values are psi_k(t_{n-1}^+) = (-1)^k and psi_k(t_n^-) = 1: the coupling of
+// step s to s-1 (forward) uses sum_l u_{s-1,l} and enters row k with sign
+// (-1)^k; the transposed coupling to s+1 uses sum_l (-1)^l u_{s+1,l} and
+// enters every row with sign +1.  Additions only, no multiplies.
+template <typename T, int Q, bool ADJ>
+__device__ __forceinline__ T step_trace(const T* nb, int64_t Nx, int64_t o) {
+  T v = nb[o];
+#pragma unroll
+  for (int l = 1; l < Q; ++l) {
+    const T x = nb[(int64_t)l * Nx + o];
+    v = (ADJ && (l & 1)) ? v - x : v + x;
+  }
+  return v;
+}
+
+template <typename T, bool ADJ>
+__device__ __forceinline__ T couple(int k, T g, T mt) {
+  return (!ADJ && (k & 1)) ? g - mt : g + mt;
+}
+
+// Pointer type with or without __restrict__ (kernels whose buffers may alias
+// in one use and not in another).
+template <typename P, bool RESTRICT>
+struct PtrSel {
+  typedef P* type;
+};
+template <typename P>
+struct PtrSel<P, true> {
+  typedef P* __restrict__ type;
+};
+
+// lamM_i times the coupling trace of step s (forward: u_{s-1}, or the
+// transformed initial value u0^ at s = 0; adjoint: u_{s+1}); 0 without one.
+template <typename T, int Q, bool ADJ>
+__device__ __forceinline__ T coupling(const T* u, const T* __restrict__ u0, const T* __restrict__ lamM, int64_t Nx,
+                                      int N, int s, int64_t j) {
+  const T* nb = nullptr;
+  if (u != nullptr) {
+    if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
+    if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
+  }
+  if (nb != nullptr) return lamM[j] * step_trace<T, Q, ADJ>(nb, Nx, j);
+  if (!ADJ && s == 0 && u0 != nullptr) return lamM[j] * u0[j];
+  return T(0);
+}
+
+// ---------------------------------------------------------------------------
+// Residual r^ = f^ - L^ u^ (forward) or f^ - L^T u^ (adjoint) in the sine basis:
+//   r_{s,k} = f_{s,k} - sum_l A_i[k,l] u_{s,l} + (-1)^k lamM_i sum_l u_{s-1,l}
+// (adjoint: A_i^T and + lamM_i sum_l (-1)^l u_{s+1,l}); at s = 0 of the forward
+// problem the trace is the transformed initial value u0^ (or 0).
+// amat[e * Nx + j] = A_i[k,l] (adjoint tables hold A_i^T).  One thread per
+// (mode, step in [s0, s0 + gridDim.y)).
+// ---------------------------------------------------------------------------
+template <typename T, int Q, bool ADJ>
+__global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, const T* __restrict__ u,
+                                                   const T* __restrict__ u0, T* __restrict__ r, int64_t Nx, int N,
+                                                   int s0, const T* __restrict__ amat, const T* __restrict__ lamM) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N) return;
+  const T c = coupling<T, Q, ADJ>(u, u0, lamM, Nx, N, s, j);
+  const T* us = u + (int64_t)s * Q * Nx + j;
+  T uv[Q];
+#pragma unroll
+  for (int l = 0; l < Q; ++l) uv[l] = us[(int64_t)l * Nx];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    T acc = couple<T, ADJ>(k, f[idx], c);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc -= amat[(int64_t)(k * Q + l) * Nx + j] * uv[l];
+    r[idx] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One damped block-Jacobi step with the exact block inverse (eq. chap4_smoother,
+// Section 3.1): out = (1 - w) u + w A_i^{-1} (f - B_i u_prev) per (mode, step);
+// the block inverse of the block row removes A u and only the rank-one time
+// coupling is applied.  DAMP: ainv holds w A_i^{-1} and out = that + wc u
+// (wc = 1 - w); without DAMP ainv holds A_i^{-1}, out = A_i^{-1}(f - B_i u_prev)
+// and u at step s is never read, so `out` may be `u` itself (forward
+// substitution of the coarsest solve, one step per launch).  u == nullptr is a
+// zero iterate.  With DAMP, u and out must differ (steps read their
+// neighbour's old value).  One thread per (mode, step in [s0, s0 + gridDim.y)).
+// ---------------------------------------------------------------------------
+template <typename T, int Q, bool ADJ, bool DAMP>
+__global__ void __launch_bounds__(256) k_fsmooth(const T* __restrict__ f, typename PtrSel<const T, DAMP>::type u,
+                                                 const T* __restrict__ u0, typename PtrSel<T, DAMP>::type out,
+                                                 int64_t Nx, int N, int s0, T wc, const T* __restrict__ ainv,
+                                                 const T* __restrict__ lamM) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N) return;
+  const T c = coupling<T, Q, ADJ>(u, u0, lamM, Nx, N, s, j);
+  T g[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) g[k] = couple<T, ADJ>(k, f[((int64_t)s * Q + k) * Nx + j], c);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    T x = ainv[(int64_t)(k * Q) * Nx + j] * g[0];
+#pragma unroll
+    for (int l = 1; l < Q; ++l) x += ainv[(int64_t)(k * Q + l) * Nx + j] * g[l];
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    if (DAMP && u != nullptr) x += wc * u[idx];
+    out[idx] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full-coarsening restriction in the sine basis (eqs. chap4_restrictionTime,
+// chap4_spaceRestrictionProlongation): coarse mode (c_1, .., c_d) takes the
+// 2^d fine modes with index c_a or nf - 1 - c_a per axis, weighted by the
+// products of ra / rb, then the time blocks
+//   fc[m, k] = sum_l R1[k,l] (.)[2m, l] + R2[k,l] (.)[2m+1, l].
+// Semi coarsening is the identity in space and uses k_restrict<.., false>.
+// One thread per coarse (mode, step).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ int64_t pow_d(int64_t n) {
+  return D == 1 ? n : D == 2 ? n * n : n * n * n;
+}
+
+template <typename T, int D, int Q>
+__global__ void k_frestrict(const T* __restrict__ r, T* __restrict__ fc, int nf, int nc, int Nc,
+                            const T* __restrict__ ra, const T* __restrict__ rb, TimeCoef<T, Q> tc) {
+  const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (J >= Nxc || m >= Nc) return;
+  constexpr int NT = 1 << D;
+  int c[3] = {0, 0, 0};
+  {
+    int64_t rest = J;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      c[a] = (int)(rest % nc);
+      rest /= nc;
+    }
+  }
+  T wa[3], wb[3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    wa[a] = ra[c[a]];
+    wb[a] = rb[c[a]];
+  }
+  int64_t src[NT];
+  T wm[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    int64_t idx = 0, stride = 1;
+    T w = T(1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const bool hi = (t >> a) & 1;
+      idx += stride * (hi ? nf - 1 - c[a] : c[a]);
+      w = (a == 0) ? (hi ? wb[a] : wa[a]) : w * (hi ? wb[a] : wa[a]);
+      stride *= nf;
+    }
+    src[t] = idx;
+    wm[t] = w;
+  }
+  T acc2[2][Q];
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const T* rl = r + ((int64_t)(2 * m + sl) * Q + l) * Nxf;
+      T acc = wm[0] * rl[src[0]];
+#pragma unroll
+      for (int t = 1; t < NT; ++t) acc += wm[t] * rl[src[t]];
+      acc2[sl][l] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    T acc = T(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc += tc.R1[k * Q + l] * acc2[0][l] + tc.R2[k * Q + l] * acc2[1][l];
+    fc[((int64_t)m * Q + k) * Nxc + J] = acc;
+  }
+}
+
+// Full-coarsening prolongation and correction u^_f += (P e)^ in the sine basis:
+// per axis fine mode i < nc takes 2 ra_i e^_i, fine mode i > nc takes
+// 2 rb_j e^_j (j = nf - 1 - i), mode nc takes nothing; in time R_sl^T.  The
+// host passes the time blocks pre-multiplied by 2^d, so the pair weights are
+// ra, rb themselves.  One thread per fine (mode, step).
+template <typename T>
+__device__ __forceinline__ bool mode_source(int i, int nf, int nc, const T* __restrict__ ra,
+                                            const T* __restrict__ rb, int& src, T& wgt) {
+  if (i < nc) {
+    src = i;
+    wgt = ra[i];
+    return true;
+  }
+  if (i > nc) {
+    src = nf - 1 - i;
+    wgt = rb[src];
+    return true;
+  }
+  return false;
+}
+
+template <typename T, int D, int Q>
+__global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf, int nc, int Nf_steps,
+                           const T* __restrict__ ra, const T* __restrict__ rb, TimeCoef<T, Q> tc) {
+  const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (I >= Nxf || s >= Nf_steps) return;
+  const int m = s >> 1, sl = s & 1;
+  int64_t rest = I, jc = 0, stride = 1;
+  T w = T(1);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int src;
+    T wa;
+    if (!mode_source<T>((int)(rest % nf), nf, nc, ra, rb, src, wa)) return;   // unpaired mode: no correction
+    rest /= nf;
+    jc += stride * src;
+    stride *= nc;
+    w = (a == 0) ? wa : w * wa;
+  }
+  T e[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) e[k] = w * ec[((int64_t)m * Q + k) * Nxc + jc];
+  const T* Rb = sl ? tc.R2 : tc.R1;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    T* dst = uf + ((int64_t)s * Q + l) * Nxf + I;
+    T acc = *dst;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) acc += Rb[k * Q + l] * e[k];
+    *dst = acc;
+  }
+}
+
+}  // namespace stmg
