@@ -478,15 +478,17 @@ template <typename T, int D, int Q>
 void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0,
                         int ns) {
   Tables<T>& tb = tables<T>(lv);
+  constexpr int TS = stmg::kStepsPerThread;
+  const int nblk = (ns + TS - 1) / TS;
   dim3 grid(blocks_for(lv.Nx), 1);
-  for (int c = 0; c < ns; c += 65535) {
-    grid.y = std::min(65535, ns - c);
+  for (int c = 0; c < nblk; c += 65535) {
+    grid.y = std::min(65535, nblk - c);
     if (adj)
-      stmg::k_fresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c,
+      stmg::k_fresidual<T, Q, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c * TS, s0 + ns,
                                                                       tb.amat[1], tb.lamM);
     else
-      stmg::k_fresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c,
-                                                                       tb.amat[0], tb.lamM);
+      stmg::k_fresidual<T, Q, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c * TS,
+                                                                       s0 + ns, tb.amat[0], tb.lamM);
   }
 }
 
@@ -497,12 +499,14 @@ void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, const T* f, 
   const int a = adj ? 1 : 0;
   const T* ai = damp ? tb.ainvw[a] : tb.ainv[a];
   const T wc = (T)(1.0 - h->opt.omega);
+  constexpr int TS = stmg::kStepsPerThread;
+  const int nblk = (ns + TS - 1) / TS;
   dim3 grid(blocks_for(lv.Nx), 1);
-  for (int c = 0; c < ns; c += 65535) {
-    grid.y = std::min(65535, ns - c);
-#define STMG_FSMOOTH(ADJ, DAMP)                                                                              \
-  stmg::k_fsmooth<T, Q, ADJ, DAMP><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c, wc, ai, \
-                                                                     tb.lamM)
+  for (int c = 0; c < nblk; c += 65535) {
+    grid.y = std::min(65535, nblk - c);
+#define STMG_FSMOOTH(ADJ, DAMP)                                                                                  \
+  stmg::k_fsmooth<T, Q, ADJ, DAMP><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c * TS, s0 + ns, \
+                                                                     wc, ai, tb.lamM)
     if (adj) {
       if (damp) STMG_FSMOOTH(true, true); else STMG_FSMOOTH(true, false);
     } else {

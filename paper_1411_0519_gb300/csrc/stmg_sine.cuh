@@ -18,9 +18,9 @@
 // forward transform of the data and one inverse transform of the result per solve.
 //
 // Layout: index ((s * Q + l) * Nx + j): time step s, time dof l, spatial mode j
-// (first axis fastest, Nx = n^d modes).  One thread per (mode, step), consecutive
-// threads on consecutive modes, so every access is coalesced; the per-mode q x q
-// blocks are tabulated on the host as tab[e * Nx + j], e = k * Q + l.
+// (first axis fastest, Nx = n^d modes).  Consecutive threads take consecutive
+// modes, so every access is coalesced; the per-mode q x q blocks are tabulated
+// on the host as tab[e * Nx + j], e = k * Q + l.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -45,11 +45,6 @@ __device__ __forceinline__ T step_trace(const T* nb, int64_t Nx, int64_t o) {
   return v;
 }
 
-template <typename T, bool ADJ>
-__device__ __forceinline__ T couple(int k, T g, T mt) {
-  return (!ADJ && (k & 1)) ? g - mt : g + mt;
-}
-
 // Pointer type with or without __restrict__ (kernels whose buffers may alias
 // in one use and not in another).
 template <typename P, bool RESTRICT>
@@ -61,19 +56,32 @@ struct PtrSel<P, true> {
   typedef P* __restrict__ type;
 };
 
-// lamM_i times the coupling trace of step s (forward: u_{s-1}, or the
-// transformed initial value u0^ at s = 0; adjoint: u_{s+1}); 0 without one.
+// Steps per thread of the pointwise kernels: a thread walks TS consecutive
+// steps of one mode (forward in time for L, backward for L^T), loads the
+// mode's table entries once and keeps each step's iterate in registers as the
+// coupling trace of the next one.
+constexpr int kStepsPerThread = 4;
+
+// Coupling trace of the step before the first one a thread handles: forward,
+// step sb - 1 of u (or the transformed initial value u0^ at sb = 0); adjoint,
+// step se + 1 of u.  0 without one.
 template <typename T, int Q, bool ADJ>
-__device__ __forceinline__ T coupling(const T* u, const T* __restrict__ u0, const T* __restrict__ lamM, int64_t Nx,
-                                      int N, int s, int64_t j) {
-  const T* nb = nullptr;
-  if (u != nullptr) {
-    if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * Q * Nx;
-    if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * Q * Nx;
+__device__ __forceinline__ T entry_trace(const T* u, const T* __restrict__ u0, int64_t Nx, int N, int sb, int se,
+                                         int64_t j) {
+  if (!ADJ) {
+    if (sb > 0) return u != nullptr ? step_trace<T, Q, ADJ>(u + (int64_t)(sb - 1) * Q * Nx, Nx, j) : T(0);
+    return u0 != nullptr ? u0[j] : T(0);
   }
-  if (nb != nullptr) return lamM[j] * step_trace<T, Q, ADJ>(nb, Nx, j);
-  if (!ADJ && s == 0 && u0 != nullptr) return lamM[j] * u0[j];
-  return T(0);
+  return (u != nullptr && se + 1 < N) ? step_trace<T, Q, ADJ>(u + (int64_t)(se + 1) * Q * Nx, Nx, j) : T(0);
+}
+
+// Trace of a step from its values held in registers.
+template <typename T, int Q, bool ADJ>
+__device__ __forceinline__ T reg_trace(const T (&v)[Q]) {
+  T t = v[0];
+#pragma unroll
+  for (int l = 1; l < Q; ++l) t = (ADJ && (l & 1)) ? t - v[l] : t + v[l];
+  return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -81,28 +89,40 @@ __device__ __forceinline__ T coupling(const T* u, const T* __restrict__ u0, cons
 //   r_{s,k} = f_{s,k} - sum_l A_i[k,l] u_{s,l} + (-1)^k lamM_i sum_l u_{s-1,l}
 // (adjoint: A_i^T and + lamM_i sum_l (-1)^l u_{s+1,l}); at s = 0 of the forward
 // problem the trace is the transformed initial value u0^ (or 0).
-// amat[e * Nx + j] = A_i[k,l] (adjoint tables hold A_i^T).  One thread per
-// (mode, step in [s0, s0 + gridDim.y)).
+// amat[e * Nx + j] = A_i[k,l] (adjoint tables hold A_i^T).  Steps [s0, s1);
+// one thread per (mode, kStepsPerThread consecutive steps).
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ>
 __global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, const T* __restrict__ u,
                                                    const T* __restrict__ u0, T* __restrict__ r, int64_t Nx, int N,
-                                                   int s0, const T* __restrict__ amat, const T* __restrict__ lamM) {
+                                                   int s0, int s1, const T* __restrict__ amat,
+                                                   const T* __restrict__ lamM) {
+  constexpr int TS = kStepsPerThread;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = s0 + blockIdx.y;
-  if (j >= Nx || s >= N) return;
-  const T c = coupling<T, Q, ADJ>(u, u0, lamM, Nx, N, s, j);
-  const T* us = u + (int64_t)s * Q * Nx + j;
-  T uv[Q];
+  const int sb = s0 + blockIdx.y * TS;
+  if (j >= Nx || sb >= s1) return;
+  const int se = min(sb + TS, s1) - 1;
+  T A[Q * Q];
 #pragma unroll
-  for (int l = 0; l < Q; ++l) uv[l] = us[(int64_t)l * Nx];
+  for (int e = 0; e < Q * Q; ++e) A[e] = amat[(int64_t)e * Nx + j];
+  const T lam = lamM[j];
+  T t = entry_trace<T, Q, ADJ>(u, u0, Nx, N, sb, se, j);
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
-    T acc = couple<T, ADJ>(k, f[idx], c);
+  for (int i = 0; i < TS; ++i) {
+    const int s = ADJ ? se - i : sb + i;
+    if (ADJ ? s < sb : s > se) break;
+    T uv[Q];
 #pragma unroll
-    for (int l = 0; l < Q; ++l) acc -= amat[(int64_t)(k * Q + l) * Nx + j] * uv[l];
-    r[idx] = acc;
+    for (int l = 0; l < Q; ++l) uv[l] = u[((int64_t)s * Q + l) * Nx + j];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+      T acc = f[idx] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) acc -= A[k * Q + l] * uv[l];
+      r[idx] = acc;
+    }
+    t = reg_trace<T, Q, ADJ>(uv);
   }
 }
 
@@ -112,31 +132,46 @@ __global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, cons
 // the block inverse of the block row removes A u and only the rank-one time
 // coupling is applied.  DAMP: ainv holds w A_i^{-1} and out = that + wc u
 // (wc = 1 - w); without DAMP ainv holds A_i^{-1}, out = A_i^{-1}(f - B_i u_prev)
-// and u at step s is never read, so `out` may be `u` itself (forward
-// substitution of the coarsest solve, one step per launch).  u == nullptr is a
-// zero iterate.  With DAMP, u and out must differ (steps read their
-// neighbour's old value).  One thread per (mode, step in [s0, s0 + gridDim.y)).
+// and u at the steps being written is never read, so `out` may be `u` itself
+// for a single step (forward substitution of the coarsest solve, one step per
+// launch).  u == nullptr is a zero iterate.  With DAMP, u and out must differ
+// (steps read their neighbour's old value).  Steps [s0, s1); one thread per
+// (mode, kStepsPerThread consecutive steps).
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ, bool DAMP>
 __global__ void __launch_bounds__(256) k_fsmooth(const T* __restrict__ f, typename PtrSel<const T, DAMP>::type u,
                                                  const T* __restrict__ u0, typename PtrSel<T, DAMP>::type out,
-                                                 int64_t Nx, int N, int s0, T wc, const T* __restrict__ ainv,
+                                                 int64_t Nx, int N, int s0, int s1, T wc, const T* __restrict__ ainv,
                                                  const T* __restrict__ lamM) {
+  constexpr int TS = kStepsPerThread;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = s0 + blockIdx.y;
-  if (j >= Nx || s >= N) return;
-  const T c = coupling<T, Q, ADJ>(u, u0, lamM, Nx, N, s, j);
-  T g[Q];
+  const int sb = s0 + blockIdx.y * TS;
+  if (j >= Nx || sb >= s1) return;
+  const int se = min(sb + TS, s1) - 1;
+  T W[Q * Q];
 #pragma unroll
-  for (int k = 0; k < Q; ++k) g[k] = couple<T, ADJ>(k, f[((int64_t)s * Q + k) * Nx + j], c);
+  for (int e = 0; e < Q * Q; ++e) W[e] = ainv[(int64_t)e * Nx + j];
+  const T lam = lamM[j];
+  T t = entry_trace<T, Q, ADJ>(u, u0, Nx, N, sb, se, j);
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    T x = ainv[(int64_t)(k * Q) * Nx + j] * g[0];
+  for (int i = 0; i < TS; ++i) {
+    const int s = ADJ ? se - i : sb + i;
+    if (ADJ ? s < sb : s > se) break;
+    T g[Q], uv[Q];
 #pragma unroll
-    for (int l = 1; l < Q; ++l) x += ainv[(int64_t)(k * Q + l) * Nx + j] * g[l];
-    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
-    if (DAMP && u != nullptr) x += wc * u[idx];
-    out[idx] = x;
+    for (int k = 0; k < Q; ++k) {
+      g[k] = f[((int64_t)s * Q + k) * Nx + j] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+      uv[k] = (u != nullptr) ? u[((int64_t)s * Q + k) * Nx + j] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T x = W[k * Q] * g[0];
+#pragma unroll
+      for (int l = 1; l < Q; ++l) x += W[k * Q + l] * g[l];
+      if (DAMP && u != nullptr) x += wc * uv[k];
+      out[((int64_t)s * Q + k) * Nx + j] = x;
+    }
+    t = (u != nullptr) ? reg_trace<T, Q, ADJ>(uv) : T(0);
   }
 }
 
