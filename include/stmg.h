@@ -61,7 +61,8 @@ extern "C" {
 #define ST_SMOOTH_VCYCLE 1  /* D~^{-1}: one spatial multigrid V-cycle per step (Remark on the V-cycle
                                approximation in space; damped point-block Jacobi, nu_x, omega_x) */
 
-#define ST_MAX_PT    3   /* largest supported DG degree p_t (q <= 4) */
+#define ST_MAX_PT    47  /* largest supported DG degree p_t (q <= 48); degrees above 3 use the
+                             generic-q kernels and need ST_SMOOTH_EXACT */
 
 typedef struct st_mesh {
   int dim;  /* 1, 2 or 3 */

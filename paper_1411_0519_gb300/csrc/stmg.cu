@@ -21,6 +21,7 @@ using stmg::TimeCoef;
 namespace {
 
 constexpr int kQmax = ST_MAX_PT + 1;
+constexpr int kQfix = 4;   // q <= kQfix: compile-time q kernels; above: the generic-q kernels
 
 // ---------------------------------------------------------------------------
 // Host-side time data in the Legendre basis (Section 1 definitions evaluated
@@ -143,6 +144,7 @@ struct Tables {
   T* ainv[2] = {nullptr, nullptr};   // A_i^{-1}
   T* ainvw[2] = {nullptr, nullptr};  // w A_i^{-1} (damped smoother)
   T* lamM = nullptr;                 // lamM_i (coupling B_i = -lamM_i N_tau)
+  T* lamKt = nullptr;                // lamK_i tau (generic-q residual)
   T* ra = nullptr;     // full-coarsening pair weights to level L-1: (1 + c_k) / 2
   T* rb = nullptr;     //                                             -(1 - c_k) / 2
 };
@@ -197,7 +199,10 @@ struct st_handle {
   double* coarse64_f = nullptr;
   double* coarse64_r = nullptr;
   double* r64 = nullptr;         // mixed precision: finest FP64 residual
-  double* u0m = nullptr;         // transformed initial value (mixed basis)
+  double* u0m = nullptr;         // transformed initial value (sine basis)
+  // generic-q kernels: Mh (1/(2k+1)), R1, R2 and R1, R2 times 2^d (prolongation), q x q row-major
+  double* tt64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  float* tt32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::string err;
   // kernel timing
   bool prof = false;
@@ -293,7 +298,7 @@ void upload(st_handle* h, T* dst, const std::vector<double>& src) {
 // (K = K_tau, transposed for the adjoint) and its inverse (Gauss-Jordan with
 // partial pivoting), laid out tab[e * Nx + j].
 void mode_blocks(const HostTime& tm, int D, int n, double h, double tau, bool adj, std::vector<double>& amat,
-                 std::vector<double>& ainv, std::vector<double>& lamMv) {
+                 std::vector<double>& ainv, std::vector<double>& lamMv, std::vector<double>& lamKtv) {
   const int q = tm.q, qq = q * q;
   const int Nf = n + 1;
   int64_t Nx = 1;
@@ -307,6 +312,7 @@ void mode_blocks(const HostTime& tm, int D, int n, double h, double tau, bool ad
   amat.assign((size_t)qq * Nx, 0.0);
   ainv.assign((size_t)qq * Nx, 0.0);
   lamMv.assign((size_t)Nx, 0.0);
+  lamKtv.assign((size_t)Nx, 0.0);
   std::vector<double> A(qq), X(qq), M(qq);
   for (int64_t j = 0; j < Nx; ++j) {
     int idx[3] = {0, 0, 0};
@@ -324,6 +330,7 @@ void mode_blocks(const HostTime& tm, int D, int n, double h, double tau, bool ad
       lamM *= m1[idx[a]];
     }
     lamMv[j] = lamM;
+    lamKtv[j] = lamK * tau;
     for (int k = 0; k < q; ++k)
       for (int l = 0; l < q; ++l)
         A[k * q + l] = lamM * (adj ? tm.K[l * q + k] : tm.K[k * q + l]) + (k == l ? lamK * tau * tm.Mh[k] : 0.0);
@@ -377,19 +384,23 @@ void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
   upload(h, tb.twc, tc);
   upload(h, tb.tws, ts);
   for (int adj = 0; adj < 2; ++adj) {
-    std::vector<double> am, ai, lm;
-    mode_blocks(h->tm, h->d, n, lv.h, lv.tau, adj != 0, am, ai, lm);
+    std::vector<double> am, ai, lm, lk;
+    mode_blocks(h->tm, h->d, n, lv.h, lv.tau, adj != 0, am, ai, lm, lk);
     std::vector<double> aw(ai);
     for (double& x : aw) x *= h->opt.omega;
-    tb.amat[adj] = dalloc<T>(h, am.size());
+    if (h->q <= kQfix) {   // the generic-q residual uses the structure of K_tau instead
+      tb.amat[adj] = dalloc<T>(h, am.size());
+      upload(h, tb.amat[adj], am);
+    }
     tb.ainv[adj] = dalloc<T>(h, ai.size());
     tb.ainvw[adj] = dalloc<T>(h, aw.size());
-    upload(h, tb.amat[adj], am);
     upload(h, tb.ainv[adj], ai);
     upload(h, tb.ainvw[adj], aw);
     if (adj == 0) {
       tb.lamM = dalloc<T>(h, lm.size());
+      tb.lamKt = dalloc<T>(h, lk.size());
       upload(h, tb.lamM, lm);
+      upload(h, tb.lamKt, lk);
     }
   }
   if (lv.coarsen_full) {
@@ -516,6 +527,84 @@ void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, const T* f, 
   }
 }
 
+// ---- generic-q launchers (q > kQfix)
+template <typename T> T* const* ttabs(st_handle* h);
+template <> double* const* ttabs<double>(st_handle* h) { return h->tt64; }
+template <> float* const* ttabs<float>(st_handle* h) { return h->tt32; }
+
+template <typename T>
+void launch_mresidual_dyn(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0,
+                          int ns) {
+  Tables<T>& tb = tables<T>(lv);
+  constexpr int TS = stmg::kStepsPerThread;
+  const int nblk = (ns + TS - 1) / TS;
+  dim3 grid(blocks_for(lv.Nx), 1);
+  for (int c = 0; c < nblk; c += 65535) {
+    grid.y = std::min(65535, nblk - c);
+    if (adj)
+      stmg::k_fresidual_dyn<T, true><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c * TS,
+                                                                       s0 + ns, h->q, tb.lamM, tb.lamKt, ttabs<T>(h)[0]);
+    else
+      stmg::k_fresidual_dyn<T, false><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r, lv.Nx, lv.N, s0 + c * TS,
+                                                                        s0 + ns, h->q, tb.lamM, tb.lamKt, ttabs<T>(h)[0]);
+  }
+}
+
+template <typename T>
+void launch_msmooth_dyn(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out,
+                        int s0, int ns) {
+  Tables<T>& tb = tables<T>(lv);
+  const int a = adj ? 1 : 0;
+  const T* ai = damp ? tb.ainvw[a] : tb.ainv[a];
+  const T wc = (T)(1.0 - h->opt.omega);
+  constexpr int TS = stmg::kStepsPerThread;
+  const int nblk = (ns + TS - 1) / TS;
+  dim3 grid(blocks_for(lv.Nx), 1);
+  for (int c = 0; c < nblk; c += 65535) {
+    grid.y = std::min(65535, nblk - c);
+#define STMG_FSMOOTH_DYN(ADJ, DAMP)                                                                        \
+  stmg::k_fsmooth_dyn<T, ADJ, DAMP><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c * TS, \
+                                                                      s0 + ns, h->q, wc, ai, tb.lamM)
+    if (adj) {
+      if (damp) STMG_FSMOOTH_DYN(true, true); else STMG_FSMOOTH_DYN(true, false);
+    } else {
+      if (damp) STMG_FSMOOTH_DYN(false, true); else STMG_FSMOOTH_DYN(false, false);
+    }
+#undef STMG_FSMOOTH_DYN
+  }
+}
+
+template <typename T, int D>
+void launch_restrict_dyn_t(st_handle* h, Level& fine, const Level& coarse, const T* r, T* fc) {
+  const size_t smem = 2 * sizeof(T) * h->q * h->q;
+  T* const* tt = ttabs<T>(h);
+  dim3 grid(blocks_for(coarse.Nx), coarse.N);
+  if (fine.coarsen_full)
+    stmg::k_frestrict_dyn<T, D, true><<<grid, kThreads, smem, h->stream>>>(
+        r, fc, fine.n, coarse.n, coarse.N, h->q, tables<T>(fine).ra, tables<T>(fine).rb, tt[1], tt[2]);
+  else
+    stmg::k_frestrict_dyn<T, D, false><<<grid, kThreads, smem, h->stream>>>(
+        r, fc, fine.n, coarse.n, coarse.N, h->q, (const T*)nullptr, (const T*)nullptr, tt[1], tt[2]);
+}
+
+template <typename T, int D>
+void launch_prolong_dyn_t(st_handle* h, Level& fine, const Level& coarse, const T* ec, T* uf) {
+  const size_t smem = 2 * sizeof(T) * h->q * h->q;
+  T* const* tt = ttabs<T>(h);
+  dim3 grid(blocks_for(fine.Nx), fine.N);
+  if (fine.coarsen_full)   // time blocks pre-multiplied by 2^d (tt[3], tt[4])
+    stmg::k_fprolong_dyn<T, D, true><<<grid, kThreads, smem, h->stream>>>(
+        ec, uf, fine.n, coarse.n, fine.N, h->q, tables<T>(fine).ra, tables<T>(fine).rb, tt[3], tt[4]);
+  else
+    stmg::k_fprolong_dyn<T, D, false><<<grid, kThreads, smem, h->stream>>>(
+        ec, uf, fine.n, coarse.n, fine.N, h->q, (const T*)nullptr, (const T*)nullptr, tt[1], tt[2]);
+}
+
+template <typename T, int D>
+void launch_ic_grad_dyn_t(st_handle* h, const Level& lv, const T* lam, T* g) {
+  stmg::k_ic_gradient_dyn<T, D><<<blocks_for(lv.Nx), kThreads, 0, h->stream>>>(lam, g, lv.n, (T)lv.h, h->q);
+}
+
 // Restriction / prolongation between levels L and L-1.  modal: vectors in the
 // mixed basis (full coarsening pairs sine modes); otherwise on nodes.  Semi
 // coarsening is the identity in space and the same kernel serves both.
@@ -609,6 +698,16 @@ void launch_space_transfer_t(st_handle* h, const Level& lv, int nf, int nc, bool
     }                                                                            \
   } while (0)
 
+#define STMG_DISPATCH_D(FN, ...)                                                 \
+  do {                                                                           \
+    switch (h->d) {                                                              \
+      case 1: FN<T, 1>(__VA_ARGS__); break;                                      \
+      case 2: FN<T, 2>(__VA_ARGS__); break;                                      \
+      case 3: FN<T, 3>(__VA_ARGS__); break;                                      \
+      default: fail(h, ST_EINVAL, "unsupported dim");                            \
+    }                                                                            \
+  } while (0)
+
 template <typename T>
 void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0 = 0,
               int ns = -1) {
@@ -633,7 +732,8 @@ void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const 
   // bytes: read u, f, write r (+ u0)
   Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)),
           nodes * (2.0 * Q * Q + 2.0 * Q), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
+  if (h->q > kQfix) launch_mresidual_dyn<T>(h, lv, adj, f, u, u0, r, s0, ns);
+  else STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
 // Fused damped block-Jacobi step with the exact block inverse in the mixed
@@ -647,7 +747,8 @@ void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* 
   const double passes = 2.0 + ((damp && u) ? 1.0 : 0.0);   // read f (and u), write out
   // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i^{-1} g Q^2 FMA, damping Q FMA
   Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * (2.0 * Q * Q + 4.0 * Q), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, f, u, u0, out, s0, ns);
+  if (h->q > kQfix) launch_msmooth_dyn<T>(h, lv, adj, damp, f, u, u0, out, s0, ns);
+  else STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, f, u, u0, out, s0, ns);
 }
 
 template <typename T>
@@ -657,7 +758,8 @@ void restrict_to(st_handle* h, int L, bool modal, const T* r, T* fc) {
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   const double ns = fine.coarsen_full ? std::pow(modal ? 2.0 : 3.0, h->d) : 1.0;
   Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * h->q), 1, L);
-  STMG_DISPATCH(launch_restrict_t, h, fine, coarse, modal, r, fc);
+  if (h->q > kQfix) STMG_DISPATCH_D(launch_restrict_dyn_t, h, fine, coarse, r, fc);
+  else STMG_DISPATCH(launch_restrict_t, h, fine, coarse, modal, r, fc);
 }
 
 template <typename T>
@@ -667,7 +769,8 @@ void prolong_add(st_handle* h, int L, bool modal, const T* ec, T* uf) {
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   const double ns = fine.coarsen_full ? (modal ? 1.0 : std::pow(2.0, h->d)) : 1.0;
   Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + h->q), 1, L);
-  STMG_DISPATCH(launch_prolong_t, h, fine, coarse, modal, ec, uf);
+  if (h->q > kQfix) STMG_DISPATCH_D(launch_prolong_dyn_t, h, fine, coarse, ec, uf);
+  else STMG_DISPATCH(launch_prolong_t, h, fine, coarse, modal, ec, uf);
 }
 
 template <typename T>
@@ -1277,6 +1380,8 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
     if (h->opt.smoother != ST_SMOOTH_EXACT && h->opt.smoother != ST_SMOOTH_VCYCLE) fail(h, ST_EINVAL, "bad smoother");
     if (h->opt.smoother == ST_SMOOTH_VCYCLE && (h->opt.nu_x < 1 || !(h->opt.omega_x > 0.0)))
       fail(h, ST_EINVAL, "bad spatial smoothing options");
+    if (h->opt.smoother == ST_SMOOTH_VCYCLE && p_t + 1 > kQfix)
+      fail(h, ST_EINVAL, "the inexact block inverse supports p_t <= 3");
     if (h->opt.gamma < 1 || h->opt.gamma > 2) fail(h, ST_EINVAL, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
     if (h->opt.coarsest_steps < 1) h->opt.coarsest_steps = 1;
     if (!is_pow2(h->opt.coarsest_steps) || h->opt.coarsest_steps > N) fail(h, ST_EINVAL, "bad coarsest_steps");
@@ -1343,6 +1448,27 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       h->r64 = finest(h).v64.r;
     }
     h->u0m = dalloc<double>(h, finest(h).Nx);
+    {   // time tables of the generic-q kernels
+      const int q = h->q;
+      std::vector<double> mh(q), r1(q * q), r2(q * q), p1(q * q), p2(q * q);
+      const double sc = (double)(1 << h->d);
+      for (int k = 0; k < q; ++k) mh[k] = h->tm.Mh[k];
+      for (int e = 0; e < q * q; ++e) {
+        r1[e] = h->tm.R1[e];
+        r2[e] = h->tm.R2[e];
+        p1[e] = sc * r1[e];
+        p2[e] = sc * r2[e];
+      }
+      const std::vector<double>* src[5] = {&mh, &r1, &r2, &p1, &p2};
+      for (int i = 0; i < 5; ++i) {
+        h->tt64[i] = dalloc<double>(h, src[i]->size());
+        upload(h, h->tt64[i], *src[i]);
+        if (mixed) {
+          h->tt32[i] = dalloc<float>(h, src[i]->size());
+          upload(h, h->tt32[i], *src[i]);
+        }
+      }
+    }
     dst_set_smem_limits<double>(h);
     if (mixed) dst_set_smem_limits<float>(h);
     h->partial = dalloc<double>(h, kNormBlocks);
@@ -1391,7 +1517,18 @@ int st_level_info(const st_handle* h, int L, int* N_L, int* n_L, double* mu_L, i
 int st_residual(st_handle* h, const double* f, const double* u0_ic, const double* u, double* r) {
   return guarded(h, [&]() -> int {
     if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
-    residual<double>(h, finest(h), false, f, u, u0_ic, r);
+    Level& lv = finest(h);
+    if (h->q > kQfix) {   // no node-basis kernels for large q: through the sine basis
+      const int64_t slabs = (int64_t)lv.N * h->q;
+      copy<double>(h, lv.v64.r, u, lv.ndof);
+      to_modal<double>(h, lv, lv.v64.r, slabs);
+      const CycleInputs in = enter_cycle_basis(h, f, u0_ic, lv.v64.r, false);
+      mresidual<double>(h, lv, false, in.f, lv.v64.r, in.u0, r);
+      from_modal<double>(h, lv, r, slabs);
+      after_launch(h);
+      return ST_OK;
+    }
+    residual<double>(h, lv, false, f, u, u0_ic, r);
     after_launch(h);
     return ST_OK;
   });
@@ -1432,7 +1569,8 @@ int st_adjoint_solve(st_handle* h, const double* g, double* lambda, double* grad
     int rc = solve_impl(h, true, g, nullptr, lambda, 0, iters, relres);
     if (grad_u0) {
       using T = double;
-      STMG_DISPATCH(launch_ic_grad_t, h, finest(h), lambda, grad_u0);
+      if (h->q > kQfix) STMG_DISPATCH_D(launch_ic_grad_dyn_t, h, finest(h), lambda, grad_u0);
+      else STMG_DISPATCH(launch_ic_grad_t, h, finest(h), lambda, grad_u0);
     }
     after_launch(h);
     return rc;

@@ -928,6 +928,22 @@ __global__ void k_ic_gradient(const T* __restrict__ lam, T* __restrict__ g, int 
   });
 }
 
+// The same for a runtime number q of time dofs (psi_k(t_0^+) = (-1)^k).
+template <typename T, int D>
+__global__ void k_ic_gradient_dyn(const T* __restrict__ lam, T* __restrict__ g, int n, T h, int q) {
+  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Nx) return;
+  int ix, iy, iz;
+  node_coords(j, n, D, ix, iy, iz);
+  Stencil<T, D> S(h, T(0));   // M_h only
+  g[j] = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t nd) {
+    T t = T(0);
+    for (int k = 0; k < q; ++k) t = (k & 1) ? t - lam[(int64_t)k * Nx + nd] : t + lam[(int64_t)k * Nx + nd];
+    return t;
+  });
+}
+
 // ---------------------------------------------------------------------------
 // Inexact block inverse (Remark on the V-cycle approximation in space): one
 // spatial multigrid V-cycle per time step for A = K_tau (x) M_h + M_tau (x) K_h,

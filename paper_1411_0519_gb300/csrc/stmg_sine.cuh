@@ -304,4 +304,229 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
   }
 }
 
+// ===========================================================================
+// Generic time degree (q > 4, up to kQmaxDyn): the same operators with q a
+// runtime value.  The residual uses the structure of the Legendre K_tau,
+//   K[k,l] = 1 - 2 [l < k and k - l odd],
+// so (K u)_k = S - 2 sum_{l < k, k - l odd} u_l (S = sum_l u_l) and
+// (K^T u)_k = S - 2 sum_{l > k, l - k odd} u_l: running sums by parity, O(q)
+// per (mode, step) and no table; A_i u = lamM_i (K u) + (lamK_i tau) Mh o u.
+// The smoother applies the tabulated w A_i^{-1} (q^2 per mode).  Transfers read
+// the time blocks from shared memory.
+// ===========================================================================
+constexpr int kQmaxDyn = 48;
+
+// Both traces of step s of a mode: sum_l u_l (forward coupling) and
+// sum_l (-1)^l u_l (transposed coupling).
+template <typename T>
+__device__ __forceinline__ void traces_dyn(const T* us, int64_t Nx, int q, T& plain, T& alt) {
+  plain = T(0);
+  alt = T(0);
+  for (int l = 0; l < q; ++l) {
+    const T x = us[(int64_t)l * Nx];
+    plain += x;
+    alt = (l & 1) ? alt - x : alt + x;
+  }
+}
+
+template <typename T, bool ADJ>
+__device__ __forceinline__ T entry_trace_dyn(const T* u, const T* __restrict__ u0, int64_t Nx, int N, int q, int sb,
+                                             int se, int64_t j) {
+  T plain, alt;
+  if (!ADJ) {
+    if (sb > 0) {
+      if (u == nullptr) return T(0);
+      traces_dyn<T>(u + (int64_t)(sb - 1) * q * Nx + j, Nx, q, plain, alt);
+      return plain;
+    }
+    return u0 != nullptr ? u0[j] : T(0);
+  }
+  if (u == nullptr || se + 1 >= N) return T(0);
+  traces_dyn<T>(u + (int64_t)(se + 1) * q * Nx + j, Nx, q, plain, alt);
+  return alt;
+}
+
+// mh[k] = M_tau[k][k] / tau = 1 / (2k + 1); lamKt[j] = lamK_j tau.
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(256) k_fresidual_dyn(const T* __restrict__ f, const T* __restrict__ u,
+                                                       const T* __restrict__ u0, T* __restrict__ r, int64_t Nx,
+                                                       int N, int s0, int s1, int q, const T* __restrict__ lamM,
+                                                       const T* __restrict__ lamKt, const T* __restrict__ mh) {
+  __shared__ T smh[kQmaxDyn];
+  if (threadIdx.x < q) smh[threadIdx.x] = mh[threadIdx.x];
+  __syncthreads();
+  constexpr int TS = kStepsPerThread;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sb = s0 + blockIdx.y * TS;
+  if (j >= Nx || sb >= s1) return;
+  const int se = min(sb + TS, s1) - 1;
+  const T lam = lamM[j], kt = lamKt[j];
+  T t = entry_trace_dyn<T, ADJ>(u, u0, Nx, N, q, sb, se, j);
+  for (int i = 0; i < TS; ++i) {
+    const int s = ADJ ? se - i : sb + i;
+    if (ADJ ? s < sb : s > se) break;
+    const T* us = u + (int64_t)s * q * Nx + j;
+    T S, alt;
+    traces_dyn<T>(us, Nx, q, S, alt);
+    T even = T(0), odd = T(0);   // running sums over the l already passed, by parity of l
+    for (int c = 0; c < q; ++c) {
+      const int k = ADJ ? q - 1 - c : c;
+      const T uk = us[(int64_t)k * Nx];
+      const T Ku = S - T(2) * ((k & 1) ? even : odd);
+      const int64_t idx = ((int64_t)s * q + k) * Nx + j;
+      r[idx] = f[idx] + ((!ADJ && (k & 1)) ? -lam : lam) * t - lam * Ku - kt * smh[k] * uk;
+      if (k & 1) odd += uk; else even += uk;
+    }
+    t = ADJ ? alt : S;
+  }
+}
+
+template <typename T, bool ADJ, bool DAMP>
+__global__ void __launch_bounds__(256) k_fsmooth_dyn(const T* __restrict__ f, typename PtrSel<const T, DAMP>::type u,
+                                                     const T* __restrict__ u0, typename PtrSel<T, DAMP>::type out,
+                                                     int64_t Nx, int N, int s0, int s1, int q, T wc,
+                                                     const T* __restrict__ ainv, const T* __restrict__ lamM) {
+  constexpr int TS = kStepsPerThread;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sb = s0 + blockIdx.y * TS;
+  if (j >= Nx || sb >= s1) return;
+  const int se = min(sb + TS, s1) - 1;
+  const T lam = lamM[j];
+  T t = entry_trace_dyn<T, ADJ>(u, u0, Nx, N, q, sb, se, j);
+  T g[kQmaxDyn];
+  for (int i = 0; i < TS; ++i) {
+    const int s = ADJ ? se - i : sb + i;
+    if (ADJ ? s < sb : s > se) break;
+    for (int k = 0; k < q; ++k) g[k] = f[((int64_t)s * q + k) * Nx + j] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+    T plain = T(0), alt = T(0);
+    for (int k = 0; k < q; ++k) {
+      const T* wk = ainv + (int64_t)(k * q) * Nx + j;
+      T x = T(0);
+      for (int l = 0; l < q; ++l) x += wk[(int64_t)l * Nx] * g[l];
+      const int64_t idx = ((int64_t)s * q + k) * Nx + j;
+      if (u != nullptr) {
+        const T uk = u[idx];
+        plain += uk;
+        alt = (k & 1) ? alt - uk : alt + uk;
+        if (DAMP) x += wc * uk;
+      }
+      out[idx] = x;
+    }
+    t = (u != nullptr) ? (ADJ ? alt : plain) : T(0);
+  }
+}
+
+// Restriction (FULL: mode pairs along every axis; otherwise identity in space)
+// and time blocks R1, R2 (q x q, row = coarse) staged in shared memory.
+template <typename T, int D, bool FULL>
+__global__ void k_frestrict_dyn(const T* __restrict__ r, T* __restrict__ fc, int nf, int nc, int Nc, int q,
+                                const T* __restrict__ ra, const T* __restrict__ rb, const T* __restrict__ R1,
+                                const T* __restrict__ R2) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sR1 = reinterpret_cast<T*>(smem_raw);
+  T* sR2 = sR1 + q * q;
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    sR1[e] = R1[e];
+    sR2[e] = R2[e];
+  }
+  __syncthreads();
+  const int64_t Nxc = pow_d<D>(nc), Nxf = FULL ? pow_d<D>(nf) : Nxc;
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (J >= Nxc || m >= Nc) return;
+  constexpr int NT = FULL ? (1 << D) : 1;
+  int64_t src[NT];
+  T wm[NT];
+  if (!FULL) {
+    src[0] = J;
+    wm[0] = T(1);
+  } else {
+    int c[3] = {0, 0, 0};
+    int64_t rest = J;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      c[a] = (int)(rest % nc);
+      rest /= nc;
+    }
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) {
+      int64_t idx = 0, stride = 1;
+      T w = T(1);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const bool hi = (tt >> a) & 1;
+        idx += stride * (hi ? nf - 1 - c[a] : c[a]);
+        w = (a == 0) ? (hi ? rb[c[a]] : ra[c[a]]) : w * (hi ? rb[c[a]] : ra[c[a]]);
+        stride *= nf;
+      }
+      src[tt] = idx;
+      wm[tt] = w;
+    }
+  }
+  T a0[kQmaxDyn], a1[kQmaxDyn];
+  for (int l = 0; l < q; ++l) {
+    const T* r0 = r + ((int64_t)(2 * m) * q + l) * Nxf;
+    const T* r1 = r + ((int64_t)(2 * m + 1) * q + l) * Nxf;
+    T x0 = T(0), x1 = T(0);
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) {
+      x0 += wm[tt] * r0[src[tt]];
+      x1 += wm[tt] * r1[src[tt]];
+    }
+    a0[l] = x0;
+    a1[l] = x1;
+  }
+  for (int k = 0; k < q; ++k) {
+    T acc = T(0);
+    for (int l = 0; l <= k; ++l) acc += sR1[k * q + l] * a0[l] + sR2[k * q + l] * a1[l];   // R lower triangular
+    fc[((int64_t)m * q + k) * Nxc + J] = acc;
+  }
+}
+
+// Prolongation and correction; the host passes R1, R2 pre-multiplied by 2^d
+// for full coarsening (the pair weights are then ra, rb themselves).
+template <typename T, int D, bool FULL>
+__global__ void k_fprolong_dyn(const T* __restrict__ ec, T* __restrict__ uf, int nf, int nc, int Nf_steps, int q,
+                               const T* __restrict__ ra, const T* __restrict__ rb, const T* __restrict__ R1,
+                               const T* __restrict__ R2) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sR1 = reinterpret_cast<T*>(smem_raw);
+  T* sR2 = sR1 + q * q;
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    sR1[e] = R1[e];
+    sR2[e] = R2[e];
+  }
+  __syncthreads();
+  const int64_t Nxc = pow_d<D>(nc), Nxf = FULL ? pow_d<D>(nf) : Nxc;
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (I >= Nxf || s >= Nf_steps) return;
+  const int m = s >> 1, sl = s & 1;
+  int64_t jc = I;
+  T w = T(1);
+  if (FULL) {
+    int64_t rest = I, stride = 1;
+    jc = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int src;
+      T wa;
+      if (!mode_source<T>((int)(rest % nf), nf, nc, ra, rb, src, wa)) return;   // unpaired mode
+      rest /= nf;
+      jc += stride * src;
+      stride *= nc;
+      w = (a == 0) ? wa : w * wa;
+    }
+  }
+  T e[kQmaxDyn];
+  for (int k = 0; k < q; ++k) e[k] = w * ec[((int64_t)m * q + k) * Nxc + jc];
+  const T* Rb = sl ? sR2 : sR1;
+  for (int l = 0; l < q; ++l) {
+    T* dst = uf + ((int64_t)s * q + l) * Nxf + I;
+    T acc = *dst;
+    for (int k = l; k < q; ++k) acc += Rb[k * q + l] * e[k];   // R lower triangular: k >= l
+    *dst = acc;
+  }
+}
+
 }  // namespace stmg

@@ -20,7 +20,7 @@ ST_OK, ST_EINVAL, ST_ENOMEM, ST_ENOTCONV, ST_ENAN, ST_ECUDA = range(6)
 ST_FP64, ST_MIXED = 0, 1
 ST_AUTO, ST_SEMI, ST_FULL = 0, 1, 2
 ST_INIT_GIVEN = 1
-ST_MAX_PT = 3
+ST_MAX_PT = 47
 ST_SMOOTH_EXACT, ST_SMOOTH_VCYCLE = 0, 1
 
 EXPORTS = [
