@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-inexact", action="store_true",
                     help="skip the solve with the inexact block inverse (one spatial V-cycle per step)")
+    ap.add_argument("--no-high-order", action="store_true",
+                    help="skip the Example 2 solve at p_t = 45 (generic-q kernels)")
     ap.add_argument("--inner-cycles", type=int, default=4)
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
                     help="run one precision only (profiling); the line's value is that precision's")
@@ -390,6 +392,43 @@ def main():
             torch.cuda.empty_cache()
         inexact["smoother"] = "one spatial V-cycle per time step, damped point-block Jacobi nu_x=2, omega_x=2/3"
 
+    # ---------------------------------------------------------------- high time degree (Example 2)
+    high = None
+    if not args.no_high_order:
+        wh = workloads.WORKLOADS["example2_p45"]
+        sh = stmg.Solver(wh["d"], wh["n"], wh["p_t"], wh["N"], wh["T"], rtol=wh["rtol"], maxit=40)
+        it0 = torch.from_numpy(workloads.uniform_iterate(wh["d"], wh["n"], wh["p_t"], wh["N"], seed=rank)).cuda()
+        it0 = it0.view(sh.shape)
+        fz = torch.zeros_like(it0)
+        uh = sh.empty()
+        nst = min(args.steps, 2)
+        for _ in range(max(1, args.warmup // 3)):
+            uh.copy_(it0)
+            sh.solve(fz, u=uh, initial_guess=True)
+        barrier()
+        torch.cuda.synchronize()
+        sh.profile_start(400000)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(sh.stream)
+        ith = []
+        for _ in range(nst):
+            with torch.cuda.stream(sh.stream):
+                uh.copy_(it0)
+            _, itx, rrh = sh.solve(fz, u=uh, initial_guess=True)
+            ith.append(itx)
+        ev1.record(sh.stream)
+        ev1.synchronize()
+        profh = sh.profile_stop()
+        msh = max_over_ranks(ev0.elapsed_time(ev1))
+        high = {"workload": "example2_p45: 2D 127^2 Q1, p_t = 45 (q = 46), N = 64, tau = 1, f = 0, "
+                            "iterate ~ U[0, 1] (Example 2 protocol)",
+                "value": world * sh.ndof / (msh / nst / 1e3), "unit": "DoF/s", "ms_per_step": msh / nst,
+                "iters": ith[-1], "relres": rrh, "dof": sh.ndof, "roofline": roofline(sh, profh, False, pk, wh),
+                "kernels": breakdown(profh)}
+        sh.close()
+        del it0, fz, uh
+        torch.cuda.empty_cache()
+
     if rank != 0:
         pd.finalize()
         return 0
@@ -413,6 +452,7 @@ def main():
         "kernels": breakdown(prof64),
         "mixed": mixed,
         "inexact_smoother": inexact,
+        "high_order": high,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,

@@ -728,10 +728,10 @@ void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const 
                int ns = -1) {
   if (ns < 0) ns = lv.N;
   const double Q = h->q, nodes = (double)ns * lv.Nx;
-  // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i u Q^2 FMA;
-  // bytes: read u, f, write r (+ u0)
+  // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i u Q^2 FMA (q > kQfix: the
+  // structured K_tau product, 12 flops per time dof); bytes: read u, f, write r (+ u0)
   Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)),
-          nodes * (2.0 * Q * Q + 2.0 * Q), 1, level_of(h, lv));
+          nodes * (h->q > kQfix ? 12.0 * Q : 2.0 * Q * Q + 2.0 * Q), 1, level_of(h, lv));
   if (h->q > kQfix) launch_mresidual_dyn<T>(h, lv, adj, f, u, u0, r, s0, ns);
   else STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }

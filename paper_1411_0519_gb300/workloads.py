@@ -18,6 +18,8 @@ Workloads (unit square / cube, homogeneous Dirichlet, p_t = DG degree):
   heat2d_511     2D, 511^2 nodes, p_t=1, N=2048, T = mu/128 for
                  mu in {1/16, 1/4, 1, 16}; f ~ U[-1,1] seed 0
   heat2d_255_n256  heat2d_255 cut to its first 256 time steps (profiling)
+  example2_p45     Example 2 protocol at the highest degree of its table: 127^2 Q1,
+                   p_t = 45, tau = 1 (N = 64, T = 64), f = 0, iterate ~ U[0, 1]
 """
 import numpy as np
 
@@ -30,6 +32,7 @@ WORKLOADS = {
     # profiling case: the 255^2 mesh and tau of heat2d_255 on 256 time steps
     # (33M unknowns, 266 MB per vector: above L2, a few GB on the device)
     "heat2d_255_n256": dict(d=2, n=255, p_t=1, N=256, T=0.25, rtol=1e-8),
+    "example2_p45": dict(d=2, n=127, p_t=45, N=64, T=64.0, rtol=1e-8),
 }
 
 
