@@ -757,7 +757,10 @@ void restrict_to(st_handle* h, int L, bool modal, const T* r, T* fc) {
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   const double ns = fine.coarsen_full ? std::pow(modal ? 2.0 : 3.0, h->d) : 1.0;
-  Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * h->q), 1, L);
+  // time blocks: q FMA per coarse dof and block, half of them for q > kQfix (R is lower triangular
+  // and the generic-q kernels skip its zeros)
+  const double tq = h->q > kQfix ? 0.5 * (h->q + 1) : h->q;
+  Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_restrict_dyn_t, h, fine, coarse, r, fc);
   else STMG_DISPATCH(launch_restrict_t, h, fine, coarse, modal, r, fc);
 }
@@ -768,7 +771,8 @@ void prolong_add(st_handle* h, int L, bool modal, const T* ec, T* uf) {
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   const double ns = fine.coarsen_full ? (modal ? 1.0 : std::pow(2.0, h->d)) : 1.0;
-  Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + h->q), 1, L);
+  const double tq = h->q > kQfix ? 0.5 * (h->q + 1) : h->q;
+  Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_prolong_dyn_t, h, fine, coarse, ec, uf);
   else STMG_DISPATCH(launch_prolong_t, h, fine, coarse, modal, ec, uf);
 }
