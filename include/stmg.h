@@ -66,7 +66,8 @@ extern "C" {
 
 typedef struct st_mesh {
   int dim;  /* 1, 2 or 3 */
-  int n;    /* interior nodes per axis, 2^k - 1, k >= 1 */
+  int n;    /* interior nodes per axis, 2^k - 1, k >= 1; n <= 1023 with the exact block
+               inverse (the sine transform of a line is held in shared memory) */
 } st_mesh;
 
 typedef struct st_options {

@@ -214,3 +214,27 @@ def test_heat2d_511_mu_sweep_mixed_forward_and_adjoint(mu):
     assert eu < 1e-5 and el < 1e-5
     del u64, lam64, umx, lammx
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("d,n,p,N", [(2, 1023, 1, 4), (3, 127, 1, 2), (1, 1023, 3, 8)])
+def test_largest_lines_converge_checked_by_the_node_residual(d, n, p, N):
+    """Line lengths at the top of the supported range (the sine transforms of
+    1024-point lines run in the shared-memory kernels, 128-point 3D lines in the
+    register kernels): the solve in the sine basis reaches 1e-10, and the
+    residual recomputed by the node-basis stencil kernel (independent of the
+    sine path) confirms it."""
+    require_gpu()
+    from paper_1411_0519_gb300 import stmg
+    T = 1.0
+    f = to_gpu(workloads.uniform_load(d, n, p, N, seed=3))
+    u0 = to_gpu(workloads.sine_ic(d, n))
+    s = stmg.Solver(d, n, p, N, T, rtol=1e-10, maxit=60)
+    u, it, rr = s.solve(f, u0)
+    assert rr <= 1e-10 and it <= 15
+    r = s.residual(f, u, u0)
+    r0 = s.residual(f, torch.zeros_like(u), u0)
+    ratio = (r.norm() / r0.norm()).item()
+    print(f"d={d} n={n} p_t={p} N={N}: {it} V-cycles, node-basis relative residual {ratio:.2e}")
+    assert ratio <= 2e-10
+    s.close()
+    torch.cuda.empty_cache()
