@@ -177,6 +177,7 @@ struct Level {
   Vecs<float> v32;
   Tables<double> t64;
   Tables<float> t32;
+  stmg::DstTables<stmg::dfloat> tdf{nullptr, nullptr, nullptr};   // finest level, mixed form: double-float transforms
   std::vector<SpaceLvl<double>> sp64;   // spatial hierarchy of the inexact block inverse
   std::vector<SpaceLvl<float>> sp32;
 };
@@ -946,6 +947,96 @@ void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale
   }
 }
 
+// ---- double-float sine transforms (mixed form): the register kernels with
+// dfloat arithmetic on FP64 storage; other line lengths use the FP64 kernels.
+bool df_len(int Nf) { return Nf >= 64 && Nf <= 512; }
+
+void make_df_tables(st_handle* h, Level& lv) {
+  const int Nf = lv.n + 1;
+  std::vector<stmg::dfloat> sp(Nf), tc(Nf), ts(Nf);
+  for (int j = 0; j < Nf; ++j) {
+    sp[j] = stmg::dfloat(std::sin(j * M_PI / Nf));
+    tc[j] = stmg::dfloat(std::cos(2.0 * M_PI * j / Nf));
+    ts[j] = stmg::dfloat(std::sin(2.0 * M_PI * j / Nf));
+  }
+  stmg::dfloat* d[3];
+  const std::vector<stmg::dfloat>* src[3] = {&sp, &tc, &ts};
+  for (int i = 0; i < 3; ++i) {
+    d[i] = reinterpret_cast<stmg::dfloat*>(dalloc<double>(h, Nf));   // 8-byte elements
+    check(h, cudaMemcpy(d[i], src[i]->data(), Nf * sizeof(stmg::dfloat), cudaMemcpyHostToDevice), "upload table");
+  }
+  lv.tdf = stmg::DstTables<stmg::dfloat>{d[0], d[1], d[2]};
+}
+
+template <int LP, int LG, typename SIN, typename SOUT>
+void df_set_smem_io(st_handle* h) {
+  using DF = stmg::dfloat;
+  check(h, cudaFuncSetAttribute((const void*)stmg::k_dst_rows_reg<DF, LP, LG, SIN, SOUT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dst_reg_smem<DF, LP, LG>()),
+        "cudaFuncSetAttribute");
+  check(h, cudaFuncSetAttribute((const void*)stmg::k_dst_cols_reg<DF, LP, LG, SIN, SOUT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dst_cols_reg_smem<DF, LP, LG>()),
+        "cudaFuncSetAttribute");
+}
+template <int LP, int LG>
+void df_set_smem(st_handle* h) {
+  using DF = stmg::dfloat;
+  df_set_smem_io<LP, LG, double, double>(h);
+  df_set_smem_io<LP, LG, double, DF>(h);
+  df_set_smem_io<LP, LG, DF, DF>(h);
+  df_set_smem_io<LP, LG, DF, double>(h);
+}
+
+template <int LP, int LG, typename SIN, typename SOUT>
+void df_launch_io(st_handle* h, double* data, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
+                  stmg::DstTables<stmg::dfloat> dt, bool rows) {
+  using DF = stmg::dfloat;
+  constexpr int G = 1 << LG;
+  const int thr = dst_reg_threads<DF>();
+  const unsigned grid = (unsigned)((nlines + thr / G - 1) / (thr / G));
+  if (rows)
+    stmg::k_dst_rows_reg<DF, LP, LG, SIN, SOUT><<<grid, thr, dst_reg_smem<DF, LP, LG>(), h->stream>>>(
+        data, n, nlines, scale, dt);
+  else
+    stmg::k_dst_cols_reg<DF, LP, LG, SIN, SOUT><<<grid, thr, dst_cols_reg_smem<DF, LP, LG>(), h->stream>>>(
+        data, n, nlines, inner, scale, dt);
+}
+
+// first / last axis pass: FP64 in / out; between passes the 8-byte slots hold float pairs
+template <int LP, int LG>
+void df_launch(st_handle* h, double* data, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
+               stmg::DstTables<stmg::dfloat> dt, bool rows, bool first, bool last) {
+  using DF = stmg::dfloat;
+  if (first && last) df_launch_io<LP, LG, double, double>(h, data, n, nlines, inner, scale, dt, rows);
+  else if (first) df_launch_io<LP, LG, double, DF>(h, data, n, nlines, inner, scale, dt, rows);
+  else if (last) df_launch_io<LP, LG, DF, double>(h, data, n, nlines, inner, scale, dt, rows);
+  else df_launch_io<LP, LG, DF, DF>(h, data, n, nlines, inner, scale, dt, rows);
+}
+
+// scale * DST-I along every axis of `slabs` FP64 fields, computed in double-float.
+void dst_axes_df(st_handle* h, Level& lv, double* data, int64_t slabs, double axis_scale) {
+  const int n = lv.n, Nf = n + 1;
+  if (!df_len(Nf) || lv.tdf.sinp == nullptr) {
+    dst_axes<double>(h, lv, data, slabs, axis_scale);
+    return;
+  }
+  const int64_t nlines = slabs * lv.Nx / n;
+  const double line_flops = dst_line_flops(n);
+  const stmg::dfloat scale(axis_scale);   // 1 or 2 / Nf: exact in FP32
+  int64_t inner = 1;
+  for (int a = 0; a < h->d; ++a) {
+    Prof pr(h, ST_K_DST, 8.0 * 2.0 * (double)nlines * n, line_flops * (double)nlines, 1, level_of(h, lv));
+    const bool rows = a == 0, first = a == 0, last = a == h->d - 1;
+    switch (Nf) {
+      case 64: df_launch<3, 2>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      case 128: df_launch<3, 3>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      case 256: df_launch<4, 3>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      default: df_launch<4, 4>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+    }
+    inner *= n;
+  }
+}
+
 // Change of basis of `slabs` spatial fields of level lv: nodes -> sine basis
 // (S, the unnormalised DST-I along every axis) and back (S^{-1} = (2/Nf)^d S).
 template <typename T>
@@ -1260,24 +1351,33 @@ struct CycleInputs {
   const double* u0;
 };
 
+// Basis change of the finest-level FP64 vectors at the boundary of a solve: in
+// FP64, or in double-float on the FP32 pipe for the mixed form.
+void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
+  Level& lv = finest(h);
+  const double sc = inverse ? 2.0 / (lv.n + 1) : 1.0;
+  if (h->opt.precision == ST_MIXED) dst_axes_df(h, lv, data, slabs, sc);
+  else dst_axes<double>(h, lv, data, slabs, sc);
+}
+
 CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, double* u, bool u_given) {
   Level& lv = finest(h);
   if (!modal(h)) return {f, u0};
   copy<double>(h, lv.v64.f, f, lv.ndof);
-  to_modal<double>(h, lv, lv.v64.f, (int64_t)lv.N * h->q);
+  boundary_dst(h, lv.v64.f, (int64_t)lv.N * h->q, false);
   const double* u0m = nullptr;
   if (u0) {
     copy<double>(h, h->u0m, u0, lv.Nx);
-    to_modal<double>(h, lv, h->u0m, 1);
+    boundary_dst(h, h->u0m, 1, false);
     u0m = h->u0m;
   }
-  if (u_given) to_modal<double>(h, lv, u, (int64_t)lv.N * h->q);
+  if (u_given) boundary_dst(h, u, (int64_t)lv.N * h->q, false);
   return {lv.v64.f, u0m};
 }
 
 void leave_cycle_basis(st_handle* h, double* u) {
   Level& lv = finest(h);
-  if (modal(h)) from_modal<double>(h, lv, u, (int64_t)lv.N * h->q);
+  if (modal(h)) boundary_dst(h, u, (int64_t)lv.N * h->q, true);
 }
 
 int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double* u, int flags, int* iters,
@@ -1474,7 +1574,19 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       }
     }
     dst_set_smem_limits<double>(h);
-    if (mixed) dst_set_smem_limits<float>(h);
+    if (mixed) {
+      dst_set_smem_limits<float>(h);
+      Level& fl = finest(h);
+      if (df_len(fl.n + 1)) {
+        make_df_tables(h, fl);
+        switch (fl.n + 1) {
+          case 64: df_set_smem<3, 2>(h); break;
+          case 128: df_set_smem<3, 3>(h); break;
+          case 256: df_set_smem<4, 3>(h); break;
+          default: df_set_smem<4, 4>(h); break;
+        }
+      }
+    }
     h->partial = dalloc<double>(h, kNormBlocks);
     h->dnorm = dalloc<double>(h, 1);
     check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");

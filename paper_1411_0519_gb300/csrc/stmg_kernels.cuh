@@ -303,6 +303,74 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_residual2d(const T* __restr
 // columns so that every global access is a W-wide contiguous segment
 // (k_dst_cols).  Twiddles are staged in shared memory once per CTA.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 pipe, for the sine transforms of the
+// mixed-precision form: a value is hi + lo with |lo| <= ulp(hi) / 2 (about 48
+// significand bits).  Error-free transformations: Knuth's TwoSum, Dekker's
+// FastTwoSum and the exact product through one FMA; the sum is the "sloppy"
+// double-word addition and the product the double-word multiplication of
+// Joldes, Muller and Popescu (ACM TOMS 43(2), 2017), whose absolute errors are
+// a few units of 2^-48 of the operands' magnitudes -- the measure that bounds
+// the error of a linear transform such as the FFT.  Exponent range is FP32's.
+// ---------------------------------------------------------------------------
+struct dfloat {
+  float hi, lo;
+  __host__ __device__ dfloat() : hi(0.f), lo(0.f) {}
+  __host__ __device__ dfloat(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit dfloat(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ explicit dfloat(int v) : hi((float)v), lo(0.f) {}
+};
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  return dfloat(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
+  const dfloat s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat x, dfloat y) { return x + (-y); }
+__device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = x + y; }
+__device__ __forceinline__ bool operator==(dfloat x, dfloat y) { return x.hi == y.hi && x.lo == y.lo; }
+
+// Warp shuffles and storage conversions for the arithmetic types of the transforms.
+template <typename T>
+__device__ __forceinline__ T shfl_up_t(T v, int off, int width) { return __shfl_up_sync(0xffffffffu, v, off, width); }
+template <>
+__device__ __forceinline__ dfloat shfl_up_t<dfloat>(dfloat v, int off, int width) {
+  return dfloat(__shfl_up_sync(0xffffffffu, v.hi, off, width), __shfl_up_sync(0xffffffffu, v.lo, off, width));
+}
+template <typename T>
+__device__ __forceinline__ T shfl_t(T v, int src, int width) { return __shfl_sync(0xffffffffu, v, src, width); }
+template <>
+__device__ __forceinline__ dfloat shfl_t<dfloat>(dfloat v, int src, int width) {
+  return dfloat(__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width));
+}
+template <typename T, typename S>
+__device__ __forceinline__ T load_as(S x) { return x; }
+template <>
+__device__ __forceinline__ dfloat load_as<dfloat, double>(double x) {
+  const float h = __double2float_rn(x);
+  return dfloat(h, __double2float_rn(x - (double)h));
+}
+template <typename S, typename T>
+__device__ __forceinline__ S store_as(T x) { return x; }
+template <>
+__device__ __forceinline__ double store_as<double, dfloat>(dfloat x) { return (double)x.hi + (double)x.lo; }
+
 template <typename T>
 struct DstTables {
   const T* sinp;   // sin(j pi / Nf), j < Nf
@@ -636,10 +704,10 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
   T incl = loc;
 #pragma unroll
   for (int off = 1; off < G; off <<= 1) {
-    const T v = __shfl_up_sync(0xffffffffu, incl, off, G);
+    const T v = shfl_up_t<T>(incl, off, G);
     if (g >= off) incl += v;
   }
-  const T R0 = __shfl_sync(0xffffffffu, Rk[0], 0, G);      // thread 0's first prefix is R_0
+  const T R0 = shfl_t<T>(Rk[0], 0, G);      // thread 0's first prefix is R_0
   const T shift = (incl - loc) - T(0.5) * R0;
 #pragma unroll
   for (int c = 0; c < P; ++c) {
@@ -650,8 +718,11 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
 }
 
 // x-axis sine transform of nrows contiguous rows: data <- scale * DST(data).
-template <typename T, int LP, int LG>
-__global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int n, int64_t nrows, T scale,
+// SIN / SOUT: element types read from and written back to `data` (in place, the
+// same 8 bytes per element); the double-float transforms keep the float pairs
+// between their axis passes and convert only on the first read and last write.
+template <typename T, int LP, int LG, typename SIN = T, typename SOUT = SIN>
+__global__ void __launch_bounds__(256) k_dst_rows_reg(void* __restrict__ data, int n, int64_t nrows, T scale,
                                                       DstTables<T> tb) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int BS = Lay::BS, RS = Lay::RS;
@@ -665,11 +736,11 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int 
   const int rcount = (int)((nrows - r0) < rpc ? (nrows - r0) : rpc);
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   for (int r = warp; r < rcount; r += nw) {     // coalesced, de-interleaved load
-    const T* src = data + (r0 + r) * n;
+    const SIN* src = reinterpret_cast<const SIN*>(data) + (r0 + r) * n;
     T* br = rows + r * RS;
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
-      br[(j & 1) * BS + (j >> 1)] = src[c];
+      br[(j & 1) * BS + (j >> 1)] = load_as<T, SIN>(src[c]);
     }
     if (lane == 0) br[0] = T(0);
   }
@@ -679,12 +750,12 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int 
   __syncthreads();
   const bool unit = scale == T(1);
   for (int r = warp; r < rcount; r += nw) {
-    T* dst = data + (r0 + r) * n;
+    SOUT* dst = reinterpret_cast<SOUT*>(data) + (r0 + r) * n;
     const T* br = rows + r * RS;
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
       const T v = br[(j & 1) * BS + (j >> 1)];
-      dst[c] = unit ? v : scale * v;
+      dst[c] = store_as<SOUT, T>(unit ? v : scale * v);
     }
   }
 }
@@ -696,8 +767,8 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(T* __restrict__ data, int 
 // the per-line buffers of k_dst_rows_reg, transforms each line with a group of
 // G threads and writes them back.  Shared memory: the k_dst_rows_reg layout
 // followed by one int64 line base per line.
-template <typename T, int LP, int LG>
-__global__ void __launch_bounds__(256) k_dst_cols_reg(T* __restrict__ data, int n, int64_t nlines, int64_t inner,
+template <typename T, int LP, int LG, typename SIN = T, typename SOUT = SIN>
+__global__ void __launch_bounds__(256) k_dst_cols_reg(void* __restrict__ data, int n, int64_t nlines, int64_t inner,
                                                       T scale, DstTables<T> tb) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int BS = Lay::BS, RS = Lay::RS;
@@ -720,7 +791,8 @@ __global__ void __launch_bounds__(256) k_dst_cols_reg(T* __restrict__ data, int 
     const int r = idx % rpc, c = idx / rpc;
     if (r < rcount) {
       const int j = c + 1;
-      rows[r * RS + (j & 1) * BS + (j >> 1)] = data[base[r] + (int64_t)c * inner];
+      rows[r * RS + (j & 1) * BS + (j >> 1)] =
+          load_as<T, SIN>(reinterpret_cast<const SIN*>(data)[base[r] + (int64_t)c * inner]);
     }
   }
   if (tid < rpc) rows[tid * RS] = T(0);
@@ -734,7 +806,7 @@ __global__ void __launch_bounds__(256) k_dst_cols_reg(T* __restrict__ data, int 
     if (r < rcount) {
       const int j = c + 1;
       const T v = rows[r * RS + (j & 1) * BS + (j >> 1)];
-      data[base[r] + (int64_t)c * inner] = unit ? v : scale * v;
+      reinterpret_cast<SOUT*>(data)[base[r] + (int64_t)c * inner] = store_as<SOUT, T>(unit ? v : scale * v);
     }
   }
 }

@@ -238,3 +238,29 @@ def test_largest_lines_converge_checked_by_the_node_residual(d, n, p, N):
     assert ratio <= 2e-10
     s.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("d,n,p,N", [(2, 255, 1, 64), (2, 63, 2, 32), (3, 127, 1, 4), (2, 511, 1, 8)])
+def test_mixed_boundary_transforms_keep_the_fp64_residual(d, n, p, N):
+    """The mixed form transforms f and u in double-float arithmetic (register
+    kernels, n + 1 = 64 ... 512).  Its solve stops on the relative residual in
+    the sine basis; the residual recomputed on nodes by the independent stencil
+    kernel must reach the same 1e-8, which an FP32-accurate transform (about
+    1e-7) would not."""
+    require_gpu()
+    from paper_1411_0519_gb300 import stmg
+    T = 1.0
+    f = to_gpu(workloads.uniform_load(d, n, p, N, seed=4))
+    u0 = to_gpu(workloads.sine_ic(d, n))
+    s = stmg.Solver(d, n, p, N, T, rtol=1e-9, maxit=60, precision="mixed", inner_cycles=4)
+    u, it, rr = s.solve(f, u0)
+    s.close()
+    assert rr <= 1e-9
+    s64 = stmg.Solver(d, n, p, N, T, rtol=1e-9, maxit=60)
+    r = s64.residual(f, u, u0)
+    r0 = s64.residual(f, torch.zeros_like(u), u0)
+    s64.close()
+    ratio = (r.norm() / r0.norm()).item()
+    print(f"mixed d={d} n={n} p_t={p} N={N}: {it} refinements, sine-basis {rr:.2e}, node-basis {ratio:.2e}")
+    assert ratio <= 3e-9
+    torch.cuda.empty_cache()
