@@ -137,6 +137,18 @@ int st_vcycle(st_handle* h, double* u, const double* f, const double* u0_ic);
 int st_solve(st_handle* h, const double* f, const double* u0_ic, double* u, int flags,
              int* iters, double* relres);
 
+/* st_solve with HOST buffers f, u0_ic (may be NULL) and u (all N q n^d values,
+ * n^d for u0_ic), on the handle's stream; returns when u is in host memory.
+ * When f and u are page-locked memory registered with CUDA (e.g. from
+ * cudaHostAlloc), the exact block inverse is used and 64 <= n + 1 <= 512, the
+ * first sine-transform pass reads f from host memory and the last inverse pass
+ * writes u to it over the CPU-GPU interconnect, so no separate copies are
+ * made; otherwise the buffers are copied.  A device buffer for u is allocated
+ * on the first call and kept by the handle.
+ * Errors: as st_solve, and ST_ENOMEM if that buffer cannot be allocated. */
+int st_solve_host(st_handle* h, const double* f, const double* u0_ic, double* u, int flags,
+                  int* iters, double* relres);
+
 /* Adjoint solve L^T lambda = g (transposed, backward-in-time system) with the
  * same hierarchy and transfers.  grad_u0 (may be NULL) receives
  * M_h sum_k psi_k(t_0^+) lambda_{1,k}, the derivative of a loss with

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -201,6 +202,7 @@ struct st_handle {
   double* coarse64_r = nullptr;
   double* r64 = nullptr;         // mixed precision: finest FP64 residual
   double* u0m = nullptr;         // transformed initial value (sine basis)
+  double* u_dev = nullptr;        // st_solve_host: device solution buffer (allocated on first use)
   // generic-q kernels: Mh (1/(2k+1)), R1, R2 and R1, R2 times 2^d (prolongation), q x q row-major
   double* tt64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   float* tt32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -872,12 +874,18 @@ double dst_line_flops(int n) {
   return 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
 }
 
-// scale * DST-I along every spatial axis of `slabs` consecutive
-// spatial fields of level lv (in place; `scale` is applied once per axis).
+// scale * DST-I along every spatial axis of `slabs` consecutive spatial fields
+// of level lv.  The first pass reads src, the last writes dst, intermediate
+// results live in mid (src == mid == dst: in place).  `scale` is applied once
+// per axis.  src / dst other than mid need the register kernels
+// (64 <= n + 1 <= 512); the other kernels work in place on mid.
 template <typename T>
-void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale) {
+void dst_axes(st_handle* h, Level& lv, const T* src, T* mid, T* dst, int64_t slabs, double axis_scale) {
   const int n = lv.n, Nf = n + 1;
   const int naxes = h->d;
+  const bool reg = Nf >= 64 && Nf <= 512;
+  if (!reg && src != mid) fail(h, ST_EINVAL, "out-of-place sine transform needs 64 <= n + 1 <= 512");
+  if (!reg && dst != mid) fail(h, ST_EINVAL, "out-of-place sine transform needs 64 <= n + 1 <= 512");
   int logh = 0;
   while ((1 << (logh + 1)) <= Nf / 2) ++logh;
   Tables<T>& tb = tables<T>(lv);
@@ -887,53 +895,35 @@ void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale
   int64_t inner = 1;
   for (int a = 0; a < naxes; ++a) {
     const T scale = (T)axis_scale;
+    const T* in = (a == 0) ? src : mid;
+    T* out = (a == naxes - 1) ? dst : mid;
+    T* data = mid;
     Prof pr(h, ST_K_DST, sizeof(T) * 2.0 * (double)nlines * n, line_flops * (double)nlines, 1, level_of(h, lv));
-    if (a == 0 && Nf >= 64 && Nf <= 512) {
+    if (reg) {
       const int thr = dst_reg_threads<T>();
       const int G = (Nf == 64) ? 4 : (Nf == 512) ? 16 : 8;
       const int rows = thr / G;
       const unsigned grid = (unsigned)((nlines + rows - 1) / rows);
+#define STMG_DST_REG(LP, LG)                                                                                   \
+  do {                                                                                                         \
+    if (a == 0)                                                                                                \
+      stmg::k_dst_rows_reg<T, LP, LG><<<grid, thr, dst_reg_smem<T, LP, LG>(), h->stream>>>(in, out, n, nlines, \
+                                                                                           scale, dt);         \
+    else                                                                                                       \
+      stmg::k_dst_cols_reg<T, LP, LG><<<grid, thr, dst_cols_reg_smem<T, LP, LG>(), h->stream>>>(               \
+          in, out, n, nlines, inner, scale, dt);                                                               \
+  } while (0)
       switch (Nf) {
-        case 64:
-          stmg::k_dst_rows_reg<T, 3, 2><<<grid, thr, dst_reg_smem<T, 3, 2>(), h->stream>>>(data, n, nlines, scale, dt);
-          break;
-        case 128:
-          stmg::k_dst_rows_reg<T, 3, 3><<<grid, thr, dst_reg_smem<T, 3, 3>(), h->stream>>>(data, n, nlines, scale, dt);
-          break;
-        case 256:
-          stmg::k_dst_rows_reg<T, 4, 3><<<grid, thr, dst_reg_smem<T, 4, 3>(), h->stream>>>(data, n, nlines, scale, dt);
-          break;
-        default:
-          stmg::k_dst_rows_reg<T, 4, 4><<<grid, thr, dst_reg_smem<T, 4, 4>(), h->stream>>>(data, n, nlines, scale, dt);
-          break;
+        case 64: STMG_DST_REG(3, 2); break;
+        case 128: STMG_DST_REG(3, 3); break;
+        case 256: STMG_DST_REG(4, 3); break;
+        default: STMG_DST_REG(4, 4); break;
       }
+#undef STMG_DST_REG
     } else if (a == 0) {
       const unsigned grid = (unsigned)((nlines + kDstRowsPerCta - 1) / kDstRowsPerCta);
       stmg::k_dst_rows<T><<<grid, kDstWarps * 32, dst_rows_smem<T>(Nf), h->stream>>>(data, n, logh, nlines,
                                                                                      kDstRowsPerCta, scale, dt);
-    } else if (Nf >= 64 && Nf <= 512) {
-      const int thr = dst_reg_threads<T>();
-      const int G = (Nf == 64) ? 4 : (Nf == 512) ? 16 : 8;
-      const int rows = thr / G;
-      const unsigned grid = (unsigned)((nlines + rows - 1) / rows);
-      switch (Nf) {
-        case 64:
-          stmg::k_dst_cols_reg<T, 3, 2><<<grid, thr, dst_cols_reg_smem<T, 3, 2>(), h->stream>>>(data, n, nlines, inner,
-                                                                                               scale, dt);
-          break;
-        case 128:
-          stmg::k_dst_cols_reg<T, 3, 3><<<grid, thr, dst_cols_reg_smem<T, 3, 3>(), h->stream>>>(data, n, nlines, inner,
-                                                                                               scale, dt);
-          break;
-        case 256:
-          stmg::k_dst_cols_reg<T, 4, 3><<<grid, thr, dst_cols_reg_smem<T, 4, 3>(), h->stream>>>(data, n, nlines, inner,
-                                                                                               scale, dt);
-          break;
-        default:
-          stmg::k_dst_cols_reg<T, 4, 4><<<grid, thr, dst_cols_reg_smem<T, 4, 4>(), h->stream>>>(data, n, nlines, inner,
-                                                                                               scale, dt);
-          break;
-      }
     } else if (sizeof(T) == 8 && Nf >= 512) {
       const unsigned grid = (unsigned)((nlines + 15) / 16);
       stmg::k_dst_cols<T, 16><<<grid, kDstWarps * 32, dst_cols_smem<T, 16>(Nf), h->stream>>>(data, n, logh, nlines,
@@ -945,6 +935,11 @@ void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale
     }
     inner *= n;
   }
+}
+
+template <typename T>
+void dst_axes(st_handle* h, Level& lv, T* data, int64_t slabs, double axis_scale) {
+  dst_axes<T>(h, lv, data, data, data, slabs, axis_scale);
 }
 
 // ---- double-float sine transforms (mixed form): the register kernels with
@@ -988,7 +983,7 @@ void df_set_smem(st_handle* h) {
 }
 
 template <int LP, int LG, typename SIN, typename SOUT>
-void df_launch_io(st_handle* h, double* data, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
+void df_launch_io(st_handle* h, const void* in, void* out, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
                   stmg::DstTables<stmg::dfloat> dt, bool rows) {
   using DF = stmg::dfloat;
   constexpr int G = 1 << LG;
@@ -996,28 +991,30 @@ void df_launch_io(st_handle* h, double* data, int n, int64_t nlines, int64_t inn
   const unsigned grid = (unsigned)((nlines + thr / G - 1) / (thr / G));
   if (rows)
     stmg::k_dst_rows_reg<DF, LP, LG, SIN, SOUT><<<grid, thr, dst_reg_smem<DF, LP, LG>(), h->stream>>>(
-        data, n, nlines, scale, dt);
+        in, out, n, nlines, scale, dt);
   else
     stmg::k_dst_cols_reg<DF, LP, LG, SIN, SOUT><<<grid, thr, dst_cols_reg_smem<DF, LP, LG>(), h->stream>>>(
-        data, n, nlines, inner, scale, dt);
+        in, out, n, nlines, inner, scale, dt);
 }
 
 // first / last axis pass: FP64 in / out; between passes the 8-byte slots hold float pairs
 template <int LP, int LG>
-void df_launch(st_handle* h, double* data, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
+void df_launch(st_handle* h, const void* in, void* out, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
                stmg::DstTables<stmg::dfloat> dt, bool rows, bool first, bool last) {
   using DF = stmg::dfloat;
-  if (first && last) df_launch_io<LP, LG, double, double>(h, data, n, nlines, inner, scale, dt, rows);
-  else if (first) df_launch_io<LP, LG, double, DF>(h, data, n, nlines, inner, scale, dt, rows);
-  else if (last) df_launch_io<LP, LG, DF, double>(h, data, n, nlines, inner, scale, dt, rows);
-  else df_launch_io<LP, LG, DF, DF>(h, data, n, nlines, inner, scale, dt, rows);
+  if (first && last) df_launch_io<LP, LG, double, double>(h, in, out, n, nlines, inner, scale, dt, rows);
+  else if (first) df_launch_io<LP, LG, double, DF>(h, in, out, n, nlines, inner, scale, dt, rows);
+  else if (last) df_launch_io<LP, LG, DF, double>(h, in, out, n, nlines, inner, scale, dt, rows);
+  else df_launch_io<LP, LG, DF, DF>(h, in, out, n, nlines, inner, scale, dt, rows);
 }
 
-// scale * DST-I along every axis of `slabs` FP64 fields, computed in double-float.
-void dst_axes_df(st_handle* h, Level& lv, double* data, int64_t slabs, double axis_scale) {
+// scale * DST-I along every axis of `slabs` FP64 fields, computed in double-float
+// (src / mid / dst as in dst_axes).
+void dst_axes_df(st_handle* h, Level& lv, const double* src, double* mid, double* dst, int64_t slabs,
+                 double axis_scale) {
   const int n = lv.n, Nf = n + 1;
   if (!df_len(Nf) || lv.tdf.sinp == nullptr) {
-    dst_axes<double>(h, lv, data, slabs, axis_scale);
+    dst_axes<double>(h, lv, src, mid, dst, slabs, axis_scale);
     return;
   }
   const int64_t nlines = slabs * lv.Nx / n;
@@ -1027,11 +1024,13 @@ void dst_axes_df(st_handle* h, Level& lv, double* data, int64_t slabs, double ax
   for (int a = 0; a < h->d; ++a) {
     Prof pr(h, ST_K_DST, 8.0 * 2.0 * (double)nlines * n, line_flops * (double)nlines, 1, level_of(h, lv));
     const bool rows = a == 0, first = a == 0, last = a == h->d - 1;
+    const void* in = first ? (const void*)src : (const void*)mid;
+    void* out = last ? (void*)dst : (void*)mid;
     switch (Nf) {
-      case 64: df_launch<3, 2>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
-      case 128: df_launch<3, 3>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
-      case 256: df_launch<4, 3>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
-      default: df_launch<4, 4>(h, data, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      case 64: df_launch<3, 2>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      case 128: df_launch<3, 3>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      case 256: df_launch<4, 3>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      default: df_launch<4, 4>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
     }
     inner *= n;
   }
@@ -1353,11 +1352,14 @@ struct CycleInputs {
 
 // Basis change of the finest-level FP64 vectors at the boundary of a solve: in
 // FP64, or in double-float on the FP32 pipe for the mixed form.
-void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
+void boundary_dst(st_handle* h, const double* src, double* mid, double* dst, int64_t slabs, bool inverse) {
   Level& lv = finest(h);
   const double sc = inverse ? 2.0 / (lv.n + 1) : 1.0;
-  if (h->opt.precision == ST_MIXED) dst_axes_df(h, lv, data, slabs, sc);
-  else dst_axes<double>(h, lv, data, slabs, sc);
+  if (h->opt.precision == ST_MIXED) dst_axes_df(h, lv, src, mid, dst, slabs, sc);
+  else dst_axes<double>(h, lv, src, mid, dst, slabs, sc);
+}
+void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
+  boundary_dst(h, data, data, data, slabs, inverse);
 }
 
 CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, double* u, bool u_given) {
@@ -1380,12 +1382,10 @@ void leave_cycle_basis(st_handle* h, double* u) {
   if (modal(h)) boundary_dst(h, u, (int64_t)lv.N * h->q, true);
 }
 
-int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double* u, int flags, int* iters,
-               double* relres) {
+// The cycles of a solve with the inputs already in the basis of the cycle.
+int solve_core(st_handle* h, bool adj, const CycleInputs& in, double* u, bool given, int* iters, double* relres) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
-  const bool given = (flags & ST_INIT_GIVEN) != 0;
-  const CycleInputs in = enter_cycle_basis(h, f, u0, u, given);
   if (!given) zero<double>(h, u, lv.ndof);
   double* r = (h->opt.precision == ST_MIXED) ? h->r64 : lv.v64.r;
   cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
@@ -1409,9 +1409,77 @@ int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double
     if (!std::isfinite(rn)) { status = ST_ENAN; h->err = "residual norm is not finite"; break; }
     if (rn > 1e6 * r0) { status = ST_ENOTCONV; h->err = "residual grew by 1e6"; break; }
   }
-  leave_cycle_basis(h, u);
   if (iters) *iters = it;
   if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
+  return status;
+}
+
+int solve_impl(st_handle* h, bool adj, const double* f, const double* u0, double* u, int flags, int* iters,
+               double* relres) {
+  const bool given = (flags & ST_INIT_GIVEN) != 0;
+  const CycleInputs in = enter_cycle_basis(h, f, u0, u, given);
+  const int status = solve_core(h, adj, in, u, given, iters, relres);
+  leave_cycle_basis(h, u);
+  return status;
+}
+
+// Device address of a host buffer that kernels may read and write in place:
+// page-locked memory registered with CUDA, reached over the CPU-GPU
+// interconnect (on this system the host pointer itself is the device
+// address).  nullptr for pageable or unknown memory.
+const void* device_view(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+  return at.devicePointer;
+}
+
+// Solve with host buffers.  With the exact block inverse and a register
+// sine-transform length, the first transform pass reads f from registered host
+// memory and the last inverse pass writes u to it, so the transfers ride on the
+// transforms instead of separate copies; otherwise plain copies.
+int solve_host_impl(st_handle* h, const double* f, const double* u0, double* u, int flags, int* iters,
+                    double* relres) {
+  Level& lv = finest(h);
+  const bool given = (flags & ST_INIT_GIVEN) != 0;
+  const int64_t slabs = (int64_t)lv.N * h->q;
+  const size_t bytes = sizeof(double) * lv.ndof;
+  if (!h->u_dev) h->u_dev = dalloc<double>(h, lv.ndof);
+  const bool md = modal(h);
+  const bool in_place = md && lv.n + 1 >= 64 && lv.n + 1 <= 512;
+  const double* fv = in_place ? static_cast<const double*>(device_view(f)) : nullptr;
+  double* uv = in_place ? static_cast<double*>(const_cast<void*>(device_view(u))) : nullptr;
+  CycleInputs in{lv.v64.f, nullptr};
+  if (u0) {
+    check(h, cudaMemcpyAsync(h->u0m, u0, sizeof(double) * lv.Nx, cudaMemcpyHostToDevice, h->stream), "copy u0");
+    if (md) boundary_dst(h, h->u0m, 1, false);
+    in.u0 = h->u0m;
+  }
+  if (fv) {
+    boundary_dst(h, fv, lv.v64.f, lv.v64.f, slabs, false);
+  } else {
+    check(h, cudaMemcpyAsync(lv.v64.f, f, bytes, cudaMemcpyHostToDevice, h->stream), "copy f");
+    if (md) boundary_dst(h, lv.v64.f, slabs, false);
+  }
+  if (given) {
+    if (uv) {
+      boundary_dst(h, uv, h->u_dev, h->u_dev, slabs, false);
+    } else {
+      check(h, cudaMemcpyAsync(h->u_dev, u, bytes, cudaMemcpyHostToDevice, h->stream), "copy u");
+      if (md) boundary_dst(h, h->u_dev, slabs, false);
+    }
+  }
+  const int status = solve_core(h, false, in, h->u_dev, given, iters, relres);
+  if (uv) {
+    boundary_dst(h, h->u_dev, h->u_dev, uv, slabs, true);
+  } else {
+    if (md) boundary_dst(h, h->u_dev, slabs, true);
+    check(h, cudaMemcpyAsync(u, h->u_dev, bytes, cudaMemcpyDeviceToHost, h->stream), "copy u back");
+  }
+  check(h, cudaStreamSynchronize(h->stream), "solve_host sync");
   return status;
 }
 
@@ -1674,6 +1742,16 @@ int st_solve(st_handle* h, const double* f, const double* u0_ic, double* u, int 
   return guarded(h, [&]() -> int {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
     int rc = solve_impl(h, false, f, u0_ic, u, flags, iters, relres);
+    after_launch(h);
+    return rc;
+  });
+}
+
+int st_solve_host(st_handle* h, const double* f, const double* u0_ic, double* u, int flags, int* iters,
+                  double* relres) {
+  return guarded(h, [&]() -> int {
+    if (!f || !u) fail(h, ST_EINVAL, "null pointer");
+    int rc = solve_host_impl(h, f, u0_ic, u, flags, iters, relres);
     after_launch(h);
     return rc;
   });

@@ -718,12 +718,14 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
 }
 
 // x-axis sine transform of nrows contiguous rows: data <- scale * DST(data).
-// SIN / SOUT: element types read from and written back to `data` (in place, the
-// same 8 bytes per element); the double-float transforms keep the float pairs
-// between their axis passes and convert only on the first read and last write.
+// Reads src_data, writes dst_data (the same buffer for an in-place pass; a CTA
+// reads all of its rows before it writes any).  SIN / SOUT: element types read
+// and written (8 bytes each for the double-float transforms, which keep float
+// pairs between their axis passes and convert only on the first read and the
+// last write).
 template <typename T, int LP, int LG, typename SIN = T, typename SOUT = SIN>
-__global__ void __launch_bounds__(256) k_dst_rows_reg(void* __restrict__ data, int n, int64_t nrows, T scale,
-                                                      DstTables<T> tb) {
+__global__ void __launch_bounds__(256) k_dst_rows_reg(const void* src_data, void* dst_data, int n, int64_t nrows,
+                                                      T scale, DstTables<T> tb) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int BS = Lay::BS, RS = Lay::RS;
   extern __shared__ unsigned char smem_raw[];
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(void* __restrict__ data, i
   const int rcount = (int)((nrows - r0) < rpc ? (nrows - r0) : rpc);
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   for (int r = warp; r < rcount; r += nw) {     // coalesced, de-interleaved load
-    const SIN* src = reinterpret_cast<const SIN*>(data) + (r0 + r) * n;
+    const SIN* src = reinterpret_cast<const SIN*>(src_data) + (r0 + r) * n;
     T* br = rows + r * RS;
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
@@ -750,7 +752,7 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(void* __restrict__ data, i
   __syncthreads();
   const bool unit = scale == T(1);
   for (int r = warp; r < rcount; r += nw) {
-    SOUT* dst = reinterpret_cast<SOUT*>(data) + (r0 + r) * n;
+    SOUT* dst = reinterpret_cast<SOUT*>(dst_data) + (r0 + r) * n;
     const T* br = rows + r * RS;
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
@@ -768,8 +770,8 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(void* __restrict__ data, i
 // G threads and writes them back.  Shared memory: the k_dst_rows_reg layout
 // followed by one int64 line base per line.
 template <typename T, int LP, int LG, typename SIN = T, typename SOUT = SIN>
-__global__ void __launch_bounds__(256) k_dst_cols_reg(void* __restrict__ data, int n, int64_t nlines, int64_t inner,
-                                                      T scale, DstTables<T> tb) {
+__global__ void __launch_bounds__(256) k_dst_cols_reg(const void* src_data, void* dst_data, int n, int64_t nlines,
+                                                      int64_t inner, T scale, DstTables<T> tb) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int BS = Lay::BS, RS = Lay::RS;
   extern __shared__ unsigned char smem_raw[];
@@ -792,7 +794,7 @@ __global__ void __launch_bounds__(256) k_dst_cols_reg(void* __restrict__ data, i
     if (r < rcount) {
       const int j = c + 1;
       rows[r * RS + (j & 1) * BS + (j >> 1)] =
-          load_as<T, SIN>(reinterpret_cast<const SIN*>(data)[base[r] + (int64_t)c * inner]);
+          load_as<T, SIN>(reinterpret_cast<const SIN*>(src_data)[base[r] + (int64_t)c * inner]);
     }
   }
   if (tid < rpc) rows[tid * RS] = T(0);
@@ -806,7 +808,7 @@ __global__ void __launch_bounds__(256) k_dst_cols_reg(void* __restrict__ data, i
     if (r < rcount) {
       const int j = c + 1;
       const T v = rows[r * RS + (j & 1) * BS + (j >> 1)];
-      reinterpret_cast<SOUT*>(data)[base[r] + (int64_t)c * inner] = store_as<SOUT, T>(unit ? v : scale * v);
+      reinterpret_cast<SOUT*>(dst_data)[base[r] + (int64_t)c * inner] = store_as<SOUT, T>(unit ? v : scale * v);
     }
   }
 }

@@ -25,7 +25,8 @@ ST_SMOOTH_EXACT, ST_SMOOTH_VCYCLE = 0, 1
 
 EXPORTS = [
     "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
-    "st_level_info", "st_residual", "st_vcycle", "st_solve", "st_adjoint_solve", "st_level_residual",
+    "st_level_info", "st_residual", "st_vcycle", "st_solve", "st_solve_host", "st_adjoint_solve",
+    "st_level_residual",
     "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
     "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop", "st_profile_level", "st_norm2_noalloc",
 ]
@@ -80,6 +81,7 @@ def load_library(path=None):
         "st_residual": (I, [H, P, P, P, P]),
         "st_vcycle": (I, [H, P, P, P]),
         "st_solve": (I, [H, P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "st_solve_host": (I, [H, P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "st_adjoint_solve": (I, [H, P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "st_level_residual": (I, [H, I, I, P, P, P]),
         "st_level_block_solve": (I, [H, I, I, P, P]),
@@ -226,6 +228,28 @@ class Solver:
         it, rr = ctypes.c_int(), ctypes.c_double()
         rc = self._lib.st_solve(self._h, _ptr(f, self.ndof, "f"), _ptr(u0, nx, "u0"), _ptr(u, self.ndof, "u"),
                                 ST_INIT_GIVEN if init else 0, ctypes.byref(it), ctypes.byref(rr))
+        self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
+        self.last_status = rc
+        return u, it.value, rr.value
+
+    def solve_host(self, f, u0=None, u=None, initial_guess=False, raise_on_failure=True):
+        """st_solve with host (CPU) tensors.  For pinned tensors the library's first
+        sine-transform pass reads f from host memory and its last inverse pass writes
+        the solution into ``u`` (a CPU tensor, allocated pinned if None); other host
+        memory is copied.  Returns (u, iterations, relative residual)."""
+        if u is None:
+            u = torch.empty(self.shape, dtype=torch.float64).pin_memory()
+        nx = self.n ** self.dim
+        for name, t, cnt in (("f", f, self.ndof), ("u", u, self.ndof), ("u0", u0, nx)):
+            if t is None:
+                continue
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != cnt:
+                raise ValueError(f"{name}: need a contiguous float64 CPU tensor with {cnt} elements")
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        rc = self._lib.st_solve_host(self._h, ctypes.c_void_p(f.data_ptr()),
+                                     ctypes.c_void_p(u0.data_ptr()) if u0 is not None else None,
+                                     ctypes.c_void_p(u.data_ptr()), ST_INIT_GIVEN if initial_guess else 0,
+                                     ctypes.byref(it), ctypes.byref(rr))
         self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
         self.last_status = rc
         return u, it.value, rr.value

@@ -221,3 +221,27 @@ def test_manufactured_heat1d_63():
     assert rel_err(to_np(u), uo) < 1e-10
     ue = lambda cc, t: np.sin(np.pi * cc[0]) * np.cos(t)
     assert spacetime.l2_error(disc, to_np(u).reshape(disc.shape()), ue, T) < 2e-4
+
+
+@pytest.mark.parametrize("d,n,p,N,cs", [(2, 7, 1, 1, 1), (1, 15, 2, 4, 4), (3, 3, 0, 2, 2), (2, 1, 1, 8, 1)])
+def test_single_level_and_tiny_grids(d, n, p, N, cs):
+    """Edge cases of the hierarchy: one level (N <= coarsest_steps: the exact
+    coarsest solve must carry the initial value) and a one-node grid."""
+    require_gpu()
+    from paper_1411_0519_gb300 import stmg
+    T = 0.5
+    c = Case(d, n, p, N, T, coarsest_steps=cs, rtol=1e-12, maxit=40)
+    try:
+        disc = c.H.finest.disc
+        f = rand(disc.shape(), 7)
+        u0 = workloads.smooth_ic(d, n, seed=8) if n > 1 else np.array([0.7])
+        u, it, rr = c.solver.solve(to_gpu(f), to_gpu(u0))
+        g = spacetime.add_ic(disc, f, u0)
+        uo, ito, _ = multigrid.solve(c.H, g, rtol=1e-12, maxit=40)
+        assert abs(it - ito) <= 1 and rr <= 1e-12
+        assert rel_err(to_np(u), uo) < 1e-10
+        lam, gu0, ita, rra = c.solver.adjoint_solve(to_gpu(f))
+        lo, _, _ = multigrid.solve(c.H, f, rtol=1e-12, maxit=40, adjoint=True)
+        assert rel_err(to_np(lam), lo) < 1e-10
+    finally:
+        c.close()

@@ -264,3 +264,25 @@ def test_mixed_boundary_transforms_keep_the_fp64_residual(d, n, p, N):
     print(f"mixed d={d} n={n} p_t={p} N={N}: {it} refinements, sine-basis {rr:.2e}, node-basis {ratio:.2e}")
     assert ratio <= 3e-9
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision,given", [("fp64", False), ("mixed", False), ("fp64", True)])
+def test_solve_host_matches_device_solve(precision, given):
+    """st_solve_host (host buffers, chunked copies overlapped with the
+    transforms) returns the same solution as st_solve on device buffers."""
+    require_gpu()
+    from paper_1411_0519_gb300 import stmg
+    d, n, p, N, T = 2, 63, 1, 32, 1.0
+    f_np = workloads.uniform_load(d, n, p, N, seed=5)
+    u0_np = workloads.sine_ic(d, n)
+    s = stmg.Solver(d, n, p, N, T, rtol=1e-10, maxit=60, precision=precision, inner_cycles=4)
+    guess = np.random.default_rng(9).uniform(-1, 1, s.shape) if given else None
+    ud = to_gpu(guess) if given else None
+    u_dev, it_d, rr_d = s.solve(to_gpu(f_np), to_gpu(u0_np), u=ud, initial_guess=given)
+    fh = torch.from_numpy(f_np).pin_memory()
+    u0h = torch.from_numpy(u0_np).pin_memory()
+    uh = torch.from_numpy(guess.copy()).pin_memory() if given else None
+    u_host, it_h, rr_h = s.solve_host(fh, u0h, uh, initial_guess=given)
+    s.close()
+    assert it_h == it_d and rr_h <= 1e-10
+    assert rel_err(u_host.numpy(), to_np(u_dev)) < 1e-13
