@@ -167,6 +167,9 @@ struct SpaceLvl {
   T* x = nullptr;
   T* b = nullptr;
   T* t = nullptr;
+  T* amat[2] = {nullptr, nullptr};   // A_i per mode of this spatial grid (forward, transposed)
+  T* ra = nullptr;                   // mode-pair weights to the next coarser spatial grid
+  T* rb = nullptr;
 };
 
 struct Level {
@@ -436,6 +439,25 @@ void make_space(st_handle* h, Level& lv, std::vector<SpaceLvl<T>>& sp) {
     s.x = dalloc<T>(h, cnt);
     s.t = dalloc<T>(h, cnt);
     if (!sp.empty()) s.b = dalloc<T>(h, cnt);   // the finest spatial level reads the caller's vector
+    for (int adj = 0; adj < 2; ++adj) {   // the spatial operator A_i of this grid, in the sine basis
+      std::vector<double> am, ai, lm, lk;
+      mode_blocks(h->tm, h->d, nl, hl, lv.tau, adj != 0, am, ai, lm, lk);
+      s.amat[adj] = dalloc<T>(h, am.size());
+      upload(h, s.amat[adj], am);
+    }
+    if (nl > 1) {
+      const int nc = (nl - 1) / 2;
+      std::vector<double> a(nc), b(nc);
+      for (int k = 1; k <= nc; ++k) {
+        const double c = std::cos(k * M_PI / (nl + 1));
+        a[k - 1] = 0.5 * (1.0 + c);
+        b[k - 1] = -0.5 * (1.0 - c);
+      }
+      s.ra = dalloc<T>(h, nc);
+      s.rb = dalloc<T>(h, nc);
+      upload(h, s.ra, a);
+      upload(h, s.rb, b);
+    }
     sp.push_back(s);
     if (nl == 1) break;
     nl = (nl - 1) / 2;
@@ -608,29 +630,27 @@ void launch_ic_grad_dyn_t(st_handle* h, const Level& lv, const T* lam, T* g) {
   stmg::k_ic_gradient_dyn<T, D><<<blocks_for(lv.Nx), kThreads, 0, h->stream>>>(lam, g, lv.n, (T)lv.h, h->q);
 }
 
-// Restriction / prolongation between levels L and L-1.  modal: vectors in the
-// mixed basis (full coarsening pairs sine modes); otherwise on nodes.  Semi
-// coarsening is the identity in space and the same kernel serves both.
+// Restriction / prolongation between levels L and L-1 in the sine basis: full
+// coarsening pairs sine modes; semi coarsening is the identity in space (the
+// node-basis kernel with FULL = false is the same operation in any basis).
 template <typename T, int D, int Q>
-void launch_restrict_t(st_handle* h, Level& fine, const Level& coarse, bool modal, const T* r, T* fc) {
+void launch_restrict_t(st_handle* h, Level& fine, const Level& coarse, const T* r, T* fc) {
   auto tc = to_coef<T, Q>(h->tm);
   dim3 grid(blocks_for(coarse.Nx), coarse.N);
   if (!fine.coarsen_full)
     stmg::k_restrict<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
-  else if (modal)
+  else
     stmg::k_frestrict<T, D, Q><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N,
                                                                   tables<T>(fine).ra, tables<T>(fine).rb, tc);
-  else
-    stmg::k_restrict<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(r, fc, fine.n, coarse.n, coarse.N, tc);
 }
 
 template <typename T, int D, int Q>
-void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, bool modal, const T* ec, T* uf) {
+void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, const T* ec, T* uf) {
   auto tc = to_coef<T, Q>(h->tm);
   dim3 grid(blocks_for(fine.Nx), fine.N);
-  if (!fine.coarsen_full)
+  if (!fine.coarsen_full) {
     stmg::k_prolong<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
-  else if (modal) {
+  } else {
     // pair weights of the prolongation are 2 ra, 2 rb per axis: fold 2^D into R^T
     for (int i = 0; i < Q * Q; ++i) {
       tc.R1[i] *= (T)(1 << D);
@@ -639,8 +659,6 @@ void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, bool modal
     stmg::k_fprolong<T, D, Q><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N,
                                                                  tables<T>(fine).ra, tables<T>(fine).rb, tc);
   }
-  else
-    stmg::k_prolong<T, D, Q, true><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
 }
 
 template <typename T, int D, int Q>
@@ -650,36 +668,30 @@ void launch_ic_grad_t(st_handle* h, const Level& lv, const T* lam, T* g) {
 }
 
 template <typename T, int D, int Q>
-void launch_space_op_t(st_handle* h, const Level& lv, int n, double hl, int mode, bool adj, const T* x, const T* b,
-                       T* xo, double w, const double* dinv) {
-  auto tc = to_coef<T, Q>(h->tm);
+void launch_space_op_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, int mode, bool adj, const T* x,
+                       const T* b, T* xo, double w, const double* dinv) {
   stmg::SmallMat<T, Q> m{};
   for (int i = 0; i < Q * Q; ++i) m.a[i] = (T)dinv[i];
-  int64_t Nx = 1;
-  for (int a = 0; a < D; ++a) Nx *= n;
-  dim3 grid(blocks_for(Nx), lv.N);
-  const T tau = (T)lv.tau, hh = (T)hl, hinv = (T)(1.0 / hl), ww = (T)w;
-#define STMG_SPACE_OP(ADJ, MODE) \
-  stmg::k_space_op<T, D, Q, ADJ, MODE><<<grid, kThreads, 0, h->stream>>>(x, b, xo, n, lv.N, tau, hh, hinv, ww, m, tc)
-  if (adj) {
-    if (mode == 0) STMG_SPACE_OP(true, 0); else if (mode == 1) STMG_SPACE_OP(true, 1); else STMG_SPACE_OP(true, 2);
-  } else {
-    if (mode == 0) STMG_SPACE_OP(false, 0); else if (mode == 1) STMG_SPACE_OP(false, 1); else STMG_SPACE_OP(false, 2);
-  }
-#undef STMG_SPACE_OP
+  dim3 grid(blocks_for(sl.Nx), lv.N);
+  const T ww = (T)w;
+  const T* am = sl.amat[adj ? 1 : 0];
+  if (mode == 0)
+    stmg::k_fspace_op<T, Q, 0><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
+  else if (mode == 1)
+    stmg::k_fspace_op<T, Q, 1><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
+  else
+    stmg::k_fspace_op<T, Q, 2><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
 }
 
 template <typename T, int D, int Q>
-void launch_space_transfer_t(st_handle* h, const Level& lv, int nf, int nc, bool restrict_, const T* in, T* out) {
-  int64_t Nxf = 1, Nxc = 1;
-  for (int a = 0; a < D; ++a) {
-    Nxf *= nf;
-    Nxc *= nc;
-  }
+void launch_space_transfer_t(st_handle* h, const Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse,
+                             bool restrict_, const T* in, T* out) {
   if (restrict_)
-    stmg::k_restrict_space<T, D, Q><<<dim3(blocks_for(Nxc), lv.N), kThreads, 0, h->stream>>>(in, out, nf, nc, lv.N);
+    stmg::k_fspace_restrict<T, D, Q><<<dim3(blocks_for(coarse.Nx), lv.N), kThreads, 0, h->stream>>>(
+        in, out, fine.n, coarse.n, lv.N, fine.ra, fine.rb);
   else
-    stmg::k_prolong_space<T, D, Q><<<dim3(blocks_for(Nxf), lv.N), kThreads, 0, h->stream>>>(in, out, nf, nc, lv.N);
+    stmg::k_fspace_prolong<T, D, Q><<<dim3(blocks_for(fine.Nx), lv.N), kThreads, 0, h->stream>>>(
+        in, out, fine.n, coarse.n, lv.N, fine.ra, fine.rb, (T)(1 << D));
 }
 
 #define STMG_DISPATCH(FN, ...)                                                   \
@@ -755,29 +767,29 @@ void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* 
 }
 
 template <typename T>
-void restrict_to(st_handle* h, int L, bool modal, const T* r, T* fc) {
+void restrict_to(st_handle* h, int L, const T* r, T* fc) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
-  const double ns = fine.coarsen_full ? std::pow(modal ? 2.0 : 3.0, h->d) : 1.0;
+  const double ns = fine.coarsen_full ? std::pow(2.0, h->d) : 1.0;
   // time blocks: q FMA per coarse dof and block, half of them for q > kQfix (R is lower triangular
   // and the generic-q kernels skip its zeros)
   const double tq = h->q > kQfix ? 0.5 * (h->q + 1) : h->q;
   Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_restrict_dyn_t, h, fine, coarse, r, fc);
-  else STMG_DISPATCH(launch_restrict_t, h, fine, coarse, modal, r, fc);
+  else STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
 }
 
 template <typename T>
-void prolong_add(st_handle* h, int L, bool modal, const T* ec, T* uf) {
+void prolong_add(st_handle* h, int L, const T* ec, T* uf) {
   Level& fine = h->levels[L];
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
-  const double ns = fine.coarsen_full ? (modal ? 1.0 : std::pow(2.0, h->d)) : 1.0;
+  const double ns = 1.0;
   const double tq = h->q > kQfix ? 0.5 * (h->q + 1) : h->q;
   Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_prolong_dyn_t, h, fine, coarse, ec, uf);
-  else STMG_DISPATCH(launch_prolong_t, h, fine, coarse, modal, ec, uf);
+  else STMG_DISPATCH(launch_prolong_t, h, fine, coarse, ec, uf);
 }
 
 template <typename T>
@@ -1113,17 +1125,18 @@ template <typename T>
 void space_op(st_handle* h, Level& lv, const SpaceLvl<T>& sl, int mode, bool adj, const T* x, const T* b, T* xo,
               double w, const double* dinv) {
   const double nodes = (double)lv.N * sl.Nx, Q = h->q;
+  // per (mode, step): A_i x Q^2 FMA (modes 0, 1), Dinv r Q^2 FMA and the update (modes 0, 2)
   Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * nodes * (mode == 2 ? 2.0 : 3.0),
-          2.0 * nodes * (mode == 2 ? Q * Q : Q * (9.0 * h->d - 3.0) + 2.0 * Q * Q + Q), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_space_op_t, h, lv, sl.n, sl.h, mode, adj, x, b, xo, w, dinv);
+          2.0 * nodes * (mode == 2 ? Q * Q : mode == 1 ? Q * Q : 2.0 * Q * Q + Q), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_op_t, h, lv, sl, mode, adj, x, b, xo, w, dinv);
 }
 
 template <typename T>
 void space_transfer(st_handle* h, Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse, bool restrict_,
                     const T* in, T* out) {
   Prof pr(h, ST_K_SPACEMG, sizeof(T) * h->q * (double)lv.N * (restrict_ ? fine.Nx + coarse.Nx : 2.0 * fine.Nx + coarse.Nx),
-          0.0, 1, level_of(h, lv));
-  STMG_DISPATCH(launch_space_transfer_t, h, lv, fine.n, coarse.n, restrict_, in, out);
+          2.0 * h->q * (double)lv.N * (restrict_ ? coarse.Nx * std::pow(2.0, h->d) : fine.Nx), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_transfer_t, h, lv, fine, coarse, restrict_, in, out);
 }
 
 // x = D~^{-1} b on every time step of level lv: one spatial V-cycle from x = 0
@@ -1138,9 +1151,11 @@ void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) 
     space_op<T>(h, lv, sl, 2, adj, nullptr, b, x, 1.0, dinv);
     return;
   }
+  // 2 nu_x sweeps alternate between two buffers; starting in the scratch buffer
+  // makes the last one land in x
   const double w = h->opt.omega_x;
-  T* cur = x;
-  T* oth = sl.t;
+  T* cur = sl.t;
+  T* oth = x;
   space_op<T>(h, lv, sl, 2, adj, nullptr, b, cur, w, dinv);
   for (int i = 1; i < h->opt.nu_x; ++i) {
     space_op<T>(h, lv, sl, 0, adj, cur, b, oth, w, dinv);
@@ -1155,37 +1170,32 @@ void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) 
     space_op<T>(h, lv, sl, 0, adj, cur, b, oth, w, dinv);
     std::swap(cur, oth);
   }
-  if (cur != x) copy<T>(h, x, cur, (int64_t)lv.N * h->q * sl.Nx);
+  if (cur != x) copy<T>(h, x, cur, (int64_t)lv.N * h->q * sl.Nx);   // not reached: 2 nu_x sweeps
 }
 
-// The exact block inverse runs the whole cycle in the mixed basis; the
-// inexact one (spatial V-cycle per step) works on nodes.
-bool modal(const st_handle* h) { return h->opt.smoother == ST_SMOOTH_EXACT; }
+bool inexact(const st_handle* h) { return h->opt.smoother == ST_SMOOTH_VCYCLE; }
 
-// d = D~^{-1} r on nodes, the smoother's block inverse: exact, or one spatial
-// V-cycle.  r and d may be the same buffer.
+// d = D~^{-1} r on nodes, the smoother's block inverse (exact, or one spatial
+// V-cycle), computed in the sine basis.  r and d may be the same buffer.
 template <typename T>
 void smoother_block_solve(st_handle* h, Level& lv, bool adj, const T* r, T* d) {
-  if (!modal(h)) {
-    if (r == d) {
-      T* x = spaces<T>(lv)[0].x;
-      space_vcycle<T>(h, lv, 0, adj, x, r);
-      copy<T>(h, d, x, lv.ndof);
-    } else {
-      space_vcycle<T>(h, lv, 0, adj, d, r);
-    }
-    return;
-  }
   T* tmp = vecs<T>(lv).f;
   copy<T>(h, tmp, r, lv.ndof);
-  block_solve<T>(h, lv, adj, tmp, d, 0, lv.N);
+  if (!inexact(h)) {
+    block_solve<T>(h, lv, adj, tmp, d, 0, lv.N);
+    return;
+  }
+  const int64_t slabs = (int64_t)lv.N * h->q;
+  to_modal<T>(h, lv, tmp, slabs);
+  space_vcycle<T>(h, lv, 0, adj, d, tmp);
+  from_modal<T>(h, lv, d, slabs);
 }
 
-// One damped block-Jacobi step with the inexact block inverse on nodes
-// (eq. chap4_smootherApprox): u <- u + w D~^{-1} (f - L u).
+// One damped block-Jacobi step with the inexact block inverse in the sine
+// basis (eq. chap4_smootherApprox): u <- u + w D~^{-1} (f - L u).
 template <typename T>
-void smooth_step_nodes(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
-  residual<T>(h, lv, adj, f, u, u0, work);
+void smooth_step_inexact(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
+  mresidual<T>(h, lv, adj, f, u, u0, work);
   T* d = spaces<T>(lv)[0].x;
   space_vcycle<T>(h, lv, 0, adj, d, work);
   axpy<T>(h, u, d, (T)h->opt.omega, lv.ndof);
@@ -1226,21 +1236,8 @@ void coarsest_modal(st_handle* h, bool adj, T* u, const T* f, const T* u0) {
   }
 }
 
-// The same on nodes: residual of step s with u_s = 0, then the block inverse.
-template <typename T>
-void coarsest_nodes(st_handle* h, bool adj, T* u, const T* f, const T* u0, T* work) {
-  Level& lv = h->levels[0];
-  zero<T>(h, u, lv.ndof);
-  for (int i = 0; i < lv.N; ++i) {
-    const int s = adj ? lv.N - 1 - i : i;
-    residual<T>(h, lv, adj, f, u, u0, work, s, 1);
-    block_solve<T>(h, lv, adj, work, u, s, 1);
-  }
-}
-
 void coarsest_fp64(st_handle* h, bool adj, double* u, const double* f, const double* u0) {
-  if (modal(h)) coarsest_modal<double>(h, adj, u, f, u0);
-  else coarsest_nodes<double>(h, adj, u, f, u0, h->levels[0].v64.r);
+  coarsest_modal<double>(h, adj, u, f, u0);
 }
 
 // Mixed precision: the coarsest level is solved in FP64.
@@ -1251,8 +1248,7 @@ void coarsest_mixed(st_handle* h, bool adj, float* u, const float* f) {
     Prof pr(h, ST_K_VECTOR, 12.0 * (double)n, 0.0);
     stmg::k_cast_up<<<blocks_for(n), kThreads, 0, h->stream>>>(h->coarse64_f, f, n);
   }
-  if (modal(h)) coarsest_modal<double>(h, adj, h->coarse64_u, h->coarse64_f, (const double*)nullptr);
-  else coarsest_nodes<double>(h, adj, h->coarse64_u, h->coarse64_f, (const double*)nullptr, h->coarse64_r);
+  coarsest_modal<double>(h, adj, h->coarse64_u, h->coarse64_f, (const double*)nullptr);
   Prof pr(h, ST_K_VECTOR, 12.0 * (double)n, 0.0);
   stmg::k_cast_down<<<blocks_for(n), kThreads, 0, h->stream>>>(u, h->coarse64_u, 1.0, n);
 }
@@ -1282,33 +1278,30 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u
     coarsest_solve<T>(h, adj, u, f, u0);
     return;
   }
-  const bool md = modal(h);
-  if (md) {
+  if (!inexact(h)) {
     smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu1, u_zero);
-    mresidual<T>(h, lv, adj, f, u, u0, work);
   } else {
     if (u_zero) zero<T>(h, u, lv.ndof);
-    for (int i = 0; i < h->opt.nu1; ++i) smooth_step_nodes<T>(h, lv, adj, u, f, u0, work);
-    residual<T>(h, lv, adj, f, u, u0, work);
+    for (int i = 0; i < h->opt.nu1; ++i) smooth_step_inexact<T>(h, lv, adj, u, f, u0, work);
   }
+  mresidual<T>(h, lv, adj, f, u, u0, work);
   Level& cl = h->levels[L - 1];
   Vecs<T>& cv = vecs<T>(cl);
-  restrict_to<T>(h, L, md, work, cv.f);
+  restrict_to<T>(h, L, work, cv.f);
   const int reps = (L - 1 == 0) ? 1 : h->opt.gamma;
   for (int g = 0; g < reps; ++g) vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, g == 0);
-  prolong_add<T>(h, L, md, cv.u, u);
-  if (md) {
+  prolong_add<T>(h, L, cv.u, u);
+  if (!inexact(h)) {
     smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false);
   } else {
-    for (int i = 0; i < h->opt.nu2; ++i) smooth_step_nodes<T>(h, lv, adj, u, f, u0, work);
+    for (int i = 0; i < h->opt.nu2; ++i) smooth_step_inexact<T>(h, lv, adj, u, f, u0, work);
   }
 }
 
 // Residual of the finest level in the basis of the cycle.
 template <typename T>
 void cycle_residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r) {
-  if (modal(h)) mresidual<T>(h, lv, adj, f, u, u0, r);
-  else residual<T>(h, lv, adj, f, u, u0, r);
+  mresidual<T>(h, lv, adj, f, u, u0, r);
 }
 
 template <typename T>
@@ -1343,8 +1336,8 @@ void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
   stmg::k_axpy_up<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(u, v.u, s, lv.ndof);
 }
 
-// Inputs of a finest-level cycle in its basis: with the exact block inverse f
-// and u0 are transformed into handle buffers (u in place); otherwise as given.
+// Inputs of a finest-level cycle in its basis: f and u0 are transformed into
+// handle buffers (u in place).
 struct CycleInputs {
   const double* f;
   const double* u0;
@@ -1364,7 +1357,6 @@ void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
 
 CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, double* u, bool u_given) {
   Level& lv = finest(h);
-  if (!modal(h)) return {f, u0};
   copy<double>(h, lv.v64.f, f, lv.ndof);
   boundary_dst(h, lv.v64.f, (int64_t)lv.N * h->q, false);
   const double* u0m = nullptr;
@@ -1379,7 +1371,7 @@ CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, d
 
 void leave_cycle_basis(st_handle* h, double* u) {
   Level& lv = finest(h);
-  if (modal(h)) boundary_dst(h, u, (int64_t)lv.N * h->q, true);
+  boundary_dst(h, u, (int64_t)lv.N * h->q, true);
 }
 
 // The cycles of a solve with the inputs already in the basis of the cycle.
@@ -1437,8 +1429,8 @@ const void* device_view(const void* p) {
   return at.devicePointer;
 }
 
-// Solve with host buffers.  With the exact block inverse and a register
-// sine-transform length, the first transform pass reads f from registered host
+// Solve with host buffers.  With a register sine-transform length, the first
+// transform pass reads f from registered host
 // memory and the last inverse pass writes u to it, so the transfers ride on the
 // transforms instead of separate copies; otherwise plain copies.
 int solve_host_impl(st_handle* h, const double* f, const double* u0, double* u, int flags, int* iters,
@@ -1448,8 +1440,8 @@ int solve_host_impl(st_handle* h, const double* f, const double* u0, double* u, 
   const int64_t slabs = (int64_t)lv.N * h->q;
   const size_t bytes = sizeof(double) * lv.ndof;
   if (!h->u_dev) h->u_dev = dalloc<double>(h, lv.ndof);
-  const bool md = modal(h);
-  const bool in_place = md && lv.n + 1 >= 64 && lv.n + 1 <= 512;
+  const bool md = true;   // every cycle runs in the sine basis
+  const bool in_place = lv.n + 1 >= 64 && lv.n + 1 <= 512;
   const double* fv = in_place ? static_cast<const double*>(device_view(f)) : nullptr;
   double* uv = in_place ? static_cast<double*>(const_cast<void*>(device_view(u))) : nullptr;
   CycleInputs in{lv.v64.f, nullptr};
@@ -1775,17 +1767,13 @@ int st_level_residual(st_handle* h, int L, int adjoint, const double* f, const d
   return guarded(h, [&]() -> int {
     if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
     Level& lv = h->levels[level_index(h, L)];
-    if (modal(h)) {
-      const int64_t slabs = (int64_t)lv.N * h->q;
-      copy<double>(h, lv.v64.f, f, lv.ndof);
-      to_modal<double>(h, lv, lv.v64.f, slabs);
-      copy<double>(h, lv.v64.r, u, lv.ndof);
-      to_modal<double>(h, lv, lv.v64.r, slabs);
-      mresidual<double>(h, lv, adjoint != 0, lv.v64.f, lv.v64.r, (const double*)nullptr, r);
-      from_modal<double>(h, lv, r, slabs);
-    } else {
-      residual<double>(h, lv, adjoint != 0, f, u, (const double*)nullptr, r);
-    }
+    const int64_t slabs = (int64_t)lv.N * h->q;
+    copy<double>(h, lv.v64.f, f, lv.ndof);
+    to_modal<double>(h, lv, lv.v64.f, slabs);
+    copy<double>(h, lv.v64.r, u, lv.ndof);
+    to_modal<double>(h, lv, lv.v64.r, slabs);
+    mresidual<double>(h, lv, adjoint != 0, lv.v64.f, lv.v64.r, (const double*)nullptr, r);
+    from_modal<double>(h, lv, r, slabs);
     after_launch(h);
     return ST_OK;
   });
@@ -1805,17 +1793,17 @@ int st_level_smooth(st_handle* h, int L, int adjoint, int nu, const double* f, d
   return guarded(h, [&]() -> int {
     if (!f || !u || nu < 0) fail(h, ST_EINVAL, "bad argument");
     Level& lv = h->levels[level_index(h, L)];
-    if (modal(h)) {
-      const int64_t slabs = (int64_t)lv.N * h->q;
-      copy<double>(h, lv.v64.f, f, lv.ndof);
-      to_modal<double>(h, lv, lv.v64.f, slabs);
-      to_modal<double>(h, lv, u, slabs);
+    const int64_t slabs = (int64_t)lv.N * h->q;
+    copy<double>(h, lv.v64.f, f, lv.ndof);
+    to_modal<double>(h, lv, lv.v64.f, slabs);
+    to_modal<double>(h, lv, u, slabs);
+    if (!inexact(h)) {
       smooth_modal<double>(h, lv, adjoint != 0, u, lv.v64.f, (const double*)nullptr, lv.v64.r, nu, false);
-      from_modal<double>(h, lv, u, slabs);
     } else {
       for (int i = 0; i < nu; ++i)
-        smooth_step_nodes<double>(h, lv, adjoint != 0, u, f, (const double*)nullptr, lv.v64.r);
+        smooth_step_inexact<double>(h, lv, adjoint != 0, u, lv.v64.f, (const double*)nullptr, lv.v64.r);
     }
+    from_modal<double>(h, lv, u, slabs);
     after_launch(h);
     return ST_OK;
   });
@@ -1824,16 +1812,12 @@ int st_level_smooth(st_handle* h, int L, int adjoint, int nu, const double* f, d
 int st_level_restrict(st_handle* h, int L, const double* r_fine, double* f_coarse) {
   return guarded(h, [&]() -> int {
     if (!r_fine || !f_coarse || level_index(h, L) < 1) fail(h, ST_EINVAL, "bad argument");
-    if (modal(h)) {
-      Level& fine = h->levels[L];
-      Level& coarse = h->levels[L - 1];
-      copy<double>(h, fine.v64.r, r_fine, fine.ndof);
-      to_modal<double>(h, fine, fine.v64.r, (int64_t)fine.N * h->q);
-      restrict_to<double>(h, L, true, fine.v64.r, f_coarse);
-      from_modal<double>(h, coarse, f_coarse, (int64_t)coarse.N * h->q);
-    } else {
-      restrict_to<double>(h, L, false, r_fine, f_coarse);
-    }
+    Level& fine = h->levels[L];
+    Level& coarse = h->levels[L - 1];
+    copy<double>(h, fine.v64.r, r_fine, fine.ndof);
+    to_modal<double>(h, fine, fine.v64.r, (int64_t)fine.N * h->q);
+    restrict_to<double>(h, L, fine.v64.r, f_coarse);
+    from_modal<double>(h, coarse, f_coarse, (int64_t)coarse.N * h->q);
     after_launch(h);
     return ST_OK;
   });
@@ -1842,17 +1826,13 @@ int st_level_restrict(st_handle* h, int L, const double* r_fine, double* f_coars
 int st_level_prolong(st_handle* h, int L, const double* e_coarse, double* u_fine) {
   return guarded(h, [&]() -> int {
     if (!e_coarse || !u_fine || level_index(h, L) < 1) fail(h, ST_EINVAL, "bad argument");
-    if (modal(h)) {
-      Level& fine = h->levels[L];
-      Level& coarse = h->levels[L - 1];
-      copy<double>(h, coarse.v64.r, e_coarse, coarse.ndof);
-      to_modal<double>(h, coarse, coarse.v64.r, (int64_t)coarse.N * h->q);
-      to_modal<double>(h, fine, u_fine, (int64_t)fine.N * h->q);
-      prolong_add<double>(h, L, true, coarse.v64.r, u_fine);
-      from_modal<double>(h, fine, u_fine, (int64_t)fine.N * h->q);
-    } else {
-      prolong_add<double>(h, L, false, e_coarse, u_fine);
-    }
+    Level& fine = h->levels[L];
+    Level& coarse = h->levels[L - 1];
+    copy<double>(h, coarse.v64.r, e_coarse, coarse.ndof);
+    to_modal<double>(h, coarse, coarse.v64.r, (int64_t)coarse.N * h->q);
+    to_modal<double>(h, fine, u_fine, (int64_t)fine.N * h->q);
+    prolong_add<double>(h, L, coarse.v64.r, u_fine);
+    from_modal<double>(h, fine, u_fine, (int64_t)fine.N * h->q);
     after_launch(h);
     return ST_OK;
   });
@@ -1862,15 +1842,11 @@ int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u) {
   return guarded(h, [&]() -> int {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
     Level& c = h->levels[0];
-    if (modal(h)) {
-      const int64_t slabs = (int64_t)c.N * h->q;
-      copy<double>(h, c.v64.f, f, c.ndof);
-      to_modal<double>(h, c, c.v64.f, slabs);
-      coarsest_modal<double>(h, adjoint != 0, u, c.v64.f, (const double*)nullptr);
-      from_modal<double>(h, c, u, slabs);
-    } else {
-      coarsest_nodes<double>(h, adjoint != 0, u, f, (const double*)nullptr, c.v64.r);
-    }
+    const int64_t slabs = (int64_t)c.N * h->q;
+    copy<double>(h, c.v64.f, f, c.ndof);
+    to_modal<double>(h, c, c.v64.f, slabs);
+    coarsest_modal<double>(h, adjoint != 0, u, c.v64.f, (const double*)nullptr);
+    from_modal<double>(h, c, u, slabs);
     after_launch(h);
     return ST_OK;
   });

@@ -1018,142 +1018,11 @@ __global__ void k_ic_gradient_dyn(const T* __restrict__ lam, T* __restrict__ g, 
   });
 }
 
-// ---------------------------------------------------------------------------
-// Inexact block inverse (Remark on the V-cycle approximation in space): one
-// spatial multigrid V-cycle per time step for A = K_tau (x) M_h + M_tau (x) K_h,
-// damped point-block Jacobi with the node block D^x = (M_h)_jj K + (K_h)_jj tau Mh
-// (the same q x q block at every node of a uniform grid, passed inverted).
-// k_space_op, one thread per (node, time step), no time coupling:
-//   MODE 0: xo = x + w Dinv (b - A x)      (Jacobi sweep)
-//   MODE 1: xo = b - A x                   (spatial residual)
-//   MODE 2: xo = w Dinv b                  (first sweep from x = 0; w = 1 and
-//                                           Dinv = A^{-1} solve a one-node level)
-// Adjoint: A^T (K_tau^T) and Dinv of the transposed block.
-// ---------------------------------------------------------------------------
+// q x q matrix passed by value (the inverted node block of the inexact block inverse).
 template <typename T, int Q>
 struct SmallMat {
   T a[Q * Q];
 };
-
-template <typename T, int D, int Q, bool ADJ, int MODE>
-__global__ void k_space_op(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ xo, int n,
-                           int nsteps, T tau, T h, T hinv, T w, SmallMat<T, Q> Dinv, TimeCoef<T, Q> tc) {
-  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (j >= Nx || s >= nsteps) return;
-  T r[Q];
-#pragma unroll
-  for (int k = 0; k < Q; ++k) r[k] = b[((int64_t)s * Q + k) * Nx + j];
-  if (MODE != 2) {
-    int ix, iy, iz;
-    node_coords(j, n, D, ix, iy, iz);
-    Stencil<T, D> S(h, hinv);
-    T mu[Q], ku[Q];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) {
-      const T* xl = x + ((int64_t)s * Q + l) * Nx;
-      apply_mk<T, D>(S, n, ix, iy, iz, [&](int64_t q) { return xl[q]; }, mu[l], ku[l]);
-    }
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      T ax = tau * tc.Mh[k] * ku[k];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) ax += (ADJ ? tc.K[l * Q + k] : tc.K[k * Q + l]) * mu[l];
-      r[k] -= ax;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
-    if (MODE == 1) {
-      xo[idx] = r[k];
-    } else {
-      T acc = T(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) acc += Dinv.a[k * Q + l] * r[l];
-      xo[idx] = (MODE == 0 ? x[idx] : T(0)) + w * acc;
-    }
-  }
-}
-
-// Space-only restriction (R_x (x) I): coarse[s, l, J] = sum of (1/2)[1 2 1]^{(x)d}
-// over fine nodes 2J .. 2J+2 (0-based), for every time step and time dof.
-template <typename T, int D, int Q>
-__global__ void k_restrict_space(const T* __restrict__ fine, T* __restrict__ coarse, int nf, int nc,
-                                 int nsteps) {
-  const int64_t Nxc = (D == 1) ? nc : (D == 2) ? (int64_t)nc * nc : (int64_t)nc * nc * nc;
-  const int64_t Nxf = (D == 1) ? nf : (D == 2) ? (int64_t)nf * nf : (int64_t)nf * nf * nf;
-  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (J >= Nxc || s >= nsteps) return;
-  int jx, jy, jz;
-  node_coords(J, nc, D, jx, jy, jz);
-  const T w[3] = {T(0.5), T(1), T(0.5)};
-#pragma unroll
-  for (int l = 0; l < Q; ++l) {
-    const T* fl = fine + ((int64_t)s * Q + l) * Nxf;
-    T acc = T(0);
-    if (D == 1) {
-#pragma unroll
-      for (int ox = 0; ox < 3; ++ox) acc += w[ox] * fl[2 * jx + ox];
-    } else if (D == 2) {
-#pragma unroll
-      for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 3; ++ox) acc += w[oy] * w[ox] * fl[(int64_t)(2 * jy + oy) * nf + 2 * jx + ox];
-    } else {
-#pragma unroll
-      for (int oz = 0; oz < 3; ++oz)
-#pragma unroll
-        for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-          for (int ox = 0; ox < 3; ++ox)
-            acc += w[oz] * w[oy] * w[ox] * fl[((int64_t)(2 * jz + oz) * nf + 2 * jy + oy) * nf + 2 * jx + ox];
-    }
-    coarse[((int64_t)s * Q + l) * Nxc + J] = acc;
-  }
-}
-
-// Space-only prolongation and correction: fine += (R_x^T (x) I) coarse.
-template <typename T, int D, int Q>
-__global__ void k_prolong_space(const T* __restrict__ coarse, T* __restrict__ fine, int nf, int nc, int nsteps) {
-  const int64_t Nxc = (D == 1) ? nc : (D == 2) ? (int64_t)nc * nc : (int64_t)nc * nc * nc;
-  const int64_t Nxf = (D == 1) ? nf : (D == 2) ? (int64_t)nf * nf : (int64_t)nf * nf * nf;
-  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (I >= Nxf || s >= nsteps) return;
-  int ix, iy, iz;
-  node_coords(I, nf, D, ix, iy, iz);
-  int cx0, cx1, cy0 = 0, cy1 = 0, cz0 = 0, cz1 = 0;
-  float wx0, wx1, wy0 = 1.f, wy1 = 0.f, wz0 = 1.f, wz1 = 0.f;
-  interp_pair(ix, nc, cx0, cx1, wx0, wx1);
-  if (D >= 2) interp_pair(iy, nc, cy0, cy1, wy0, wy1);
-  if (D >= 3) interp_pair(iz, nc, cz0, cz1, wz0, wz1);
-#pragma unroll
-  for (int l = 0; l < Q; ++l) {
-    const T* cl = coarse + ((int64_t)s * Q + l) * Nxc;
-    T acc;
-    if (D == 1) {
-      acc = T(wx0) * cl[cx0] + T(wx1) * cl[cx1];
-    } else if (D == 2) {
-      const T r0 = T(wx0) * cl[(int64_t)cy0 * nc + cx0] + T(wx1) * cl[(int64_t)cy0 * nc + cx1];
-      const T r1 = T(wx0) * cl[(int64_t)cy1 * nc + cx0] + T(wx1) * cl[(int64_t)cy1 * nc + cx1];
-      acc = T(wy0) * r0 + T(wy1) * r1;
-    } else {
-      T pz[2];
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int64_t zoff = (int64_t)(a ? cz1 : cz0) * nc;
-        const T r0 = T(wx0) * cl[(zoff + cy0) * nc + cx0] + T(wx1) * cl[(zoff + cy0) * nc + cx1];
-        const T r1 = T(wx0) * cl[(zoff + cy1) * nc + cx0] + T(wx1) * cl[(zoff + cy1) * nc + cx1];
-        pz[a] = T(wy0) * r0 + T(wy1) * r1;
-      }
-      acc = T(wz0) * pz[0] + T(wz1) * pz[1];
-    }
-    fine[((int64_t)s * Q + l) * Nxf + I] += acc;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Elementwise helpers.

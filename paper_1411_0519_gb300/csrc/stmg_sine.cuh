@@ -304,6 +304,120 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Inexact block inverse (Remark on the V-cycle approximation in space) in the
+// sine basis: one spatial V-cycle per time step for A = K_tau (x) M_h +
+// M_tau (x) K_h.  The point-block Jacobi block D^x = (M_h)_jj K_tau +
+// (K_h)_jj M_tau is the same at every node, so it commutes with the sine
+// transform, and the spatial operator of every spatial level is A_i per mode:
+// the sweep, the spatial residual and the exact one-node solve are pointwise,
+// and the spatial transfers pair modes as in k_frestrict (without time blocks).
+// k_fspace_op, per (mode, step), amat = A_i of the spatial level (adjoint: A_i^T,
+// with Dinv of the transposed block):
+//   MODE 0: xo = x + w Dinv (b - A_i x)     MODE 1: xo = b - A_i x
+//   MODE 2: xo = w Dinv b  (the first sweep from x = 0; on the one-node level
+//           w = 1 and Dinv = A^{-1} solve exactly)
+// ---------------------------------------------------------------------------
+template <typename T, int Q, int MODE>
+__global__ void __launch_bounds__(256) k_fspace_op(const T* __restrict__ x, const T* __restrict__ b,
+                                                   T* __restrict__ xo, int64_t Nx, int nsteps, T w,
+                                                   SmallMat<T, Q> Dinv, const T* __restrict__ amat) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= Nx || s >= nsteps) return;
+  T r[Q], xv[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    r[k] = b[((int64_t)s * Q + k) * Nx + j];
+    xv[k] = (MODE == 2) ? T(0) : x[((int64_t)s * Q + k) * Nx + j];
+  }
+  if (MODE != 2) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) r[k] -= amat[(int64_t)(k * Q + l) * Nx + j] * xv[l];
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    if (MODE == 1) {
+      xo[idx] = r[k];
+    } else {
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) acc += Dinv.a[k * Q + l] * r[l];
+      xo[idx] = xv[k] + w * acc;
+    }
+  }
+}
+
+// Space-only restriction / prolongation-and-correction in the sine basis (the
+// spatial factor of k_frestrict / k_fprolong, every step and time dof).  The
+// prolongation weights are 2 ra, 2 rb per axis; `pscale` = 2^d is applied once.
+template <typename T, int D, int Q>
+__global__ void k_fspace_restrict(const T* __restrict__ fine, T* __restrict__ coarse, int nf, int nc, int nsteps,
+                                  const T* __restrict__ ra, const T* __restrict__ rb) {
+  const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
+  const int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (J >= Nxc || s >= nsteps) return;
+  constexpr int NT = 1 << D;
+  int c[3] = {0, 0, 0};
+  int64_t rest = J;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    c[a] = (int)(rest % nc);
+    rest /= nc;
+  }
+  int64_t src[NT];
+  T wm[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    int64_t idx = 0, stride = 1;
+    T w = T(1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const bool hi = (t >> a) & 1;
+      idx += stride * (hi ? nf - 1 - c[a] : c[a]);
+      w = (a == 0) ? (hi ? rb[c[a]] : ra[c[a]]) : w * (hi ? rb[c[a]] : ra[c[a]]);
+      stride *= nf;
+    }
+    src[t] = idx;
+    wm[t] = w;
+  }
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const T* fl = fine + ((int64_t)s * Q + l) * Nxf;
+    T acc = wm[0] * fl[src[0]];
+#pragma unroll
+    for (int t = 1; t < NT; ++t) acc += wm[t] * fl[src[t]];
+    coarse[((int64_t)s * Q + l) * Nxc + J] = acc;
+  }
+}
+
+template <typename T, int D, int Q>
+__global__ void k_fspace_prolong(const T* __restrict__ coarse, T* __restrict__ fine, int nf, int nc, int nsteps,
+                                 const T* __restrict__ ra, const T* __restrict__ rb, T pscale) {
+  const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (I >= Nxf || s >= nsteps) return;
+  int64_t rest = I, jc = 0, stride = 1;
+  T w = pscale;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int src;
+    T wa;
+    if (!mode_source<T>((int)(rest % nf), nf, nc, ra, rb, src, wa)) return;   // unpaired mode
+    rest /= nf;
+    jc += stride * src;
+    stride *= nc;
+    w = w * wa;
+  }
+#pragma unroll
+  for (int l = 0; l < Q; ++l) fine[((int64_t)s * Q + l) * Nxf + I] += w * coarse[((int64_t)s * Q + l) * Nxc + jc];
+}
+
 // ===========================================================================
 // Generic time degree (q > 4, up to kQmaxDyn): the same operators with q a
 // runtime value.  The residual uses the structure of the Legendre K_tau,
