@@ -57,7 +57,7 @@ extern "C" {
 
 #define ST_INIT_GIVEN 1  /* st_solve flag: u holds the initial iterate (else u^0 = 0) */
 
-#define ST_SMOOTH_EXACT  0  /* block inverse D^{-1} exact (Section 3.1): sine transforms + line solves */
+#define ST_SMOOTH_EXACT  0  /* block inverse D^{-1} exact (Section 3.1): one q x q inverse per sine mode */
 #define ST_SMOOTH_VCYCLE 1  /* D~^{-1}: one spatial multigrid V-cycle per step (Remark on the V-cycle
                                approximation in space; damped point-block Jacobi, nu_x, omega_x) */
 
@@ -191,8 +191,8 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
  * Kernel classes for st_profile_stop: */
 #define ST_K_RESIDUAL   0   /* residual (forward / transposed) */
 #define ST_K_DST        1   /* batched sine transform along one axis */
-#define ST_K_LINESOLVE  2   /* fused smoothing step: coupling term, block-tridiagonal
-                               line solve per sine mode, damping */
+#define ST_K_LINESOLVE  2   /* fused smoothing step: coupling term, q x q block inverse
+                               per sine mode, damping */
 #define ST_K_RESTRICT   3
 #define ST_K_PROLONG    4
 #define ST_K_NORM       5   /* both reduction stages */

@@ -3,7 +3,9 @@
 //
 // Method: Gander & Neumueller, arXiv:1411.0519.  Section 2 (V-cycle, damped
 // block Jacobi, P = R^T, exact coarsest solve), Section 3 (exact block inverse,
-// transfers), Section 4 (coarsening rule mu_L >= mu*).
+// transfers), Section 4 (coarsening rule mu_L >= mu*).  The cycle runs in the
+// sine basis of every spatial axis (see stmg_sine.cuh): the data are
+// transformed once at the entry of a solve and the solution once at the exit.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -737,7 +739,7 @@ void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T
   STMG_DISPATCH(launch_residual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
-// Residual in the mixed basis (exact block inverse), steps [s0, s0 + ns).
+// Residual in the sine basis, steps [s0, s0 + ns).
 template <typename T>
 void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0 = 0,
                int ns = -1) {
@@ -751,8 +753,8 @@ void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const 
   else STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
-// Fused damped block-Jacobi step with the exact block inverse in the mixed
-// basis (k_msmooth): out = (1 - w) u + w A^{-1}(f - B u_prev) (damp), or
+// Fused damped block-Jacobi step with the exact block inverse in the sine
+// basis (k_fsmooth): out = (1 - w) u + w A^{-1}(f - B u_prev) (damp), or
 // out = A^{-1}(f - B u_prev) (no damping), steps [s0, s0 + ns); u may be null.
 template <typename T>
 void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out, int s0 = 0,
@@ -1202,7 +1204,7 @@ void smooth_step_inexact(st_handle* h, Level& lv, bool adj, T* u, const T* f, co
 }
 
 // nu damped block-Jacobi steps (eq. chap4_smoother) with the exact block
-// inverse in the mixed basis, u <- (1 - w) u + w A^{-1} (f - B u_prev) (the
+// inverse in the sine basis, u <- (1 - w) u + w A^{-1} (f - B u_prev) (the
 // block inverse of the block row removes A u, so only the rank-one time
 // coupling is applied).  Each step reads one buffer and writes the other
 // (Jacobi in time); the first destination is chosen so that the last step
@@ -1269,7 +1271,7 @@ void coarsest_solve<float>(st_handle* h, bool adj, float* u, const float* f, con
 // finest level), Section 2: the coarse correction equation is treated by gamma
 // cycles on level L-1 (1: V-cycle, 2: W-cycle; once when L-1 is the coarsest
 // level, whose solve is exact).  With the exact block inverse every vector is
-// in the mixed basis.  u_zero: u holds zero on entry (coarse-grid corrections).
+// in the sine basis.  u_zero: u holds zero on entry (coarse-grid corrections).
 template <typename T>
 void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u_zero) {
   Level& lv = h->levels[L];
