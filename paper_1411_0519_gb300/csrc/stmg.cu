@@ -653,6 +653,7 @@ void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, const T* e
   if (!fine.coarsen_full) {
     stmg::k_prolong<T, D, Q, false><<<grid, kThreads, 0, h->stream>>>(ec, uf, fine.n, coarse.n, fine.N, tc);
   } else {
+    grid.y = coarse.N;   // one thread per (fine mode, coarse step)
     // pair weights of the prolongation are 2 ra, 2 rb per axis: fold 2^D into R^T
     for (int i = 0; i < Q * Q; ++i) {
       tc.R1[i] *= (T)(1 << D);
@@ -774,9 +775,8 @@ void restrict_to(st_handle* h, int L, const T* r, T* fc) {
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   const double ns = fine.coarsen_full ? std::pow(2.0, h->d) : 1.0;
-  // time blocks: q FMA per coarse dof and block, half of them for q > kQfix (R is lower triangular
-  // and the generic-q kernels skip its zeros)
-  const double tq = h->q > kQfix ? 0.5 * (h->q + 1) : h->q;
+  // time blocks: (q + 1) / 2 FMA per coarse dof and block (R is lower triangular; the kernels skip its zeros)
+  const double tq = 0.5 * (h->q + 1);
   Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_restrict_dyn_t, h, fine, coarse, r, fc);
   else STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
@@ -788,7 +788,7 @@ void prolong_add(st_handle* h, int L, const T* ec, T* uf) {
   Level& coarse = h->levels[L - 1];
   const double cn = (double)coarse.ndof, fn_ = (double)fine.ndof;
   const double ns = 1.0;
-  const double tq = h->q > kQfix ? 0.5 * (h->q + 1) : h->q;
+  const double tq = 0.5 * (h->q + 1);
   Prof pr(h, ST_K_PROLONG, sizeof(T) * (cn + 2.0 * fn_), 2.0 * fn_ * (ns + tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_prolong_dyn_t, h, fine, coarse, ec, uf);
   else STMG_DISPATCH(launch_prolong_t, h, fine, coarse, ec, uf);

@@ -244,8 +244,8 @@ __global__ void k_frestrict(const T* __restrict__ r, T* __restrict__ fc, int nf,
   for (int k = 0; k < Q; ++k) {
     T acc = T(0);
 #pragma unroll
-    for (int l = 0; l < Q; ++l) acc += tc.R1[k * Q + l] * acc2[0][l] + tc.R2[k * Q + l] * acc2[1][l];
-    fc[((int64_t)m * Q + k) * Nxc + J] = acc;
+    for (int l = 0; l <= k; ++l) acc += tc.R1[k * Q + l] * acc2[0][l] + tc.R2[k * Q + l] * acc2[1][l];
+    fc[((int64_t)m * Q + k) * Nxc + J] = acc;   // R_s[k][l] = 0 for l > k (Legendre degrees)
   }
 }
 
@@ -253,7 +253,8 @@ __global__ void k_frestrict(const T* __restrict__ r, T* __restrict__ fc, int nf,
 // per axis fine mode i < nc takes 2 ra_i e^_i, fine mode i > nc takes
 // 2 rb_j e^_j (j = nf - 1 - i), mode nc takes nothing; in time R_sl^T.  The
 // host passes the time blocks pre-multiplied by 2^d, so the pair weights are
-// ra, rb themselves.  One thread per fine (mode, step).
+// ra, rb themselves.  One thread per (fine mode, coarse step): both fine steps
+// of the coarse step share the coarse values.
 template <typename T>
 __device__ __forceinline__ bool mode_source(int i, int nf, int nc, const T* __restrict__ ra,
                                             const T* __restrict__ rb, int& src, T& wgt) {
@@ -275,9 +276,8 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
                            const T* __restrict__ ra, const T* __restrict__ rb, TimeCoef<T, Q> tc) {
   const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (I >= Nxf || s >= Nf_steps) return;
-  const int m = s >> 1, sl = s & 1;
+  const int m = blockIdx.y;   // coarse step: fine steps 2m and 2m + 1
+  if (I >= Nxf || 2 * m + 1 >= Nf_steps) return;
   int64_t rest = I, jc = 0, stride = 1;
   T w = T(1);
 #pragma unroll
@@ -293,14 +293,17 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
   T e[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) e[k] = w * ec[((int64_t)m * Q + k) * Nxc + jc];
-  const T* Rb = sl ? tc.R2 : tc.R1;
 #pragma unroll
-  for (int l = 0; l < Q; ++l) {
-    T* dst = uf + ((int64_t)s * Q + l) * Nxf + I;
-    T acc = *dst;
+  for (int sl = 0; sl < 2; ++sl) {
+    const T* Rb = sl ? tc.R2 : tc.R1;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) acc += Rb[k * Q + l] * e[k];
-    *dst = acc;
+    for (int l = 0; l < Q; ++l) {
+      T* dst = uf + ((int64_t)(2 * m + sl) * Q + l) * Nxf + I;
+      T acc = *dst;
+#pragma unroll
+      for (int k = l; k < Q; ++k) acc += Rb[k * Q + l] * e[k];   // R_s[k][l] = 0 for l > k
+      *dst = acc;
+    }
   }
 }
 
