@@ -173,11 +173,15 @@ def traffic_table():
         return json.load(fh)
 
 
-def roofline(solver, prof, fp32, pk, w):
-    """Dominant kernel class of the timed region, evaluated on the finest level
-    (one launch = one pass over the finest level)."""
+KERNEL_OF_CLASS = {"line_solve": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg / k_dst_cols_reg",
+                   "restrict": "k_frestrict", "prolong": "k_fprolong", "space_mg": "k_fspace_op"}
+
+
+def roofline(solver, prof, fp32, pk, w, exclude=()):
+    """Dominant kernel class of the timed region (classes in `exclude` left out),
+    evaluated on the finest level (one launch = one pass over the finest level)."""
     classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["ms"] > 0}
-    dom = max(classes, key=lambda k: classes[k]["ms"])
+    dom = max((k for k in classes if k not in exclude), key=lambda k: classes[k]["ms"])
     total_ms = sum(c["ms"] for c in classes.values())
     L = solver.num_levels - 1
     v = solver.profile_level(dom, L)
@@ -186,7 +190,6 @@ def roofline(solver, prof, fp32, pk, w):
     sec = v["ms"] / 1e3
     gbs = v["bytes"] / sec / 1e9
     tfl = v["flops"] / sec / 1e12
-    fp32 = fp32 and dom != "dst"   # the change of basis runs in FP64 in both forms
     alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     f_hbm = gbs / pk["hbm_gbs"]
     f_alu = tfl / alu_peak
@@ -201,7 +204,8 @@ def roofline(solver, prof, fp32, pk, w):
     ndof = w["N"] * (w["p_t"] + 1) * w["n"] ** w["d"]
     key = "%s/%s/d%d_n%d_q%d" % (dom, "fp32" if fp32 else "fp64", w["d"], w["n"], w["p_t"] + 1)
     t = traffic_table().get(key)
-    name = t["kernel"] if t else None
+    name = t["kernel"] if t else KERNEL_OF_CLASS.get(dom, dom) + ("_dyn" if w["p_t"] > 3 and dom in
+                                                                   ("line_solve", "residual") else "")
     traffic = t["bytes_per_dof"] * ndof if t else None
     rf.update({"kernel": name or dom, "level": "finest", "launches": v["launches"],
                "avg_launch_ms": round(v["ms"] / launches, 4), "share_of_class_total": round(
@@ -209,6 +213,21 @@ def roofline(solver, prof, fp32, pk, w):
                "alg_bytes_per_launch": v["bytes"] / launches, "alg_flops_per_launch": v["flops"] / launches,
                "traffic": traffic})
     return rf
+
+
+def transform_note(prof, w):
+    """The boundary sine transforms of the mixed form: double-float arithmetic on
+    the FP32 pipe (FP64-equivalent algorithmic flops; latency-bound, see
+    profiles/dst_heat2d_255_n256.md), reported beside the FP32 cycle kernels."""
+    classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["ms"] > 0}
+    if "dst" not in classes:
+        return None
+    v = classes["dst"]
+    total = sum(c["ms"] for c in classes.values())
+    return {"kernel": "k_dst_rows_reg / k_dst_cols_reg <dfloat>", "arithmetic": "double-float on the FP32 pipe",
+            "share_of_kernel_time": round(v["ms"] / total, 3), "launches": v["launches"],
+            "fp64_equivalent_tflops": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4),
+            "bound": "latency (issue 39-42 %, 15.7 warps per SM; ncu)"}
 
 
 def breakdown(prof):
@@ -286,7 +305,7 @@ def run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_ov
                 "dtype": "f32 V-cycle in f64 refinement", "data": "synthetic",
                 "config": {"workload": args.workload, "d": d, "n": n, "p_t": p, "N": N, "T": T, "rtol": rtol,
                            "precision": "mixed", "inner_cycles": args.inner_cycles},
-                "iters": itm[-1], "relres": rrm, "roofline": roofline(smx, profm, True, pk, w),
+                "iters": itm[-1], "relres": rrm, "roofline": roofline(smx, profm, True, pk, w, exclude=("dst",)), "transform": transform_note(profm, w),
                 "kernels": breakdown(profm),
                 "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_")),
                 "clocks": ck}
@@ -365,7 +384,9 @@ def main():
         mixed = {"value": world * smx.ndof / (msm / args.steps / 1e3), "unit": "DoF/s",
                  "ms_per_step": msm / args.steps, "iters": itm[-1], "relres": rrm,
                  "inner_cycles": args.inner_cycles, "dtype": "f32 V-cycle in f64 refinement",
-                 "roofline": roofline(smx, profm, True, pk, w), "kernels": breakdown(profm),
+                 "roofline": roofline(smx, profm, True, pk, w, exclude=("dst",)),
+                 "transform": transform_note(profm, w),
+                 "kernels": breakdown(profm),
                  "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_"))}
         smx.close()
 
