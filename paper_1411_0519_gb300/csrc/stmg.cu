@@ -678,23 +678,33 @@ void launch_space_op_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, int
   dim3 grid(blocks_for(sl.Nx), lv.N);
   const T ww = (T)w;
   const T* am = sl.amat[adj ? 1 : 0];
-  if (mode == 0)
-    stmg::k_fspace_op<T, Q, 0><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
-  else if (mode == 1)
-    stmg::k_fspace_op<T, Q, 1><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
-  else
-    stmg::k_fspace_op<T, Q, 2><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
+  if (mode != 2) fail(h, ST_EINVAL, "spatial operator mode");   // sweeps and residuals are fused (k_fspace_pre/post)
+  stmg::k_fspace_op<T, Q, 2><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
 }
 
 template <typename T, int D, int Q>
-void launch_space_transfer_t(st_handle* h, const Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse,
-                             bool restrict_, const T* in, T* out) {
-  if (restrict_)
-    stmg::k_fspace_restrict<T, D, Q><<<dim3(blocks_for(coarse.Nx), lv.N), kThreads, 0, h->stream>>>(
-        in, out, fine.n, coarse.n, lv.N, fine.ra, fine.rb);
-  else
-    stmg::k_fspace_prolong<T, D, Q><<<dim3(blocks_for(fine.Nx), lv.N), kThreads, 0, h->stream>>>(
-        in, out, fine.n, coarse.n, lv.N, fine.ra, fine.rb, (T)(1 << D));
+void launch_space_restrict_t(st_handle* h, const Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse,
+                             const T* in, T* out) {
+  stmg::k_fspace_restrict<T, D, Q><<<dim3(blocks_for(coarse.Nx), lv.N), kThreads, 0, h->stream>>>(
+      in, out, fine.n, coarse.n, lv.N, fine.ra, fine.rb);
+}
+
+template <typename T, int D, int Q>
+void launch_space_pre_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, bool adj, const T* b, T* x, T* r,
+                        double w, const double* dinv) {
+  stmg::SmallMat<T, Q> m{};
+  for (int i = 0; i < Q * Q; ++i) m.a[i] = (T)dinv[i];
+  stmg::k_fspace_pre<T, Q><<<dim3(blocks_for(sl.Nx), lv.N), kThreads, 0, h->stream>>>(
+      b, x, r, sl.Nx, lv.N, (T)w, m, sl.amat[adj ? 1 : 0], h->opt.nu_x);
+}
+
+template <typename T, int D, int Q>
+void launch_space_post_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, const SpaceLvl<T>& cl, bool adj,
+                         const T* b, T* x, const T* xc, double w, const double* dinv) {
+  stmg::SmallMat<T, Q> m{};
+  for (int i = 0; i < Q * Q; ++i) m.a[i] = (T)dinv[i];
+  stmg::k_fspace_post<T, D, Q><<<dim3(blocks_for(sl.Nx), lv.N), kThreads, 0, h->stream>>>(
+      b, x, xc, sl.n, cl.n, lv.N, (T)w, m, sl.amat[adj ? 1 : 0], sl.ra, sl.rb, (T)(1 << D), h->opt.nu_x);
 }
 
 #define STMG_DISPATCH(FN, ...)                                                   \
@@ -1134,11 +1144,11 @@ void space_op(st_handle* h, Level& lv, const SpaceLvl<T>& sl, int mode, bool adj
 }
 
 template <typename T>
-void space_transfer(st_handle* h, Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse, bool restrict_,
-                    const T* in, T* out) {
-  Prof pr(h, ST_K_SPACEMG, sizeof(T) * h->q * (double)lv.N * (restrict_ ? fine.Nx + coarse.Nx : 2.0 * fine.Nx + coarse.Nx),
-          2.0 * h->q * (double)lv.N * (restrict_ ? coarse.Nx * std::pow(2.0, h->d) : fine.Nx), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_space_transfer_t, h, lv, fine, coarse, restrict_, in, out);
+void space_restrict(st_handle* h, Level& lv, const SpaceLvl<T>& fine, const SpaceLvl<T>& coarse, const T* in,
+                    T* out) {
+  Prof pr(h, ST_K_SPACEMG, sizeof(T) * h->q * (double)lv.N * (fine.Nx + coarse.Nx),
+          2.0 * h->q * (double)lv.N * coarse.Nx * std::pow(2.0, h->d), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_restrict_t, h, lv, fine, coarse, in, out);
 }
 
 // x = D~^{-1} b on every time step of level lv: one spatial V-cycle from x = 0
@@ -1153,26 +1163,21 @@ void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) 
     space_op<T>(h, lv, sl, 2, adj, nullptr, b, x, 1.0, dinv);
     return;
   }
-  // 2 nu_x sweeps alternate between two buffers; starting in the scratch buffer
-  // makes the last one land in x
+  // pre-smoothing (nu_x sweeps from 0) and the spatial residual in one pass per
+  // (mode, step); restriction; coarse cycle; correction and post-smoothing in one pass
   const double w = h->opt.omega_x;
-  T* cur = sl.t;
-  T* oth = x;
-  space_op<T>(h, lv, sl, 2, adj, nullptr, b, cur, w, dinv);
-  for (int i = 1; i < h->opt.nu_x; ++i) {
-    space_op<T>(h, lv, sl, 0, adj, cur, b, oth, w, dinv);
-    std::swap(cur, oth);
+  const double nodes = (double)lv.N * sl.Nx, Q = h->q, nu = h->opt.nu_x;
+  {
+    Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * nodes * 3.0, 2.0 * nodes * (nu * (2.0 * Q * Q + Q) + Q * Q), 1,
+            level_of(h, lv));
+    STMG_DISPATCH(launch_space_pre_t, h, lv, sl, adj, b, x, sl.t, w, dinv);
   }
-  space_op<T>(h, lv, sl, 1, adj, cur, b, oth, 0.0, dinv);       // residual b - A x into oth
   const SpaceLvl<T>& cl = sp[ell + 1];
-  space_transfer<T>(h, lv, sl, cl, true, oth, cl.b);
+  space_restrict<T>(h, lv, sl, cl, sl.t, cl.b);
   space_vcycle<T>(h, lv, ell + 1, adj, cl.x, cl.b);
-  space_transfer<T>(h, lv, sl, cl, false, cl.x, cur);
-  for (int i = 0; i < h->opt.nu_x; ++i) {
-    space_op<T>(h, lv, sl, 0, adj, cur, b, oth, w, dinv);
-    std::swap(cur, oth);
-  }
-  if (cur != x) copy<T>(h, x, cur, (int64_t)lv.N * h->q * sl.Nx);   // not reached: 2 nu_x sweeps
+  Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * (double)lv.N * (3.0 * sl.Nx + cl.Nx),
+          2.0 * nodes * (nu * (2.0 * Q * Q + Q) + Q), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_post_t, h, lv, sl, cl, adj, b, x, cl.x, w, dinv);
 }
 
 bool inexact(const st_handle* h) { return h->opt.smoother == ST_SMOOTH_VCYCLE; }

@@ -318,8 +318,8 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
 // k_fspace_op, per (mode, step), amat = A_i of the spatial level (adjoint: A_i^T,
 // with Dinv of the transposed block):
 //   MODE 0: xo = x + w Dinv (b - A_i x)     MODE 1: xo = b - A_i x
-//   MODE 2: xo = w Dinv b  (the first sweep from x = 0; on the one-node level
-//           w = 1 and Dinv = A^{-1} solve exactly)
+//   MODE 2: xo = w Dinv b  (on the one-node level w = 1 and Dinv = A^{-1} solve
+//           exactly; the other levels use the fused k_fspace_pre / k_fspace_post)
 // ---------------------------------------------------------------------------
 template <typename T, int Q, int MODE>
 __global__ void __launch_bounds__(256) k_fspace_op(const T* __restrict__ x, const T* __restrict__ b,
@@ -354,9 +354,107 @@ __global__ void __launch_bounds__(256) k_fspace_op(const T* __restrict__ x, cons
   }
 }
 
-// Space-only restriction / prolongation-and-correction in the sine basis (the
-// spatial factor of k_frestrict / k_fprolong, every step and time dof).  The
-// prolongation weights are 2 ra, 2 rb per axis; `pscale` = 2^d is applied once.
+// The pointwise parts of one spatial V-cycle level, fused (the sweeps act per
+// (mode, step) in registers):
+//   k_fspace_pre:  x = nu_x damped Jacobi sweeps from x = 0 (the first one is
+//                  w Dinv b), r = b - A_i x;  writes x and r.
+//   k_fspace_post: x += (P e_c)^ (mode pairs, weights pscale ra / rb per axis),
+//                  then nu_x sweeps;  updates x.
+// The same iterates as the sweeps done one launch at a time.
+template <typename T, int Q>
+__device__ __forceinline__ void fspace_sweeps(T (&xv)[Q], const T (&bv)[Q], const T (&A)[Q * Q],
+                                              const SmallMat<T, Q>& Dinv, T w, int nu) {
+  for (int it = 0; it < nu; ++it) {
+    T r[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = bv[k];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) acc -= A[k * Q + l] * xv[l];
+      r[k] = acc;
+    }
+    T xn[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) acc += Dinv.a[k * Q + l] * r[l];
+      xn[k] = xv[k] + w * acc;
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) xv[k] = xn[k];
+  }
+}
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) k_fspace_pre(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                                                    int64_t Nx, int nsteps, T w, SmallMat<T, Q> Dinv,
+                                                    const T* __restrict__ amat, int nu) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= Nx || s >= nsteps) return;
+  T A[Q * Q], bv[Q], xv[Q];
+#pragma unroll
+  for (int e = 0; e < Q * Q; ++e) A[e] = amat[(int64_t)e * Nx + j];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    bv[k] = b[((int64_t)s * Q + k) * Nx + j];
+    xv[k] = T(0);
+  }
+  fspace_sweeps<T, Q>(xv, bv, A, Dinv, w, nu);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    T acc = bv[k];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc -= A[k * Q + l] * xv[l];
+    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+    x[idx] = xv[k];
+    r[idx] = acc;
+  }
+}
+
+template <typename T, int D, int Q>
+__global__ void __launch_bounds__(256) k_fspace_post(const T* __restrict__ b, T* __restrict__ x,
+                                                     const T* __restrict__ xc, int nf, int nc, int nsteps, T w,
+                                                     SmallMat<T, Q> Dinv, const T* __restrict__ amat,
+                                                     const T* __restrict__ ra, const T* __restrict__ rb, T pscale,
+                                                     int nu) {
+  const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (I >= Nxf || s >= nsteps) return;
+  T A[Q * Q], bv[Q], xv[Q];
+#pragma unroll
+  for (int e = 0; e < Q * Q; ++e) A[e] = amat[(int64_t)e * Nxf + I];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    bv[k] = b[((int64_t)s * Q + k) * Nxf + I];
+    xv[k] = x[((int64_t)s * Q + k) * Nxf + I];
+  }
+  int64_t rest = I, jc = 0, stride = 1;
+  T wgt = pscale;
+  bool has = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int src = 0;
+    T wa = T(0);
+    if (!mode_source<T>((int)(rest % nf), nf, nc, ra, rb, src, wa)) has = false;
+    rest /= nf;
+    jc += stride * src;
+    stride *= nc;
+    wgt = wgt * wa;
+  }
+  if (has) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) xv[k] += wgt * xc[((int64_t)s * Q + k) * Nxc + jc];
+  }
+  fspace_sweeps<T, Q>(xv, bv, A, Dinv, w, nu);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) x[((int64_t)s * Q + k) * Nxf + I] = xv[k];
+}
+
+// Space-only restriction in the sine basis (the spatial factor of k_frestrict,
+// every step and time dof).
 template <typename T, int D, int Q>
 __global__ void k_fspace_restrict(const T* __restrict__ fine, T* __restrict__ coarse, int nf, int nc, int nsteps,
                                   const T* __restrict__ ra, const T* __restrict__ rb) {
@@ -398,28 +496,6 @@ __global__ void k_fspace_restrict(const T* __restrict__ fine, T* __restrict__ co
   }
 }
 
-template <typename T, int D, int Q>
-__global__ void k_fspace_prolong(const T* __restrict__ coarse, T* __restrict__ fine, int nf, int nc, int nsteps,
-                                 const T* __restrict__ ra, const T* __restrict__ rb, T pscale) {
-  const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
-  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (I >= Nxf || s >= nsteps) return;
-  int64_t rest = I, jc = 0, stride = 1;
-  T w = pscale;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    int src;
-    T wa;
-    if (!mode_source<T>((int)(rest % nf), nf, nc, ra, rb, src, wa)) return;   // unpaired mode
-    rest /= nf;
-    jc += stride * src;
-    stride *= nc;
-    w = w * wa;
-  }
-#pragma unroll
-  for (int l = 0; l < Q; ++l) fine[((int64_t)s * Q + l) * Nxf + I] += w * coarse[((int64_t)s * Q + l) * Nxc + jc];
-}
 
 // ===========================================================================
 // Generic time degree (q > 4, up to kQmaxDyn): the same operators with q a
