@@ -146,6 +146,7 @@ struct Tables {
   T* amat[2] = {nullptr, nullptr};   // A_i = lamM_i K_tau + lamK_i M_tau
   T* ainv[2] = {nullptr, nullptr};   // A_i^{-1}
   T* ainvw[2] = {nullptr, nullptr};  // w A_i^{-1} (damped smoother)
+  T* ws[2] = {nullptr, nullptr};     // coupling vectors lamM_i w A_i^{-1} sigma of the damped step on wf (q per mode)
   T* lamM = nullptr;                 // lamM_i (coupling B_i = -lamM_i N_tau)
   T* lamKt = nullptr;                // lamK_i tau (generic-q residual)
   T* ra = nullptr;     // full-coarsening pair weights to level L-1: (1 + c_k) / 2
@@ -157,6 +158,7 @@ struct Vecs {
   T* u = nullptr;
   T* f = nullptr;
   T* r = nullptr;
+  T* wf = nullptr;   // w A_i^{-1} f of the level's current right-hand side (damped steps on wf)
 };
 
 // One spatial level of the inexact block inverse: iterate x, right-hand side
@@ -396,6 +398,22 @@ void make_tables(st_handle* h, Level& lv, Tables<T>& tb) {
     mode_blocks(h->tm, h->d, n, lv.h, lv.tau, adj != 0, am, ai, lm, lk);
     std::vector<double> aw(ai);
     for (double& x : aw) x *= h->opt.omega;
+    {   // ws_k = lamM sum_l (w A^{-1})[k,l] sigma_l, sigma_l = (-1)^l (forward) or 1 (adjoint)
+      const int q = h->q;
+      const int64_t Nx = lv.Nx;
+      std::vector<double> wsv((size_t)q * Nx);
+      for (int64_t j = 0; j < Nx; ++j)
+        for (int k = 0; k < q; ++k) {
+          double acc = 0.0;
+          for (int l = 0; l < q; ++l) {
+            const double w = aw[(size_t)(k * q + l) * Nx + j];
+            acc += (adj == 0 && (l & 1)) ? -w : w;
+          }
+          wsv[(size_t)k * Nx + j] = lm[j] * acc;
+        }
+      tb.ws[adj] = dalloc<T>(h, wsv.size());
+      upload(h, tb.ws[adj], wsv);
+    }
     if (h->q <= kQfix) {   // the generic-q residual uses the structure of K_tau instead
       tb.amat[adj] = dalloc<T>(h, am.size());
       upload(h, tb.amat[adj], am);
@@ -530,26 +548,35 @@ void launch_mresidual_t(st_handle* h, Level& lv, bool adj, const T* f, const T* 
   }
 }
 
+// fmode: stmg::kFromF, kMakeWf (also writes wf) or kUseWf (f holds wf); the
+// last two only with damp.
 template <typename T, int D, int Q>
-void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out,
-                      int s0, int ns) {
+void launch_msmooth_t(st_handle* h, Level& lv, bool adj, bool damp, int fmode, const T* f, const T* u, const T* u0,
+                      T* out, T* wf, int s0, int ns) {
   Tables<T>& tb = tables<T>(lv);
   const int a = adj ? 1 : 0;
   const T* ai = damp ? tb.ainvw[a] : tb.ainv[a];
+  const T* ws = tb.ws[a];
   const T wc = (T)(1.0 - h->opt.omega);
   constexpr int TS = stmg::kStepsPerThread;
   const int nblk = (ns + TS - 1) / TS;
   dim3 grid(blocks_for(lv.Nx), 1);
   for (int c = 0; c < nblk; c += 65535) {
     grid.y = std::min(65535, nblk - c);
-#define STMG_FSMOOTH(ADJ, DAMP)                                                                                  \
-  stmg::k_fsmooth<T, Q, ADJ, DAMP><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c * TS, s0 + ns, \
-                                                                     wc, ai, tb.lamM)
+#define STMG_FSMOOTH(ADJ, DAMP, FM)                                                                         \
+  stmg::k_fsmooth<T, Q, ADJ, DAMP, FM><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c * TS, \
+                                                                         s0 + ns, wc, ai, tb.lamM, wf, ws)
+#define STMG_FSMOOTH_DIR(ADJ)                                           \
+  if (!damp) STMG_FSMOOTH(ADJ, false, stmg::kFromF);                    \
+  else if (fmode == stmg::kMakeWf) STMG_FSMOOTH(ADJ, true, stmg::kMakeWf); \
+  else if (fmode == stmg::kUseWf) STMG_FSMOOTH(ADJ, true, stmg::kUseWf);   \
+  else STMG_FSMOOTH(ADJ, true, stmg::kFromF)
     if (adj) {
-      if (damp) STMG_FSMOOTH(true, true); else STMG_FSMOOTH(true, false);
+      STMG_FSMOOTH_DIR(true);
     } else {
-      if (damp) STMG_FSMOOTH(false, true); else STMG_FSMOOTH(false, false);
+      STMG_FSMOOTH_DIR(false);
     }
+#undef STMG_FSMOOTH_DIR
 #undef STMG_FSMOOTH
   }
 }
@@ -578,25 +605,32 @@ void launch_mresidual_dyn(st_handle* h, Level& lv, bool adj, const T* f, const T
 }
 
 template <typename T>
-void launch_msmooth_dyn(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out,
-                        int s0, int ns) {
+void launch_msmooth_dyn(st_handle* h, Level& lv, bool adj, bool damp, int fmode, const T* f, const T* u, const T* u0,
+                        T* out, T* wf, int s0, int ns) {
   Tables<T>& tb = tables<T>(lv);
   const int a = adj ? 1 : 0;
   const T* ai = damp ? tb.ainvw[a] : tb.ainv[a];
+  const T* ws = tb.ws[a];
   const T wc = (T)(1.0 - h->opt.omega);
   constexpr int TS = stmg::kStepsPerThread;
   const int nblk = (ns + TS - 1) / TS;
   dim3 grid(blocks_for(lv.Nx), 1);
   for (int c = 0; c < nblk; c += 65535) {
     grid.y = std::min(65535, nblk - c);
-#define STMG_FSMOOTH_DYN(ADJ, DAMP)                                                                        \
-  stmg::k_fsmooth_dyn<T, ADJ, DAMP><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c * TS, \
-                                                                      s0 + ns, h->q, wc, ai, tb.lamM)
+#define STMG_FSMOOTH_DYN(ADJ, DAMP, FM)                                                                          \
+  stmg::k_fsmooth_dyn<T, ADJ, DAMP, FM><<<grid, kThreads, 0, h->stream>>>(f, u, u0, out, lv.Nx, lv.N, s0 + c * TS, \
+                                                                          s0 + ns, h->q, wc, ai, tb.lamM, wf, ws)
+#define STMG_FSMOOTH_DYN_DIR(ADJ)                                           \
+  if (!damp) STMG_FSMOOTH_DYN(ADJ, false, stmg::kFromF);                    \
+  else if (fmode == stmg::kMakeWf) STMG_FSMOOTH_DYN(ADJ, true, stmg::kMakeWf); \
+  else if (fmode == stmg::kUseWf) STMG_FSMOOTH_DYN(ADJ, true, stmg::kUseWf);   \
+  else STMG_FSMOOTH_DYN(ADJ, true, stmg::kFromF)
     if (adj) {
-      if (damp) STMG_FSMOOTH_DYN(true, true); else STMG_FSMOOTH_DYN(true, false);
+      STMG_FSMOOTH_DYN_DIR(true);
     } else {
-      if (damp) STMG_FSMOOTH_DYN(false, true); else STMG_FSMOOTH_DYN(false, false);
+      STMG_FSMOOTH_DYN_DIR(false);
     }
+#undef STMG_FSMOOTH_DYN_DIR
 #undef STMG_FSMOOTH_DYN
   }
 }
@@ -767,16 +801,22 @@ void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const 
 // Fused damped block-Jacobi step with the exact block inverse in the sine
 // basis (k_fsmooth): out = (1 - w) u + w A^{-1}(f - B u_prev) (damp), or
 // out = A^{-1}(f - B u_prev) (no damping), steps [s0, s0 + ns); u may be null.
+// fmode (damped steps): kMakeWf also stores w A^{-1} f in wf; kUseWf takes
+// f = wf of an earlier kMakeWf on the same right-hand side.
 template <typename T>
 void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* u, const T* u0, T* out, int s0 = 0,
-             int ns = -1) {
+             int ns = -1, int fmode = stmg::kFromF, T* wf = nullptr) {
   if (ns < 0) ns = lv.N;
+  if (!damp) fmode = stmg::kFromF;
   const double Q = h->q, nodes = (double)ns * lv.Nx;
-  const double passes = 2.0 + ((damp && u) ? 1.0 : 0.0);   // read f (and u), write out
-  // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i^{-1} g Q^2 FMA, damping Q FMA
-  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * (2.0 * Q * Q + 4.0 * Q), 1, level_of(h, lv));
-  if (h->q > kQfix) launch_msmooth_dyn<T>(h, lv, adj, damp, f, u, u0, out, s0, ns);
-  else STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, f, u, u0, out, s0, ns);
+  // read f or wf (and u), write out (and wf)
+  const double passes = 2.0 + ((damp && u) ? 1.0 : 0.0) + (fmode == stmg::kMakeWf ? 1.0 : 0.0);
+  // per (mode, step): trace Q - 1 adds, coupling Q FMA (lamM or ws), A_i^{-1} Q^2 FMA
+  // (not with kUseWf), damping Q FMA
+  const double flops = (fmode == stmg::kUseWf ? 0.0 : 2.0 * Q * Q) + 4.0 * Q + (fmode == stmg::kFromF ? Q : 0.0);
+  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * flops, 1, level_of(h, lv));
+  if (h->q > kQfix) launch_msmooth_dyn<T>(h, lv, adj, damp, fmode, f, u, u0, out, wf, s0, ns);
+  else STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, fmode, f, u, u0, out, wf, s0, ns);
 }
 
 template <typename T>
@@ -1214,17 +1254,31 @@ void smooth_step_inexact(st_handle* h, Level& lv, bool adj, T* u, const T* f, co
 // coupling is applied).  Each step reads one buffer and writes the other
 // (Jacobi in time); the first destination is chosen so that the last step
 // lands in u.  u_zero: u holds zero on entry and is not read.
+// Where the level has a wf buffer the steps run on wf = w A^{-1} f: wf_ready
+// says that it already holds that product for this f and direction (an
+// earlier smoothing of the same right-hand side); otherwise the first step
+// forms it.
 template <typename T>
-void smooth_modal(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* tmp, int nu, bool u_zero) {
+void smooth_modal(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* tmp, int nu, bool u_zero,
+                  bool wf_ready = false) {
   if (nu <= 0) {
     if (u_zero) zero<T>(h, u, lv.ndof);
     return;
   }
+  T* wf = vecs<T>(lv).wf;
   T* buf[2] = {u, tmp};
   int cur = u_zero ? -1 : 0;
   int dst = u_zero ? ((nu & 1) ? 0 : 1) : 1;
   for (int i = 0; i < nu; ++i) {
-    msmooth<T>(h, lv, adj, true, f, cur < 0 ? (const T*)nullptr : buf[cur], u0, buf[dst]);
+    const T* ui = cur < 0 ? (const T*)nullptr : buf[cur];
+    if (wf == nullptr) {
+      msmooth<T>(h, lv, adj, true, f, ui, u0, buf[dst]);
+    } else if (!wf_ready) {
+      msmooth<T>(h, lv, adj, true, f, ui, u0, buf[dst], 0, -1, stmg::kMakeWf, wf);
+      wf_ready = true;
+    } else {
+      msmooth<T>(h, lv, adj, true, (const T*)wf, ui, u0, buf[dst], 0, -1, stmg::kUseWf);
+    }
     cur = dst;
     dst = 1 - dst;
   }
@@ -1277,8 +1331,10 @@ void coarsest_solve<float>(st_handle* h, bool adj, float* u, const float* f, con
 // cycles on level L-1 (1: V-cycle, 2: W-cycle; once when L-1 is the coarsest
 // level, whose solve is exact).  With the exact block inverse every vector is
 // in the sine basis.  u_zero: u holds zero on entry (coarse-grid corrections).
+// wf_ready: the level's wf already holds w A^{-1} f for this f and direction
+// (a cycle repeated on the same right-hand side).
 template <typename T>
-void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u_zero) {
+void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u_zero, bool wf_ready = false) {
   Level& lv = h->levels[L];
   T* work = vecs<T>(lv).r;
   if (L == 0) {
@@ -1286,7 +1342,7 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u
     return;
   }
   if (!inexact(h)) {
-    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu1, u_zero);
+    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu1, u_zero, wf_ready);
   } else {
     if (u_zero) zero<T>(h, u, lv.ndof);
     for (int i = 0; i < h->opt.nu1; ++i) smooth_step_inexact<T>(h, lv, adj, u, f, u0, work);
@@ -1296,10 +1352,10 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u
   Vecs<T>& cv = vecs<T>(cl);
   restrict_to<T>(h, L, work, cv.f);
   const int reps = (L - 1 == 0) ? 1 : h->opt.gamma;
-  for (int g = 0; g < reps; ++g) vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, g == 0);
+  for (int g = 0; g < reps; ++g) vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, g == 0, g > 0);
   prolong_add<T>(h, L, cv.u, u);
   if (!inexact(h)) {
-    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false);
+    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false, wf_ready || h->opt.nu1 > 0);
   } else {
     for (int i = 0; i < h->opt.nu2; ++i) smooth_step_inexact<T>(h, lv, adj, u, f, u0, work);
   }
@@ -1338,7 +1394,7 @@ void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
         v.f, r, 1.0 / s, lv.ndof);
   }
   for (int c = 0; c < std::max(1, h->opt.inner_cycles); ++c)
-    vcycle<float>(h, L, adj, v.u, v.f, (const float*)nullptr, c == 0);
+    vcycle<float>(h, L, adj, v.u, v.f, (const float*)nullptr, c == 0, c > 0);
   Prof pr(h, ST_K_VECTOR, 20.0 * (double)lv.ndof, 2.0 * (double)lv.ndof);
   stmg::k_axpy_up<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(u, v.u, s, lv.ndof);
 }
@@ -1400,7 +1456,7 @@ int solve_core(st_handle* h, bool adj, const CycleInputs& in, double* u, bool gi
     if (h->opt.precision == ST_MIXED) {
       mixed_step(h, adj, u, r, rn);
     } else {
-      vcycle<double>(h, L, adj, u, in.f, in.u0, false);
+      vcycle<double>(h, L, adj, u, in.f, in.u0, false, it > 0);   // in.f is fixed for the whole solve
     }
     ++it;
     cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
@@ -1601,12 +1657,16 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       if (L < nlev - 1) l.v64.u = dalloc<double>(h, l.ndof);
       l.v64.f = dalloc<double>(h, l.ndof);   // finest level: the transformed right-hand side
       l.v64.r = dalloc<double>(h, l.ndof);
+      // damped steps on wf = w A^{-1} f (FP64 cycles are bound by the FP64 pipe; FP32 ones by HBM, where
+      // the extra wf store would cost, except at generic q with its q^2 inverse per step)
+      if (!inexact(h) && !mixed && L > 0) l.v64.wf = dalloc<double>(h, l.ndof);
       make_tables<double>(h, l, l.t64);
       if (h->opt.smoother == ST_SMOOTH_VCYCLE) make_space<double>(h, l, l.sp64);
       if (mixed) {
         l.v32.u = dalloc<float>(h, l.ndof);
         l.v32.f = dalloc<float>(h, l.ndof);
         l.v32.r = dalloc<float>(h, l.ndof);
+        if (!inexact(h) && h->q > kQfix && L > 0) l.v32.wf = dalloc<float>(h, l.ndof);
         make_tables<float>(h, l, l.t32);
         if (h->opt.smoother == ST_SMOOTH_VCYCLE) make_space<float>(h, l, l.sp32);
       }

@@ -137,21 +137,43 @@ __global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, cons
 // launch).  u == nullptr is a zero iterate.  With DAMP, u and out must differ
 // (steps read their neighbour's old value).  Steps [s0, s1); one thread per
 // (mode, kStepsPerThread consecutive steps).
+//
+// The right-hand side is the same in every damped step of a level visit, so
+// w A_i^{-1} f can be formed once: with the coupling vector
+//   ws_i = lamM_i w A_i^{-1} sigma  (sigma_k = (-1)^k; adjoint: w A_i^{-T} 1)
+// a damped step is out = wf + ws_i t + wc u, t the coupling trace — 2 FMA per
+// unknown instead of q + 2.  FMODE selects the form:
+//   kFromF  out from f as above (any DAMP);
+//   kMakeWf (DAMP) forms wf = w A_i^{-1} f, stores it in `wf` and takes the step;
+//   kUseWf  (DAMP) `f` holds wf from an earlier kMakeWf on the same f.
 // ---------------------------------------------------------------------------
-template <typename T, int Q, bool ADJ, bool DAMP>
+enum { kFromF = 0, kMakeWf = 1, kUseWf = 2 };
+
+template <typename T, int Q, bool ADJ, bool DAMP, int FMODE = kFromF>
 __global__ void __launch_bounds__(256) k_fsmooth(const T* __restrict__ f, typename PtrSel<const T, DAMP>::type u,
                                                  const T* __restrict__ u0, typename PtrSel<T, DAMP>::type out,
                                                  int64_t Nx, int N, int s0, int s1, T wc, const T* __restrict__ ainv,
-                                                 const T* __restrict__ lamM) {
+                                                 const T* __restrict__ lamM, T* __restrict__ wf,
+                                                 const T* __restrict__ ws) {
+  static_assert(FMODE == kFromF || DAMP, "the tabulated right-hand side serves the damped step");
   constexpr int TS = kStepsPerThread;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * TS;
   if (j >= Nx || sb >= s1) return;
   const int se = min(sb + TS, s1) - 1;
-  T W[Q * Q];
+  T W[FMODE == kUseWf ? 1 : Q * Q];
+  if (FMODE != kUseWf) {
 #pragma unroll
-  for (int e = 0; e < Q * Q; ++e) W[e] = ainv[(int64_t)e * Nx + j];
-  const T lam = lamM[j];
+    for (int e = 0; e < Q * Q; ++e) W[e] = ainv[(int64_t)e * Nx + j];
+  }
+  T wsv[FMODE == kFromF ? 1 : Q];
+  T lam = T(0);
+  if (FMODE == kFromF) {
+    lam = lamM[j];
+  } else {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) wsv[k] = ws[(int64_t)k * Nx + j];
+  }
   T t = entry_trace<T, Q, ADJ>(u, u0, Nx, N, sb, se, j);
 #pragma unroll
   for (int i = 0; i < TS; ++i) {
@@ -160,16 +182,25 @@ __global__ void __launch_bounds__(256) k_fsmooth(const T* __restrict__ f, typena
     T g[Q], uv[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      g[k] = f[((int64_t)s * Q + k) * Nx + j] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+      const T fk = f[((int64_t)s * Q + k) * Nx + j];
+      g[k] = (FMODE == kFromF) ? fk + ((!ADJ && (k & 1)) ? -lam : lam) * t : fk;
       uv[k] = (u != nullptr) ? u[((int64_t)s * Q + k) * Nx + j] : T(0);
     }
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      T x = W[k * Q] * g[0];
+      const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+      T x;
+      if (FMODE == kUseWf) {
+        x = g[k];
+      } else {
+        x = W[k * Q] * g[0];
 #pragma unroll
-      for (int l = 1; l < Q; ++l) x += W[k * Q + l] * g[l];
+        for (int l = 1; l < Q; ++l) x += W[k * Q + l] * g[l];
+      }
+      if (FMODE == kMakeWf) wf[idx] = x;
+      if (FMODE != kFromF) x += wsv[k] * t;
       if (DAMP && u != nullptr) x += wc * uv[k];
-      out[((int64_t)s * Q + k) * Nx + j] = x;
+      out[idx] = x;
     }
     t = (u != nullptr) ? reg_trace<T, Q, ADJ>(uv) : T(0);
   }
@@ -574,29 +605,44 @@ __global__ void __launch_bounds__(256) k_fresidual_dyn(const T* __restrict__ f, 
   }
 }
 
-template <typename T, bool ADJ, bool DAMP>
+// FMODE as for k_fsmooth: with the tabulated wf = w A_i^{-1} f (kUseWf) a damped
+// step costs O(q) per (mode, step) instead of q^2.
+template <typename T, bool ADJ, bool DAMP, int FMODE = kFromF>
 __global__ void __launch_bounds__(256) k_fsmooth_dyn(const T* __restrict__ f, typename PtrSel<const T, DAMP>::type u,
                                                      const T* __restrict__ u0, typename PtrSel<T, DAMP>::type out,
                                                      int64_t Nx, int N, int s0, int s1, int q, T wc,
-                                                     const T* __restrict__ ainv, const T* __restrict__ lamM) {
+                                                     const T* __restrict__ ainv, const T* __restrict__ lamM,
+                                                     T* __restrict__ wf, const T* __restrict__ ws) {
+  static_assert(FMODE == kFromF || DAMP, "the tabulated right-hand side serves the damped step");
   constexpr int TS = kStepsPerThread;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * TS;
   if (j >= Nx || sb >= s1) return;
   const int se = min(sb + TS, s1) - 1;
-  const T lam = lamM[j];
+  const T lam = (FMODE == kFromF) ? lamM[j] : T(0);
   T t = entry_trace_dyn<T, ADJ>(u, u0, Nx, N, q, sb, se, j);
-  T g[kQmaxDyn];
+  T g[FMODE == kUseWf ? 1 : kQmaxDyn];
   for (int i = 0; i < TS; ++i) {
     const int s = ADJ ? se - i : sb + i;
     if (ADJ ? s < sb : s > se) break;
-    for (int k = 0; k < q; ++k) g[k] = f[((int64_t)s * q + k) * Nx + j] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+    if (FMODE != kUseWf)
+      for (int k = 0; k < q; ++k) {
+        const T fk = f[((int64_t)s * q + k) * Nx + j];
+        g[k] = (FMODE == kFromF) ? fk + ((!ADJ && (k & 1)) ? -lam : lam) * t : fk;
+      }
     T plain = T(0), alt = T(0);
     for (int k = 0; k < q; ++k) {
-      const T* wk = ainv + (int64_t)(k * q) * Nx + j;
-      T x = T(0);
-      for (int l = 0; l < q; ++l) x += wk[(int64_t)l * Nx] * g[l];
       const int64_t idx = ((int64_t)s * q + k) * Nx + j;
+      T x;
+      if (FMODE == kUseWf) {
+        x = f[idx];
+      } else {
+        const T* wk = ainv + (int64_t)(k * q) * Nx + j;
+        x = T(0);
+        for (int l = 0; l < q; ++l) x += wk[(int64_t)l * Nx] * g[l];
+      }
+      if (FMODE == kMakeWf) wf[idx] = x;
+      if (FMODE != kFromF) x += ws[(int64_t)k * Nx + j] * t;
       if (u != nullptr) {
         const T uk = u[idx];
         plain += uk;

@@ -245,3 +245,41 @@ def test_single_level_and_tiny_grids(d, n, p, N, cs):
         assert rel_err(to_np(lam), lo) < 1e-10
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("nu1,nu2,omega,gamma,adjoint", [
+    (0, 2, 0.5, 1, False),
+    (1, 0, 0.5, 1, False),
+    (3, 1, 1.0, 1, True),
+    (0, 1, 0.5, 2, False),
+    (2, 0, 0.7, 2, True),
+])
+@pytest.mark.parametrize("shape", [(2, 15, 1, 16, 1.0), (1, 15, 5, 8, 0.5)], ids=["d2-q2", "d1-q6"])
+def test_smoothing_counts_and_damping(shape, nu1, nu2, omega, gamma, adjoint):
+    """Damped steps run on the tabulated w A^{-1} f, formed by the first step of a
+    level visit and reused by the later ones (the other half of the smoothing,
+    the second visit of a W-cycle, the next cycle of a solve): pre- or
+    post-smoothing alone, an odd count, omega = 1, the transposed problem, and
+    the generic-q kernels (q = 6) — one cycle and a solve against the oracle."""
+    require_gpu()
+    from paper_1411_0519_gb300 import stmg
+    d, n, p, N, T = shape
+    H = multigrid.Hierarchy(d, n, p, N, T)
+    s = stmg.Solver(d, n, p, N, T, nu1=nu1, nu2=nu2, omega=omega, gamma=gamma, rtol=1e-10, maxit=200)
+    try:
+        disc = H.finest.disc
+        u, f = rand(disc.shape(), 81), rand(disc.shape(), 82)
+        if not adjoint:
+            ug = to_gpu(u)
+            s.vcycle(ug, to_gpu(f))
+            ref = multigrid.vcycle(H, 0, u, f, nu1, nu2, omega, gamma=gamma)
+            assert rel_err(to_np(ug), ref) < 1e-10
+            uw, it, rr = s.solve(to_gpu(f))
+        else:
+            uw, _, it, rr = s.adjoint_solve(to_gpu(f))
+        uo, ito, _ = multigrid.solve(H, f, rtol=1e-10, maxit=200, nu1=nu1, nu2=nu2, omega=omega,
+                                     adjoint=adjoint, gamma=gamma)
+        assert abs(it - ito) <= 1, (it, ito)
+        assert rr <= 1e-10 and rel_err(to_np(uw), uo) < 1e-10
+    finally:
+        s.close()
