@@ -124,10 +124,10 @@ int st_residual(st_handle* h, const double* f, const double* u0_ic, const double
 /* One V-cycle (gamma = 1, Section 2) on L u = f + IC for the finest level, in
  * place on u.  With ST_MIXED this is one refinement step: FP64 residual,
  * inner_cycles FP32 V-cycles on the scaled residual, FP64 update.
- * With ST_SMOOTH_EXACT the cycle runs in the basis that diagonalises the
- * spatial matrices along the first dim-1 axes (sine transform, Section 3.1):
- * f, u0_ic and u are transformed on entry and u is transformed back; the
- * iterates are the same as on nodes up to rounding. */
+ * The cycle runs in the basis that diagonalises the spatial matrices along
+ * every axis (sine transform, Section 3.1): f, u0_ic and u are transformed on
+ * entry and u is transformed back; the iterates are the same as on nodes up to
+ * rounding. */
 int st_vcycle(st_handle* h, double* u, const double* f, const double* u0_ic);
 
 /* Solve L u = f + IC to ||r|| <= rtol ||r_0|| by repeated V-cycles (Section 2).
@@ -189,13 +189,15 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
 
 /* ---- kernel timing (CUDA events on the handle's stream) ----
  * Kernel classes for st_profile_stop: */
-#define ST_K_RESIDUAL   0   /* residual (forward / transposed) */
+#define ST_K_RESIDUAL   0   /* residual (forward / transposed); for q <= 4 the finest-level
+                               residual of the stopping test with its norm in one pass */
 #define ST_K_DST        1   /* batched sine transform along one axis */
 #define ST_K_LINESOLVE  2   /* fused smoothing step: coupling term, q x q block inverse
-                               per sine mode, damping */
+                               per sine mode, damping; in FP32 cycles also the first
+                               post-smoothing step with the coarse-grid correction */
 #define ST_K_RESTRICT   3
 #define ST_K_PROLONG    4
-#define ST_K_NORM       5   /* both reduction stages */
+#define ST_K_NORM       5   /* both reduction stages of a separate norm */
 #define ST_K_VECTOR     6   /* axpy, casts, copies, memsets */
 #define ST_K_RHS        7   /* separate smoother right-hand side (no longer launched:
                                fused into ST_K_LINESOLVE; the value is kept) */

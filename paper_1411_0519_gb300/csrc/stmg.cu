@@ -202,6 +202,7 @@ struct st_handle {
   std::vector<void*> allocs;
   size_t bytes = 0;
   double* partial = nullptr;   // norm partial sums
+  int64_t npartial = 0;
   double* dnorm = nullptr;     // device result of a norm
   double* hnorm = nullptr;     // pinned host copy
   double* coarse64_u = nullptr;  // mixed precision: FP64 copies for the coarsest solve
@@ -698,6 +699,37 @@ void launch_prolong_t(st_handle* h, Level& fine, const Level& coarse, const T* e
   }
 }
 
+// Coarse-grid correction and the first damped step after it in one pass
+// (k_fprolong_smooth; full coarsening, q <= kQfix): out = step(u + P ec).
+template <typename T, int D, int Q>
+void launch_prolong_smooth_t(st_handle* h, Level& fine, const Level& coarse, bool adj, int fmode, const T* ec,
+                             const T* f, const T* u, const T* u0, T* out) {
+  auto tc = to_coef<T, Q>(h->tm);
+  for (int i = 0; i < Q * Q; ++i) {   // pair weights of the prolongation: 2 ra, 2 rb per axis
+    tc.R1[i] *= (T)(1 << D);
+    tc.R2[i] *= (T)(1 << D);
+  }
+  Tables<T>& tb = tables<T>(fine);
+  const int a = adj ? 1 : 0;
+  const T wc = (T)(1.0 - h->opt.omega);
+  constexpr int TS = stmg::kStepsPerThread;
+  const int nblk = (fine.N + TS - 1) / TS;
+  dim3 grid(blocks_for(fine.Nx), 1);
+  for (int c = 0; c < nblk; c += 65535) {
+    grid.y = std::min(65535, nblk - c);
+#define STMG_FPS(ADJ, FM)                                                                                        \
+  stmg::k_fprolong_smooth<T, D, Q, ADJ, FM><<<grid, kThreads, 0, h->stream>>>(                                   \
+      ec, f, u, u0, out, fine.n, coarse.n, fine.N, c * TS, fine.N, wc, tb.ainvw[a], tb.lamM, tb.ws[a], tb.ra, tb.rb, \
+      tc)
+    if (adj) {
+      if (fmode == stmg::kUseWf) STMG_FPS(true, stmg::kUseWf); else STMG_FPS(true, stmg::kFromF);
+    } else {
+      if (fmode == stmg::kUseWf) STMG_FPS(false, stmg::kUseWf); else STMG_FPS(false, stmg::kFromF);
+    }
+#undef STMG_FPS
+  }
+}
+
 template <typename T, int D, int Q>
 void launch_ic_grad_t(st_handle* h, const Level& lv, const T* lam, T* g) {
   auto tc = to_coef<T, Q>(h->tm);
@@ -791,9 +823,10 @@ void mresidual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const 
   if (ns < 0) ns = lv.N;
   const double Q = h->q, nodes = (double)ns * lv.Nx;
   // per (mode, step): trace Q - 1 adds and lamM (1), coupling Q, A_i u Q^2 FMA (q > kQfix: the
-  // structured K_tau product, 12 flops per time dof); bytes: read u, f, write r (+ u0)
-  Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)),
-          nodes * (h->q > kQfix ? 12.0 * Q : 2.0 * Q * Q + 2.0 * Q), 1, level_of(h, lv));
+  // structured K_tau product, 12 flops per time dof); bytes: read u, f, write r (+ u0).  u == nullptr
+  // is a zero iterate: r = f plus the initial-value coupling.
+  Prof pr(h, ST_K_RESIDUAL, sizeof(T) * ((u ? 3.0 : 2.0) * nodes * Q + (u0 ? (double)lv.Nx : 0.0)),
+          u ? nodes * (h->q > kQfix ? 12.0 * Q : 2.0 * Q * Q + 2.0 * Q) : 0.0, 1, level_of(h, lv));
   if (h->q > kQfix) launch_mresidual_dyn<T>(h, lv, adj, f, u, u0, r, s0, ns);
   else STMG_DISPATCH(launch_mresidual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
@@ -830,6 +863,24 @@ void restrict_to(st_handle* h, int L, const T* r, T* fc) {
   Prof pr(h, ST_K_RESTRICT, sizeof(T) * (cn + fn_), 2.0 * cn * (2.0 * ns + 2.0 * tq), 1, L);
   if (h->q > kQfix) STMG_DISPATCH_D(launch_restrict_dyn_t, h, fine, coarse, r, fc);
   else STMG_DISPATCH(launch_restrict_t, h, fine, coarse, r, fc);
+}
+
+// The coarse-grid correction of level L fused into its first post-smoothing
+// step: out = damped step of (u + P ec), u itself unchanged.  fmode: kFromF
+// (f is the right-hand side) or kUseWf (f holds a ready wf).
+template <typename T>
+void prolong_smooth(st_handle* h, int L, bool adj, int fmode, const T* ec, const T* f, const T* u, const T* u0,
+                    T* out) {
+  Level& fine = h->levels[L];
+  Level& coarse = h->levels[L - 1];
+  const double Q = h->q, nodes = (double)fine.N * fine.Nx, fn_ = (double)fine.ndof;
+  const double tq = 0.5 * (h->q + 1);
+  // bytes: read f or wf, u and the coarse correction, write out; flops: the correction
+  // (2 (1 + tq) per fine unknown, as k_fprolong) and the damped step (as k_fsmooth)
+  const double step_flops = (fmode == stmg::kUseWf ? 0.0 : 2.0 * Q * Q) + 4.0 * Q + (fmode == stmg::kFromF ? Q : 0.0);
+  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * (3.0 * fn_ + (double)coarse.ndof),
+          2.0 * fn_ * (1.0 + tq) + nodes * step_flops, 1, L);
+  STMG_DISPATCH(launch_prolong_smooth_t, h, fine, coarse, adj, fmode, ec, f, u, u0, out);
 }
 
 template <typename T>
@@ -1258,17 +1309,19 @@ void smooth_step_inexact(st_handle* h, Level& lv, bool adj, T* u, const T* f, co
 // says that it already holds that product for this f and direction (an
 // earlier smoothing of the same right-hand side); otherwise the first step
 // forms it.
+// in_tmp: the current iterate is in tmp (after a fused first step), not in u.
 template <typename T>
 void smooth_modal(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* tmp, int nu, bool u_zero,
-                  bool wf_ready = false) {
+                  bool wf_ready = false, bool in_tmp = false) {
   if (nu <= 0) {
     if (u_zero) zero<T>(h, u, lv.ndof);
+    if (in_tmp) copy<T>(h, u, tmp, lv.ndof);
     return;
   }
   T* wf = vecs<T>(lv).wf;
   T* buf[2] = {u, tmp};
-  int cur = u_zero ? -1 : 0;
-  int dst = u_zero ? ((nu & 1) ? 0 : 1) : 1;
+  int cur = u_zero ? -1 : (in_tmp ? 1 : 0);
+  int dst = u_zero ? ((nu & 1) ? 0 : 1) : 1 - cur;
   for (int i = 0; i < nu; ++i) {
     const T* ui = cur < 0 ? (const T*)nullptr : buf[cur];
     if (wf == nullptr) {
@@ -1353,10 +1406,23 @@ void vcycle(st_handle* h, int L, bool adj, T* u, const T* f, const T* u0, bool u
   restrict_to<T>(h, L, work, cv.f);
   const int reps = (L - 1 == 0) ? 1 : h->opt.gamma;
   for (int g = 0; g < reps; ++g) vcycle<T>(h, L - 1, adj, cv.u, cv.f, (const T*)nullptr, g == 0, g > 0);
-  prolong_add<T>(h, L, cv.u, u);
-  if (!inexact(h)) {
-    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false, wf_ready || h->opt.nu1 > 0);
+  const bool post_ready = wf_ready || h->opt.nu1 > 0;   // wf holds w A^{-1} f (where the level has wf)
+  T* wf = vecs<T>(lv).wf;
+  // the correction fused into the first post-smoothing step (FP32 cycles, which are HBM-bound: the
+  // fused pass saves reading and writing u; the FP64 pipe-bound cycles gain nothing and recompute the
+  // correction of the neighbouring step): full coarsening, q <= kQfix, an even number of post-steps
+  // (the last one lands in u) and a step that reads f or a ready wf
+  const bool fuse = sizeof(T) == 4 && !inexact(h) && lv.coarsen_full && h->q <= kQfix && h->opt.nu2 >= 2 &&
+                    h->opt.nu2 % 2 == 0 && (wf == nullptr || post_ready);
+  if (fuse) {
+    const int fm = wf ? stmg::kUseWf : stmg::kFromF;
+    prolong_smooth<T>(h, L, adj, fm, cv.u, wf ? (const T*)wf : f, u, u0, work);
+    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2 - 1, false, true, true);
+  } else if (!inexact(h)) {
+    prolong_add<T>(h, L, cv.u, u);
+    smooth_modal<T>(h, lv, adj, u, f, u0, work, h->opt.nu2, false, post_ready);
   } else {
+    prolong_add<T>(h, L, cv.u, u);
     for (int i = 0; i < h->opt.nu2; ++i) smooth_step_inexact<T>(h, lv, adj, u, f, u0, work);
   }
 }
@@ -1381,14 +1447,65 @@ double norm2(st_handle* h, const T* x, int64_t n) {
 
 Level& finest(st_handle* h) { return h->levels.back(); }
 
+template <typename T, int D, int Q>
+void launch_residual_norm_t(st_handle* h, Level& lv, bool adj, const double* f, const double* u, const double* u0,
+                            float* r32) {
+  static_assert(sizeof(T) == 8, "the residual with norm is the FP64 outer residual");
+  Tables<double>& tb = lv.t64;
+  constexpr int TS = stmg::kStepsPerThread;
+  const int nblk = (lv.N + TS - 1) / TS;
+  dim3 grid(blocks_for(lv.Nx), 1);
+  for (int c = 0; c < nblk; c += 65535) {
+    grid.y = std::min(65535, nblk - c);
+    const int64_t pbase = (int64_t)c * grid.x;
+#define STMG_RN(ADJ, S32)                                                                                  \
+  stmg::k_fresidual_norm<Q, ADJ, S32><<<grid, kThreads, 0, h->stream>>>(f, u, u0, r32, lv.Nx, lv.N, c * TS, lv.N, \
+                                                                        tb.amat[adj ? 1 : 0], tb.lamM, h->partial, \
+                                                                        pbase)
+    if (adj) {
+      if (r32) STMG_RN(true, true); else STMG_RN(true, false);
+    } else {
+      if (r32) STMG_RN(false, true); else STMG_RN(false, false);
+    }
+#undef STMG_RN
+  }
+}
+
+// ||f - L u|| on the finest level (u == nullptr: zero iterate) in one pass with
+// the residual (k_fresidual_norm; q <= kQfix), storing the residual rounded to
+// FP32 in r32 when given; larger q: residual into the work vector, then norm2.
+double residual_norm(st_handle* h, bool adj, const double* f, const double* u, const double* u0, float* r32) {
+  Level& lv = finest(h);
+  if (h->q > kQfix) {
+    if (r32) fail(h, ST_EINVAL, "internal: FP32 residual output needs q <= 4");
+    cycle_residual<double>(h, lv, adj, f, u, u0, lv.v64.r);
+    return norm2<double>(h, lv.v64.r, lv.ndof);
+  }
+  {
+    const double Q = h->q, nodes = (double)lv.N * lv.Nx;
+    using T = double;
+    Prof pr(h, ST_K_RESIDUAL,
+            8.0 * ((u ? 2.0 : 1.0) * nodes * Q + (u0 ? (double)lv.Nx : 0.0)) + (r32 ? 4.0 * nodes * Q : 0.0),
+            (u ? nodes * (2.0 * Q * Q + 2.0 * Q) : 0.0) + 2.0 * nodes * Q, 1, level_of(h, lv));
+    STMG_DISPATCH(launch_residual_norm_t, h, lv, adj, f, u, u0, r32);
+    const int64_t np = (int64_t)blocks_for(lv.Nx) * ((lv.N + stmg::kStepsPerThread - 1) / stmg::kStepsPerThread);
+    stmg::k_sum_final<<<1, 1024, 0, h->stream>>>(h->partial, (int)np, h->dnorm);
+  }
+  check(h, cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm copy");
+  check(h, cudaStreamSynchronize(h->stream), "norm sync");
+  return std::sqrt(*h->hnorm);
+}
+
 // One FP64 refinement step of the mixed-precision form: given the FP64 residual
 // r (norm s), solve L e = r / s approximately with FP32 V-cycles and update
 // u += s e in FP64 (all in the basis of the cycle).
+// r == nullptr: the FP32 right-hand side is already in the finest FP32 f
+// (the unscaled residual from residual_norm) and s must be 1.
 void mixed_step(st_handle* h, bool adj, double* u, const double* r, double s) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
   Vecs<float>& v = lv.v32;
-  {
+  if (r != nullptr) {
     Prof pr(h, ST_K_VECTOR, 12.0 * (double)lv.ndof, (double)lv.ndof);
     stmg::k_cast_down<<<std::min<int64_t>(blocks_for(lv.ndof), 152 * 16), kThreads, 0, h->stream>>>(
         v.f, r, 1.0 / s, lv.ndof);
@@ -1420,8 +1537,12 @@ void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
 
 CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, double* u, bool u_given) {
   Level& lv = finest(h);
-  copy<double>(h, lv.v64.f, f, lv.ndof);
-  boundary_dst(h, lv.v64.f, (int64_t)lv.N * h->q, false);
+  if (lv.n + 1 >= 64 && lv.n + 1 <= 512) {   // the register transforms read f and write the handle's copy
+    boundary_dst(h, f, lv.v64.f, lv.v64.f, (int64_t)lv.N * h->q, false);
+  } else {
+    copy<double>(h, lv.v64.f, f, lv.ndof);
+    boundary_dst(h, lv.v64.f, (int64_t)lv.N * h->q, false);
+  }
   const double* u0m = nullptr;
   if (u0) {
     copy<double>(h, h->u0m, u0, lv.Nx);
@@ -1438,32 +1559,51 @@ void leave_cycle_basis(st_handle* h, double* u) {
 }
 
 // The cycles of a solve with the inputs already in the basis of the cycle.
+// Without a given iterate the FP64 form starts from u = 0 without storing it:
+// the first residual and the first cycle treat u as zero, and u is only
+// filled with zeros when no cycle runs.
 int solve_core(st_handle* h, bool adj, const CycleInputs& in, double* u, bool given, int* iters, double* relres) {
   Level& lv = finest(h);
   const int L = (int)h->levels.size() - 1;
-  if (!given) zero<double>(h, u, lv.ndof);
-  double* r = (h->opt.precision == ST_MIXED) ? h->r64 : lv.v64.r;
-  cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
+  const bool mixed = h->opt.precision == ST_MIXED;
+  if (!given && mixed) zero<double>(h, u, lv.ndof);   // the refinement adds into u
+  bool u_zero = !given && !mixed;
+  double* r = mixed ? h->r64 : lv.v64.r;
+  // the residual and its norm in one pass; the mixed form also gets the residual
+  // rounded to FP32, the right-hand side of its next FP32 cycles
+  float* r32 = (mixed && h->q <= kQfix) ? lv.v32.f : nullptr;
   // the sine transform is orthogonal up to a constant factor, so the relative
   // residual is the same in both bases
-  const double r0 = norm2<double>(h, r, lv.ndof);
+  const double r0 = residual_norm(h, adj, in.f, u_zero ? (const double*)nullptr : u, in.u0, r32);
   double rn = r0;
+  // the unscaled FP32 residual serves as right-hand side while its entries stay far from the FP32
+  // range limits; otherwise the FP64 residual is recomputed and scaled by its norm
+  auto fp32_rhs_ok = [&](double nrm) {
+    const double rms = nrm / std::sqrt((double)lv.ndof);
+    return r32 != nullptr && rms > 1e-20 && rms < 1e20;
+  };
   int it = 0;
   int status = ST_OK;
   if (!std::isfinite(r0)) status = ST_ENAN;
   while (status == ST_OK && r0 > 0.0 && rn > h->opt.rtol * r0) {
     if (it >= h->opt.maxit) { status = ST_ENOTCONV; h->err = "maxit reached"; break; }
-    if (h->opt.precision == ST_MIXED) {
-      mixed_step(h, adj, u, r, rn);
+    if (mixed) {
+      if (fp32_rhs_ok(rn)) {
+        mixed_step(h, adj, u, nullptr, 1.0);
+      } else {
+        cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
+        mixed_step(h, adj, u, r, rn);
+      }
     } else {
-      vcycle<double>(h, L, adj, u, in.f, in.u0, false, it > 0);   // in.f is fixed for the whole solve
+      vcycle<double>(h, L, adj, u, in.f, in.u0, u_zero, it > 0);   // in.f is fixed for the whole solve
+      u_zero = false;
     }
     ++it;
-    cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
-    rn = norm2<double>(h, r, lv.ndof);
+    rn = residual_norm(h, adj, in.f, u, in.u0, r32);
     if (!std::isfinite(rn)) { status = ST_ENAN; h->err = "residual norm is not finite"; break; }
     if (rn > 1e6 * r0) { status = ST_ENOTCONV; h->err = "residual grew by 1e6"; break; }
   }
+  if (u_zero) zero<double>(h, u, lv.ndof);
   if (iters) *iters = it;
   if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
   return status;
@@ -1596,6 +1736,7 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
   if (!h) return ST_ENOMEM;
   int rc = guarded(h, [&]() -> int {
     if (!mesh || mesh->dim < 1 || mesh->dim > 3 || !is_pow2m1(mesh->n)) fail(h, ST_EINVAL, "mesh: dim 1..3, n = 2^k-1");
+    if (mesh->n > 1023) fail(h, ST_EINVAL, "mesh: n <= 1023");
     if (p_t < 0 || p_t > ST_MAX_PT) fail(h, ST_EINVAL, "p_t out of range");
     if (!is_pow2(N)) fail(h, ST_EINVAL, "N must be a power of 2");
     if (!(T > 0.0) || !std::isfinite(T)) fail(h, ST_EINVAL, "T must be positive");
@@ -1714,7 +1855,12 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
         }
       }
     }
-    h->partial = dalloc<double>(h, kNormBlocks);
+    {   // partial sums: the norm kernel, or one per block of the finest-level residual with norm
+      const int64_t nres = (int64_t)blocks_for(finest(h).Nx) *
+                           ((finest(h).N + stmg::kStepsPerThread - 1) / stmg::kStepsPerThread);
+      h->npartial = std::max<int64_t>(kNormBlocks, nres);
+      h->partial = dalloc<double>(h, h->npartial);
+    }
     h->dnorm = dalloc<double>(h, 1);
     check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");
     check(h, cudaDeviceSynchronize(), "setup sync");

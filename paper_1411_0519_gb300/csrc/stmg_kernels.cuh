@@ -359,17 +359,73 @@ template <>
 __device__ __forceinline__ dfloat shfl_t<dfloat>(dfloat v, int src, int width) {
   return dfloat(__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width));
 }
+// FP64 <-> double-float conversions by integer operations on the IEEE 754
+// encodings: the conversion instructions between FP64 and FP32 issue on the
+// FP64 pipe, which on this part runs at 1/64 of the FP32 rate, and a rare path
+// through them would still be predicated into the common one.
+// split_double: hi = x rounded to 24 significant bits (ties away from zero),
+// lo = x - hi rounded to FP32 (nearest, into the subnormals where needed).  The
+// pair has the FP32 exponent range: |x| below 2^-126 gives zero, |x| from 2^128
+// on gives an infinite hi, NaN stays NaN.
+// float_bits_to_double: exact widening of a normal FP32 value, zero and
+// infinity; subnormal inputs give zero.
+// The two 32-bit words of an FP64 value are read through an opaque move, so
+// that the integer tests on them stay integer instructions (written on the
+// 64-bit pattern, the compiler may turn them into FP64 comparisons).
+__device__ __forceinline__ void double_words(double x, unsigned& hi, unsigned& lo) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
+
+__device__ __forceinline__ dfloat split_double(double x) {
+  unsigned h32, l32;
+  double_words(x, h32, l32);
+  const int E = (int)((h32 >> 20) & 0x7ffu);   // biased exponent
+  const unsigned sign = h32 & 0x80000000u;
+  if (E < 897) return dfloat(__uint_as_float(sign), 0.f);   // zero, or below the FP32 normal range
+  if (E > 1150) {                                             // beyond FP32: infinity, or NaN
+    const bool nan = E == 2047 && (((h32 & 0xfffffu) | l32) != 0u);
+    return dfloat(__uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u)), 0.f);
+  }
+  const unsigned m23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);   // top 23 fraction bits
+  const unsigned rem = l32 & 0x1fffffffu;                       // the 29 bits below them
+  const unsigned up = rem >> 28;                                // round the magnitude up
+  // hi = sign, exponent E - 1023 + 127, fraction m23 (+1: a carry moves into the exponent)
+  const float hi = __uint_as_float((sign | ((unsigned)(E - 896) << 23) | m23) + up);
+  // x - hi = (rem - up 2^29) 2^(E - 1075) on the magnitude: an integer m of at most
+  // 28 bits, converted by FP32 arithmetic: its two 14-bit halves are exact floats
+  // (2^23 + v read as a float, minus 2^23), and one FMA rounds m = hi 2^14 + lo;
+  // the scale 2^(E - 1075) is applied in one step, or (E < 949, where it is not a
+  // normal float) as 2^(E - 1011) and then 2^-64, rounding once into the subnormals
+  const int r = (int)rem - (int)(up << 29);
+  const unsigned m = (unsigned)(r < 0 ? -r : r);
+  const float mh = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 14)), 8388608.f);
+  const float ml = __fsub_rn(__uint_as_float(0x4B000000u | (m & 0x3fffu)), 8388608.f);
+  const bool small = E < 949;
+  const float scale = __uint_as_float((unsigned)(small ? E - 884 : E - 948) << 23);
+  const float post = small ? 5.42101086242752217e-20f : 1.f;   // 2^-64
+  const float lo = __fmul_rn(__fmul_rn(__fmaf_rn(mh, 16384.f, ml), scale), post);
+  return dfloat(hi, ((r < 0) != (sign != 0u)) ? -lo : lo);
+}
+__device__ __forceinline__ double float_bits_to_double(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u;
+  const unsigned m = u & 0x7fffffu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);   // zero (subnormals flushed)
+  if (e == 0xffu) return __hiloint2double((int)(sign | 0x7ff00000u | (m ? 0x80000u : 0u)), 0);
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
 template <typename T, typename S>
 __device__ __forceinline__ T load_as(S x) { return x; }
 template <>
-__device__ __forceinline__ dfloat load_as<dfloat, double>(double x) {
-  const float h = __double2float_rn(x);
-  return dfloat(h, __double2float_rn(x - (double)h));
-}
+__device__ __forceinline__ dfloat load_as<dfloat, double>(double x) { return split_double(x); }
 template <typename S, typename T>
 __device__ __forceinline__ S store_as(T x) { return x; }
 template <>
-__device__ __forceinline__ double store_as<double, dfloat>(dfloat x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double store_as<double, dfloat>(dfloat x) {
+  return float_bits_to_double(x.hi) + float_bits_to_double(x.lo);   // one FP64 operation
+}
 
 template <typename T>
 struct DstTables {
@@ -570,30 +626,30 @@ template <typename T, int LP, int LG>
 __device__ __forceinline__ void dst_reg_stage_tables(T* sm, DstTables<T> tb) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int P = Lay::P, G = Lay::G, H = Lay::H, NF = Lay::NF;
-  T* sep = sm;                // sin(2m pi / Nf) + 1/2
-  T* sem = sep + H;           // sin(2m pi / Nf) - 1/2
-  T* sop = sem + H;           // sin((2m+1) pi / Nf) + 1/2
-  T* som = sop + H;           // sin((2m+1) pi / Nf) - 1/2
+  T* sep = sm;                // (sin(2m pi / Nf) + 1/2) / 2
+  T* sem = sep + H;           // (sin(2m pi / Nf) - 1/2) / 2
+  T* sop = sem + H;           // (sin((2m+1) pi / Nf) + 1/2) / 2
+  T* som = sop + H;           // (sin((2m+1) pi / Nf) - 1/2) / 2
   T* t1r = som + H;
   T* t1i = t1r + H;
-  T* t3r = t1i + H;           // W_Nf^{g P + c} / 2 at c G + g (the split's factor 1/2 folded in)
+  T* t3r = t1i + H;           // W_Nf^{g P + c} at c G + g
   T* t3i = t3r + H;
   T* wc = t3i + H;
   T* ws = wc + NF / 2;
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     const T s0 = tb.sinp[2 * i], s1 = tb.sinp[2 * i + 1];
-    sep[i] = s0 + T(0.5);
-    sem[i] = s0 - T(0.5);
-    sop[i] = s1 + T(0.5);
-    som[i] = s1 - T(0.5);
+    sep[i] = T(0.5) * (s0 + T(0.5));   // the split's factor 1/2, folded into the (linear) pre-processing
+    sem[i] = T(0.5) * (s0 - T(0.5));
+    sop[i] = T(0.5) * (s1 + T(0.5));
+    som[i] = T(0.5) * (s1 - T(0.5));
     const int k1 = i / G, gg = i - k1 * G;                 // t1 entry (k1, g)
     const int j1 = (2 * gg * k1) & (NF - 1);               // W_H^{g k1} = e^{-2 pi i (2 g k1) / Nf}
     t1r[i] = tb.twc[j1];
     t1i[i] = -tb.tws[j1];
-    const int c = i / G, g3 = i - c * G;                   // t3 entry (c, g): W_Nf^{g P + c} / 2
+    const int c = i / G, g3 = i - c * G;                   // t3 entry (c, g): W_Nf^{g P + c}
     const int j3 = g3 * P + c;
-    t3r[i] = T(0.5) * tb.twc[j3];
-    t3i[i] = T(-0.5) * tb.tws[j3];
+    t3r[i] = tb.twc[j3];
+    t3i[i] = -tb.tws[j3];
   }
   for (int i = threadIdx.x; i < NF / 2; i += blockDim.x) {
     wc[i] = tb.twc[i];
@@ -607,7 +663,9 @@ __device__ __forceinline__ void dst_reg_stage_tables(T* sm, DstTables<T> tb) {
 // spans two warps.  The pre-processing is written as
 // y_j = x_j (s_j + 1/2) + x_{Nf-j} (s_j - 1/2) and the even/odd split as
 // Y_k = 1/2 [A + (w_i - i w_r) B], A = Z_k + conj Z_{H-k}, B = Z_k - conj Z_{H-k},
-// W^k = w_r + i w_i, to save FP64 instructions.
+// W^k = w_r + i w_i, to save FP64 instructions; the split's factor 1/2 is
+// applied to the pre-processing weights instead (every step in between is
+// linear), so the split is two FMA per output after A and B.
 template <typename T, int LP, int LG>
 __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) {
   using Lay = DstRegLayout<LP, LG>;
@@ -690,9 +748,9 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
     const T zcr = bre[kc + (kc >> LP)], zcm = bim[kc + (kc >> LP)];   // Z_{H-k} = zcr + i zcm
     const T ar = zkr + zcr, ai = zki - zcm;                          // A = Z_k + conj Z_{H-k}
     const T br = zkr - zcr, bi = zki + zcm;                          // B = Z_k - conj Z_{H-k}
-    const T hr = t3r[c * G + g], hi = t3i[c * G + g];                // W^k / 2
-    Rk[c] = T(0.5) * ar + (hi * br + hr * bi);                       // Re Y_k
-    Ik[c] = (hr * br - hi * bi) - T(0.5) * ai;                       // -Im Y_k
+    const T hr = t3r[c * G + g], hi = t3i[c * G + g];                // W^k
+    Rk[c] = (ar + hi * br) + hr * bi;                                // Re Y_k
+    Ik[c] = (hr * br - ai) - hi * bi;                                // -Im Y_k
   }
   __syncwarp();
   T loc = T(0);

@@ -89,8 +89,9 @@ __device__ __forceinline__ T reg_trace(const T (&v)[Q]) {
 //   r_{s,k} = f_{s,k} - sum_l A_i[k,l] u_{s,l} + (-1)^k lamM_i sum_l u_{s-1,l}
 // (adjoint: A_i^T and + lamM_i sum_l (-1)^l u_{s+1,l}); at s = 0 of the forward
 // problem the trace is the transformed initial value u0^ (or 0).
-// amat[e * Nx + j] = A_i[k,l] (adjoint tables hold A_i^T).  Steps [s0, s1);
-// one thread per (mode, kStepsPerThread consecutive steps).
+// amat[e * Nx + j] = A_i[k,l] (adjoint tables hold A_i^T).  u == nullptr is a
+// zero iterate.  Steps [s0, s1); one thread per (mode, kStepsPerThread
+// consecutive steps).
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ>
 __global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, const T* __restrict__ u,
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, cons
     if (ADJ ? s < sb : s > se) break;
     T uv[Q];
 #pragma unroll
-    for (int l = 0; l < Q; ++l) uv[l] = u[((int64_t)s * Q + l) * Nx + j];
+    for (int l = 0; l < Q; ++l) uv[l] = (u != nullptr) ? u[((int64_t)s * Q + l) * Nx + j] : T(0);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
@@ -124,6 +125,137 @@ __global__ void __launch_bounds__(256) k_fresidual(const T* __restrict__ f, cons
     }
     t = reg_trace<T, Q, ADJ>(uv);
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual of k_fresidual together with its squared l2 norm, the stopping
+// quantity of Section 2 (and the norm that scales the refinement of the mixed
+// form).  The squares are accumulated in double-float on the FP32 pipe from
+// the residual split by integer operations (split_double), so the FP64 pipe
+// does the residual only; per-block partial sums (fixed shuffle tree, then the
+// warps in order) go to partial[pbase + block], reduced by k_sum_final.
+// Entries outside 2^-40 ... 2^40 in magnitude (whose squares or rounding terms
+// would leave the FP32 exponent range) are squared in FP64 instead; that sum
+// is reduced only in blocks that have one.
+// STORE32: the residual rounded to FP32 is stored in r32 (the right-hand side
+// of the FP32 cycles); otherwise nothing but the partial sums is written.
+// ---------------------------------------------------------------------------
+// Rare path of k_fresidual_norm (entries outside the double-float range), kept
+// out of line so that it is not predicated into the common path.
+__device__ __noinline__ double fp64_square_add(double a, double w) { return fma(a, a, w); }
+__device__ __noinline__ float fp64_narrow(double a) { return __double2float_rn(a); }
+
+__device__ __forceinline__ dfloat df_square(dfloat x) {
+  const float p = __fmul_rn(x.hi, x.hi);
+  float e = __fmaf_rn(x.hi, x.hi, -p);
+  e = __fmaf_rn(__fmul_rn(2.f, x.hi), x.lo, e);
+  return dfloat(p, e);
+}
+
+// Block sum of a double-float per thread (all threads of the block call it);
+// thread 0 receives the sum.  blockDim.x is a multiple of 32, at most 1024.
+__device__ __forceinline__ dfloat df_block_sum(dfloat v) {
+  __shared__ float rh[32], rl[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const dfloat o(__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off));
+    v = v + o;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    rh[warp] = v.hi;
+    rl[warp] = v.lo;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? dfloat(rh[lane], rl[lane]) : dfloat(0.f, 0.f);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const dfloat o(__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off));
+      v = v + o;
+    }
+  }
+  return v;
+}
+
+template <int Q, bool ADJ, bool STORE32>
+__global__ void __launch_bounds__(256) k_fresidual_norm(const double* __restrict__ f, const double* __restrict__ u,
+                                                        const double* __restrict__ u0, float* __restrict__ r32,
+                                                        int64_t Nx, int N, int s0, int s1,
+                                                        const double* __restrict__ amat,
+                                                        const double* __restrict__ lamM, double* __restrict__ partial,
+                                                        int64_t pbase) {
+  constexpr int TS = kStepsPerThread;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sb = s0 + blockIdx.y * TS;
+  dfloat acc(0.f, 0.f);
+  double wide = 0.0;   // squares of the entries outside the double-float range
+  if (j < Nx && sb < s1) {   // no early return: every thread takes part in the block sum
+    const int se = min(sb + TS, s1) - 1;
+    double A[Q * Q];
+#pragma unroll
+    for (int e = 0; e < Q * Q; ++e) A[e] = amat[(int64_t)e * Nx + j];
+    const double lam = lamM[j];
+    double t = entry_trace<double, Q, ADJ>(u, u0, Nx, N, sb, se, j);
+    // all residuals of the thread first (every load ahead of the out-of-line rare path), then the squares
+    double rv[TS][Q];
+    int nsteps = 0;
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+      const int s = ADJ ? se - i : sb + i;
+      if (ADJ ? s < sb : s > se) break;
+      double uv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) uv[l] = (u != nullptr) ? u[((int64_t)s * Q + l) * Nx + j] : 0.0;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        double a = f[((int64_t)s * Q + k) * Nx + j] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) a -= A[k * Q + l] * uv[l];
+        rv[i][k] = a;
+      }
+      t = reg_trace<double, Q, ADJ>(uv);
+      nsteps = i + 1;
+    }
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+      if (i >= nsteps) break;
+      const int s = ADJ ? se - i : sb + i;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
+        const double a = rv[i][k];
+        unsigned w_hi, w_lo;
+        double_words(a, w_hi, w_lo);
+        const int E = (int)((w_hi >> 20) & 0x7ffu);
+        if (((w_hi << 1) | w_lo) == 0u || (E >= 1023 - 40 && E <= 1023 + 40)) {
+          const dfloat rs = split_double(a);
+          if (STORE32) r32[idx] = rs.hi;
+          acc = acc + df_square(rs);
+        } else {
+          if (STORE32) r32[idx] = fp64_narrow(a);
+          wide = fp64_square_add(a, wide);
+        }
+      }
+    }
+  }
+  acc = df_block_sum(acc);
+  if (__syncthreads_or(wide != 0.0)) {   // block-uniform
+    __shared__ double rw[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wide += __shfl_down_sync(0xffffffffu, wide, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) rw[warp] = wide;
+    __syncthreads();
+    if (warp == 0) {
+      wide = lane < (int)(blockDim.x >> 5) ? rw[lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) wide += __shfl_down_sync(0xffffffffu, wide, off);
+    }
+  }
+  if (threadIdx.x == 0)
+    partial[pbase + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] =
+        (float_bits_to_double(acc.hi) + float_bits_to_double(acc.lo)) + wide;
 }
 
 // ---------------------------------------------------------------------------
@@ -230,7 +362,7 @@ __global__ void k_frestrict(const T* __restrict__ r, T* __restrict__ fc, int nf,
   constexpr int NT = 1 << D;
   int c[3] = {0, 0, 0};
   {
-    int64_t rest = J;
+    unsigned rest = (unsigned)J;   // spatial mode index: n <= 1023, so below 2^30
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       c[a] = (int)(rest % nc);
@@ -309,7 +441,8 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;   // coarse step: fine steps 2m and 2m + 1
   if (I >= Nxf || 2 * m + 1 >= Nf_steps) return;
-  int64_t rest = I, jc = 0, stride = 1;
+  unsigned rest = (unsigned)I;   // 32-bit: n <= 1023
+  int64_t jc = 0, stride = 1;
   T w = T(1);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -335,6 +468,125 @@ __global__ void k_fprolong(const T* __restrict__ ec, T* __restrict__ uf, int nf,
       for (int k = l; k < Q; ++k) acc += Rb[k * Q + l] * e[k];   // R_s[k][l] = 0 for l > k
       *dst = acc;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The coarse-grid correction fused into the first damped step after it (full
+// coarsening): the step reads the uncorrected u, adds the prolongated
+// correction of each fine step it touches (the mode pair weights and R_sl^T
+// of k_fprolong, time blocks pre-multiplied by 2^d) and takes the damped step
+// of k_fsmooth on the corrected iterate (FMODE kFromF or kUseWf).  The
+// corrected iterate itself is not stored: the next step reads only `out`.
+// Threads start on even fine steps, so both fine steps of a coarse step take
+// the same coarse values.  Steps [s0, s1) of the fine level.
+// ---------------------------------------------------------------------------
+template <typename T, int Q>
+__device__ __forceinline__ void fine_correction(const T* __restrict__ ec, int64_t Nxc, int64_t jc, T w, int s,
+                                                const TimeCoef<T, Q>& tc, T (&corr)[Q]) {
+  if (w == T(0)) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) corr[l] = T(0);
+    return;
+  }
+  T e[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) e[k] = w * ec[((int64_t)(s >> 1) * Q + k) * Nxc + jc];
+  const T* Rb = (s & 1) ? tc.R2 : tc.R1;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = l; k < Q; ++k) acc += Rb[k * Q + l] * e[k];   // R_s[k][l] = 0 for l > k
+    corr[l] = acc;
+  }
+}
+
+template <typename T, int D, int Q, bool ADJ, int FMODE>
+__global__ void __launch_bounds__(256) k_fprolong_smooth(const T* __restrict__ ec, const T* __restrict__ f,
+                                                         const T* __restrict__ u, const T* __restrict__ u0,
+                                                         T* __restrict__ out, int nf, int nc, int N, int s0, int s1,
+                                                         T wc, const T* __restrict__ ainv,
+                                                         const T* __restrict__ lamM, const T* __restrict__ ws,
+                                                         const T* __restrict__ ra, const T* __restrict__ rb,
+                                                         TimeCoef<T, Q> tc) {
+  static_assert(FMODE == kFromF || FMODE == kUseWf, "the step after the correction reads f or a ready wf");
+  static_assert(kStepsPerThread % 2 == 0, "threads start on a coarse step");
+  constexpr int TS = kStepsPerThread;
+  const int64_t Nxf = pow_d<D>(nf), Nxc = pow_d<D>(nc);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sb = s0 + blockIdx.y * TS;
+  if (j >= Nxf || sb >= s1) return;
+  const int se = min(sb + TS, s1) - 1;
+  // coarse source mode of this fine mode and the product of its pair weights
+  int64_t jc = 0;
+  T w = T(1);
+  {
+    unsigned rest = (unsigned)j;   // 32-bit: n <= 1023
+    int64_t stride = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int src = 0;
+      T wa = T(0);
+      if (!mode_source<T>((int)(rest % nf), nf, nc, ra, rb, src, wa)) wa = T(0);   // unpaired: no correction
+      rest /= nf;
+      jc += stride * src;
+      stride *= nc;
+      w *= wa;
+    }
+  }
+  T W[FMODE == kUseWf ? 1 : Q * Q];
+  T wsv[FMODE == kFromF ? 1 : Q];
+  T lam = T(0);
+  if (FMODE == kFromF) {
+#pragma unroll
+    for (int e = 0; e < Q * Q; ++e) W[e] = ainv[(int64_t)e * Nxf + j];
+    lam = lamM[j];
+  } else {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) wsv[k] = ws[(int64_t)k * Nxf + j];
+  }
+  // coupling trace of the corrected iterate at the step before the first one
+  T t = T(0);
+  {
+    const int sn = ADJ ? se + 1 : sb - 1;
+    if (sn >= 0 && sn < N) {
+      T corr[Q];
+      fine_correction<T, Q>(ec, Nxc, jc, w, sn, tc, corr);
+      T v[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) v[l] = u[((int64_t)sn * Q + l) * Nxf + j] + corr[l];
+      t = reg_trace<T, Q, ADJ>(v);
+    } else if (!ADJ && u0 != nullptr) {
+      t = u0[j];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TS; ++i) {
+    const int s = ADJ ? se - i : sb + i;
+    if (ADJ ? s < sb : s > se) break;
+    T corr[Q];
+    fine_correction<T, Q>(ec, Nxc, jc, w, s, tc, corr);
+    T g[Q], uv[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const T fk = f[((int64_t)s * Q + k) * Nxf + j];
+      g[k] = (FMODE == kFromF) ? fk + ((!ADJ && (k & 1)) ? -lam : lam) * t : fk;
+      uv[k] = u[((int64_t)s * Q + k) * Nxf + j] + corr[k];
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T x;
+      if (FMODE == kUseWf) {
+        x = g[k] + wsv[k] * t;
+      } else {
+        x = W[k * Q] * g[0];
+#pragma unroll
+        for (int l = 1; l < Q; ++l) x += W[k * Q + l] * g[l];
+      }
+      out[((int64_t)s * Q + k) * Nxf + j] = x + wc * uv[k];
+    }
+    t = reg_trace<T, Q, ADJ>(uv);
   }
 }
 
@@ -462,7 +714,8 @@ __global__ void __launch_bounds__(256) k_fspace_post(const T* __restrict__ b, T*
     bv[k] = b[((int64_t)s * Q + k) * Nxf + I];
     xv[k] = x[((int64_t)s * Q + k) * Nxf + I];
   }
-  int64_t rest = I, jc = 0, stride = 1;
+  unsigned rest = (unsigned)I;   // 32-bit: n <= 1023
+  int64_t jc = 0, stride = 1;
   T wgt = pscale;
   bool has = true;
 #pragma unroll
@@ -495,7 +748,7 @@ __global__ void k_fspace_restrict(const T* __restrict__ fine, T* __restrict__ co
   if (J >= Nxc || s >= nsteps) return;
   constexpr int NT = 1 << D;
   int c[3] = {0, 0, 0};
-  int64_t rest = J;
+  unsigned rest = (unsigned)J;   // spatial mode index: n <= 1023, so below 2^30
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     c[a] = (int)(rest % nc);
@@ -589,6 +842,14 @@ __global__ void __launch_bounds__(256) k_fresidual_dyn(const T* __restrict__ f, 
   for (int i = 0; i < TS; ++i) {
     const int s = ADJ ? se - i : sb + i;
     if (ADJ ? s < sb : s > se) break;
+    if (u == nullptr) {   // zero iterate
+      for (int k = 0; k < q; ++k) {
+        const int64_t idx = ((int64_t)s * q + k) * Nx + j;
+        r[idx] = f[idx] + ((!ADJ && (k & 1)) ? -lam : lam) * t;
+      }
+      t = T(0);
+      continue;
+    }
     const T* us = u + (int64_t)s * q * Nx + j;
     T S, alt;
     traces_dyn<T>(us, Nx, q, S, alt);
@@ -681,7 +942,7 @@ __global__ void k_frestrict_dyn(const T* __restrict__ r, T* __restrict__ fc, int
     wm[0] = T(1);
   } else {
     int c[3] = {0, 0, 0};
-    int64_t rest = J;
+    unsigned rest = (unsigned)J;   // spatial mode index: n <= 1023, so below 2^30
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       c[a] = (int)(rest % nc);
@@ -744,7 +1005,8 @@ __global__ void k_fprolong_dyn(const T* __restrict__ ec, T* __restrict__ uf, int
   int64_t jc = I;
   T w = T(1);
   if (FULL) {
-    int64_t rest = I, stride = 1;
+    unsigned rest = (unsigned)I;   // 32-bit: n <= 1023
+    int64_t stride = 1;
     jc = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {

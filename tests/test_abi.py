@@ -50,6 +50,7 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
     bad = [
         (stmg.StMesh(2, 254), 1, 16, 1.0),   # n not 2^k - 1
         (stmg.StMesh(4, 7), 1, 16, 1.0),     # dim > 3
+        (stmg.StMesh(1, 2047), 1, 16, 1.0),  # n > 1023
         (stmg.StMesh(2, 7), 1, 12, 1.0),     # N not a power of two
         (stmg.StMesh(2, 7), stmg.ST_MAX_PT + 1, 16, 1.0),   # p_t too large
         (stmg.StMesh(2, 7), 1, 16, -1.0),    # T <= 0

@@ -72,3 +72,29 @@ def test_bad_tensors_are_rejected_before_any_launch():
     # a zero right-hand side is already solved: zero iterations, zero iterate
     u, it, rr = s.solve(good)
     assert it == 0 and float(u.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_without_guess_returns_zero_when_no_cycle_runs(precision):
+    """Without an initial guess the FP64 form starts from u = 0 without storing
+    it; when no cycle runs (zero data, or maxit = 0) the output buffer still
+    holds that zero iterate, whatever it held before."""
+    require_gpu()
+    stmg = _stmg()
+    d, n, p, N = 2, 15, 1, 8
+    s = stmg.Solver(d, n, p, N, 1.0, precision=precision)
+    u = torch.full(s.shape, 7.0, dtype=torch.float64, device="cuda")
+    out, it, rr = s.solve(torch.zeros(s.shape, dtype=torch.float64, device="cuda"), u=u, initial_guess=False)
+    assert it == 0 and rr == 0.0 and torch.count_nonzero(out).item() == 0
+    s0 = stmg.Solver(d, n, p, N, 1.0, precision=precision, maxit=0)
+    f = to_gpu(workloads.uniform_load(d, n, p, N, seed=0))
+    u.fill_(7.0)
+    out, it, rr = s0.solve(f, u=u, initial_guess=False, raise_on_failure=False)
+    assert s0.last_status == stmg.ST_ENOTCONV and it == 0 and rr == 1.0
+    assert torch.count_nonzero(out).item() == 0
+    # a given initial guess is kept as the iterate
+    g = to_gpu(np.random.default_rng(5).uniform(-1, 1, size=s.shape))
+    out, it, rr = s0.solve(f, u=g.clone(), initial_guess=True, raise_on_failure=False)
+    assert it == 0 and torch.allclose(out, g, rtol=1e-12, atol=1e-12)
+    s.close()
+    s0.close()

@@ -286,3 +286,23 @@ def test_solve_host_matches_device_solve(precision, given):
     s.close()
     assert it_h == it_d and rr_h <= 1e-10
     assert rel_err(u_host.numpy(), to_np(u_dev)) < 1e-13
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1.0, 1e30])
+def test_mixed_refinement_is_scale_invariant(scale):
+    """The mixed form takes the FP32 residual unscaled as the right-hand side of
+    its FP32 cycles while its entries are far from the FP32 range limits, and
+    falls back to the FP64 residual divided by its norm otherwise (entries of
+    1e-30 and 1e30 here).  Either way the refinement sees the same problem: the
+    same number of refinements, the same relative residual, and a solution that
+    scales with the data."""
+    require_gpu()
+    from paper_1411_0519_gb300 import stmg
+    d, n, p, N, T = 2, 63, 1, 32, 1.0
+    f = to_gpu(workloads.uniform_load(d, n, p, N, seed=6))
+    s = stmg.Solver(d, n, p, N, T, rtol=1e-9, maxit=60, precision="mixed", inner_cycles=4)
+    u1, it1, rr1 = s.solve(f)
+    us, its, rrs = s.solve(f * scale)
+    s.close()
+    assert abs(its - it1) <= 1 and rrs <= 1e-9 and rr1 <= 1e-9
+    assert rel_err(to_np(us) / scale, to_np(u1)) < 1e-7
