@@ -227,7 +227,7 @@ def transform_note(prof, w):
     return {"kernel": "k_dst_rows_reg / k_dst_cols_reg <dfloat>", "arithmetic": "double-float on the FP32 pipe",
             "share_of_kernel_time": round(v["ms"] / total, 3), "launches": v["launches"],
             "fp64_equivalent_tflops": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4),
-            "bound": "latency (issue 39-42 %, 15.7 warps per SM; ncu)"}
+            "bound": "latency (issue 48-52 %, 15.7 warps per SM; ncu)"}
 
 
 def breakdown(prof):
