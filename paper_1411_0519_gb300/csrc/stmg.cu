@@ -766,11 +766,12 @@ void launch_space_pre_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, bo
 
 template <typename T, int D, int Q>
 void launch_space_post_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, const SpaceLvl<T>& cl, bool adj,
-                         const T* b, T* x, const T* xc, double w, const double* dinv) {
+                         const T* b, T* x, const T* xc, double w, const double* dinv, T* upd, double wt) {
   stmg::SmallMat<T, Q> m{};
   for (int i = 0; i < Q * Q; ++i) m.a[i] = (T)dinv[i];
   stmg::k_fspace_post<T, D, Q><<<dim3(blocks_for(sl.Nx), lv.N), kThreads, 0, h->stream>>>(
-      b, x, xc, sl.n, cl.n, lv.N, (T)w, m, sl.amat[adj ? 1 : 0], sl.ra, sl.rb, (T)(1 << D), h->opt.nu_x);
+      b, x, xc, sl.n, cl.n, lv.N, (T)w, m, sl.amat[adj ? 1 : 0], sl.ra, sl.rb, (T)(1 << D), h->opt.nu_x, upd,
+      (T)wt);
 }
 
 #define STMG_DISPATCH(FN, ...)                                                   \
@@ -880,7 +881,11 @@ void prolong_smooth(st_handle* h, int L, bool adj, int fmode, const T* ec, const
   const double step_flops = (fmode == stmg::kUseWf ? 0.0 : 2.0 * Q * Q) + 4.0 * Q + (fmode == stmg::kFromF ? Q : 0.0);
   Prof pr(h, ST_K_LINESOLVE, sizeof(T) * (3.0 * fn_ + (double)coarse.ndof),
           2.0 * fn_ * (1.0 + tq) + nodes * step_flops, 1, L);
-  STMG_DISPATCH(launch_prolong_smooth_t, h, fine, coarse, adj, fmode, ec, f, u, u0, out);
+  if constexpr (sizeof(T) == 4) {   // used by the FP32 cycles only
+    STMG_DISPATCH(launch_prolong_smooth_t, h, fine, coarse, adj, fmode, ec, f, u, u0, out);
+  } else {
+    fail(h, ST_EINVAL, "internal: the fused correction serves the FP32 cycles");
+  }
 }
 
 template <typename T>
@@ -1245,7 +1250,10 @@ void space_restrict(st_handle* h, Level& lv, const SpaceLvl<T>& fine, const Spac
 // x = D~^{-1} b on every time step of level lv: one spatial V-cycle from x = 0
 // (Remark on the V-cycle approximation in space), spatial level ell.
 template <typename T>
-void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) {
+// upd (finest spatial grid only, which must have more than one node): the
+// result is not stored in x but added to upd, times omega_t (the damped update
+// of the smoothing step).
+void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b, T* upd = nullptr) {
   std::vector<SpaceLvl<T>>& sp = spaces<T>(lv);
   const SpaceLvl<T>& sl = sp[ell];
   double dinv[kQmax * kQmax];
@@ -1266,9 +1274,9 @@ void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b) 
   const SpaceLvl<T>& cl = sp[ell + 1];
   space_restrict<T>(h, lv, sl, cl, sl.t, cl.b);
   space_vcycle<T>(h, lv, ell + 1, adj, cl.x, cl.b);
-  Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * (double)lv.N * (3.0 * sl.Nx + cl.Nx),
-          2.0 * nodes * (nu * (2.0 * Q * Q + Q) + Q), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_space_post_t, h, lv, sl, cl, adj, b, x, cl.x, w, dinv);
+  Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * (double)lv.N * ((upd ? 4.0 : 3.0) * sl.Nx + cl.Nx),
+          2.0 * nodes * (nu * (2.0 * Q * Q + Q) + Q + (upd ? 1.0 : 0.0)), 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_post_t, h, lv, sl, cl, adj, b, x, cl.x, w, dinv, upd, h->opt.omega);
 }
 
 bool inexact(const st_handle* h) { return h->opt.smoother == ST_SMOOTH_VCYCLE; }
@@ -1295,8 +1303,12 @@ template <typename T>
 void smooth_step_inexact(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* u0, T* work) {
   mresidual<T>(h, lv, adj, f, u, u0, work);
   T* d = spaces<T>(lv)[0].x;
-  space_vcycle<T>(h, lv, 0, adj, d, work);
-  axpy<T>(h, u, d, (T)h->opt.omega, lv.ndof);
+  if (spaces<T>(lv)[0].n > 1) {   // the update u += omega_t d done by the last spatial pass
+    space_vcycle<T>(h, lv, 0, adj, d, work, u);
+  } else {
+    space_vcycle<T>(h, lv, 0, adj, d, work);
+    axpy<T>(h, u, d, (T)h->opt.omega, lv.ndof);
+  }
 }
 
 // nu damped block-Jacobi steps (eq. chap4_smoother) with the exact block

@@ -642,7 +642,9 @@ __global__ void __launch_bounds__(256) k_fspace_op(const T* __restrict__ x, cons
 //   k_fspace_pre:  x = nu_x damped Jacobi sweeps from x = 0 (the first one is
 //                  w Dinv b), r = b - A_i x;  writes x and r.
 //   k_fspace_post: x += (P e_c)^ (mode pairs, weights pscale ra / rb per axis),
-//                  then nu_x sweeps;  updates x.
+//                  then nu_x sweeps;  updates x, or (upd given, the finest
+//                  spatial grid of a damped smoothing step) adds wt x to upd
+//                  instead of storing x.
 // The same iterates as the sweeps done one launch at a time.
 template <typename T, int Q>
 __device__ __forceinline__ void fspace_sweeps(T (&xv)[Q], const T (&bv)[Q], const T (&A)[Q * Q],
@@ -701,7 +703,7 @@ __global__ void __launch_bounds__(256) k_fspace_post(const T* __restrict__ b, T*
                                                      const T* __restrict__ xc, int nf, int nc, int nsteps, T w,
                                                      SmallMat<T, Q> Dinv, const T* __restrict__ amat,
                                                      const T* __restrict__ ra, const T* __restrict__ rb, T pscale,
-                                                     int nu) {
+                                                     int nu, T* __restrict__ upd, T wt) {
   const int64_t Nxc = pow_d<D>(nc), Nxf = pow_d<D>(nf);
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
@@ -733,8 +735,16 @@ __global__ void __launch_bounds__(256) k_fspace_post(const T* __restrict__ b, T*
     for (int k = 0; k < Q; ++k) xv[k] += wgt * xc[((int64_t)s * Q + k) * Nxc + jc];
   }
   fspace_sweeps<T, Q>(xv, bv, A, Dinv, w, nu);
+  if (upd != nullptr) {   // finest spatial grid of a smoothing step: u += w_t x, x itself not needed
 #pragma unroll
-  for (int k = 0; k < Q; ++k) x[((int64_t)s * Q + k) * Nxf + I] = xv[k];
+    for (int k = 0; k < Q; ++k) {
+      T* up = upd + ((int64_t)s * Q + k) * Nxf + I;
+      *up += wt * xv[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) x[((int64_t)s * Q + k) * Nxf + I] = xv[k];
+  }
 }
 
 // Space-only restriction in the sine basis (the spatial factor of k_frestrict,
