@@ -1,0 +1,86 @@
+"""Host logic of bench.py, without a GPU: the reference arm's JSON line, the
+roofline bookkeeping (bound selection, per-launch figures, measured traffic)
+on a synthetic kernel profile, and the traffic table against the summaries it
+cites."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "heat1d_63", "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "heat1d_63"
+
+
+class _FakeSolver:
+    """Stands in for stmg.Solver: a level count and per-level class totals."""
+
+    def __init__(self, levels, per_level):
+        self.num_levels = levels
+        self._pl = per_level
+
+    def profile_level(self, cls, L):
+        return self._pl.get((cls, L), {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+
+
+def _prof(**classes):
+    return {k: {"launches": v[0], "ms": v[1], "bytes": v[2], "flops": v[3]} for k, v in classes.items()}
+
+
+def test_roofline_takes_the_dominant_class_on_the_finest_level():
+    from paper_1411_0519_gb300 import workloads
+    w = workloads.WORKLOADS["heat2d_255"]
+    pk = {"hbm_gbs": 6790.3, "src": "measured"}
+    # finest level: 10 launches, 6 ms, 3.2 GB and 0.55 GFLOP each
+    fs = _FakeSolver(11, {("line_solve", 10): {"launches": 10, "ms": 6.0, "bytes": 3.2e10, "flops": 5.5e9}})
+    prof = _prof(line_solve=(40, 8.0, 3.6e10, 6.0e9), dst=(6, 7.0, 6.4e9, 1.2e10), residual=(10, 5.0, 1e10, 1e9))
+    rf = bench.roofline(fs, prof, False, pk, w)
+    assert rf["level"] == "finest" and rf["launches"] == 10
+    assert rf["avg_launch_ms"] == pytest.approx(0.6)
+    gbs = 3.2e10 / 6e-3 / 1e9
+    assert rf["bound"] == "hbm" and rf["achieved"] == pytest.approx(gbs, rel=1e-3)
+    assert rf["frac"] == pytest.approx(gbs / 6790.3, rel=1e-3)
+    assert rf["alg_bytes_per_launch"] == pytest.approx(3.2e9)
+    # measured traffic of the finest-level smoother, scaled from the profiled case to a launch here
+    t = bench.traffic_table()["line_solve/fp64/d2_n255_q2"]
+    ndof = w["N"] * (w["p_t"] + 1) * w["n"] ** w["d"]
+    assert rf["traffic"] == pytest.approx(t["bytes_per_dof"] * ndof)
+    assert rf["kernel"] == t["kernel"]
+    # excluding the dominant class moves to the next one; with flops dominating the bound is the ALU
+    fs2 = _FakeSolver(11, {("residual", 10): {"launches": 5, "ms": 4.0, "bytes": 1e8, "flops": 4.0e9}})
+    rf2 = bench.roofline(fs2, prof, False, pk, w, exclude=("line_solve", "dst"))
+    assert rf2["bound"] == "alu" and rf2["unit"] == "TFLOP/s"
+    assert rf2["frac"] == pytest.approx(4.0e9 / 4e-3 / 1e12 / bench.FP64_PEAK_TFLOPS, rel=1e-3)
+
+
+def test_traffic_table_entries_cite_existing_summaries():
+    table = bench.traffic_table()
+    assert table, "profiles/traffic_per_dof.json is missing"
+    kernel_of = {"line_solve": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg"}
+    for key, t in table.items():
+        cls, prec, case = key.split("/")
+        assert prec in ("fp64", "fp32") and case.startswith("d")
+        assert t["bytes_per_dof"] > 0
+        assert t["kernel"].startswith(kernel_of[cls]), (key, t["kernel"])
+        assert os.path.exists(os.path.join(ROOT, t["summary"])), t["summary"]
+        assert "dram__bytes_read.sum + dram__bytes_write.sum" in t["measured"]
