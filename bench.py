@@ -230,6 +230,19 @@ def transform_note(prof, w):
             "bound": "latency (issue 48-52 %, 15.7 warps per SM; ncu)"}
 
 
+def vcycle_times(solver, prof, steps, iters, per_step_ms):
+    """Time of one cycle: the solve time without the boundary transforms, per
+    cycle, and the kernel time of the finest level per cycle (CUDA events of
+    the library, transforms excluded)."""
+    L = solver.num_levels - 1
+    cls = [c for c in prof if not c.startswith("_") and c != "dst"]
+    fin = sum(solver.profile_level(c, L)["ms"] for c in cls)
+    dst = prof.get("dst", {}).get("ms", 0.0) / steps
+    n = max(1, iters)
+    return {"ms_per_cycle_without_transforms": (per_step_ms - dst) / n,
+            "finest_level_kernel_ms_per_cycle": fin / steps / n}
+
+
 def breakdown(prof):
     return {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                 "GBs": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
@@ -372,6 +385,7 @@ def main():
                "ms_per_step": 1e3 * dt / args.steps, "api": "st_solve_host"}
         del fh, u0h, uh
     rf64 = roofline(s64, prof64, False, pk, w)
+    vc64 = vcycle_times(s64, prof64, args.steps, it64[-1], per_step)
     s64.close()
     torch.cuda.empty_cache()
 
@@ -460,7 +474,7 @@ def main():
         "config": {"workload": args.workload, "d": d, "n": n, "p_t": p, "N": N, "T": T, "rtol": rtol,
                    "dof_per_gpu": s64.ndof, "nu1": 2, "nu2": 2, "omega": 0.5, "precision": "fp64",
                    "l2": "inputs larger than L2 (1.07 GB per vector), no flush"},
-        "iters": it64[-1], "relres": rr64,
+        "iters": it64[-1], "relres": rr64, "vcycle": vc64,
         "gpu_launches": launches,
         "roofline": rf64,
         "kernels": breakdown(prof64),

@@ -1488,7 +1488,7 @@ void launch_residual_norm_t(st_handle* h, Level& lv, bool adj, const double* f, 
 // FP32 in r32 when given; larger q: residual into the work vector, then norm2.
 double residual_norm(st_handle* h, bool adj, const double* f, const double* u, const double* u0, float* r32) {
   Level& lv = finest(h);
-  if (h->q > kQfix) {
+  if (h->q > kQfix) {   // the residual stays in the finest FP64 work vector (the mixed form's r64)
     if (r32) fail(h, ST_EINVAL, "internal: FP32 residual output needs q <= 4");
     cycle_residual<double>(h, lv, adj, f, u, u0, lv.v64.r);
     return norm2<double>(h, lv.v64.r, lv.ndof);
@@ -1603,7 +1603,8 @@ int solve_core(st_handle* h, bool adj, const CycleInputs& in, double* u, bool gi
       if (fp32_rhs_ok(rn)) {
         mixed_step(h, adj, u, nullptr, 1.0);
       } else {
-        cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
+        // q > kQfix: residual_norm left the FP64 residual in r already
+        if (h->q <= kQfix) cycle_residual<double>(h, lv, adj, in.f, u, in.u0, r);
         mixed_step(h, adj, u, r, rn);
       }
     } else {

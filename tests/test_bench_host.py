@@ -84,3 +84,13 @@ def test_traffic_table_entries_cite_existing_summaries():
         assert t["kernel"].startswith(kernel_of[cls]), (key, t["kernel"])
         assert os.path.exists(os.path.join(ROOT, t["summary"])), t["summary"]
         assert "dram__bytes_read.sum + dram__bytes_write.sum" in t["measured"]
+
+
+def test_vcycle_times_leave_out_the_boundary_transforms():
+    fs = _FakeSolver(3, {("line_solve", 2): {"launches": 8, "ms": 12.0, "bytes": 0.0, "flops": 0.0},
+                         ("residual", 2): {"launches": 4, "ms": 6.0, "bytes": 0.0, "flops": 0.0},
+                         ("dst", 2): {"launches": 2, "ms": 9.0, "bytes": 0.0, "flops": 0.0}})
+    prof = _prof(line_solve=(10, 14.0, 0, 0), residual=(6, 7.0, 0, 0), dst=(2, 9.0, 0, 0))
+    v = bench.vcycle_times(fs, prof, steps=3, iters=2, per_step_ms=20.0)
+    assert v["ms_per_cycle_without_transforms"] == pytest.approx((20.0 - 9.0 / 3) / 2)
+    assert v["finest_level_kernel_ms_per_cycle"] == pytest.approx((12.0 + 6.0) / 3 / 2)
