@@ -173,7 +173,7 @@ def traffic_table():
         return json.load(fh)
 
 
-KERNEL_OF_CLASS = {"line_solve": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg / k_dst_cols_reg",
+KERNEL_OF_CLASS = {"smooth": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg / k_dst_cols_reg",
                    "restrict": "k_frestrict", "prolong": "k_fprolong", "space_mg": "k_fspace_op"}
 
 
@@ -205,7 +205,7 @@ def roofline(solver, prof, fp32, pk, w, exclude=()):
     key = "%s/%s/d%d_n%d_q%d" % (dom, "fp32" if fp32 else "fp64", w["d"], w["n"], w["p_t"] + 1)
     t = traffic_table().get(key)
     name = t["kernel"] if t else KERNEL_OF_CLASS.get(dom, dom) + ("_dyn" if w["p_t"] > 3 and dom in
-                                                                   ("line_solve", "residual") else "")
+                                                                   ("smooth", "residual") else "")
     traffic = t["bytes_per_dof"] * ndof if t else None
     rf.update({"kernel": name or dom, "level": "finest", "launches": v["launches"],
                "avg_launch_ms": round(v["ms"] / launches, 4), "share_of_class_total": round(

@@ -192,15 +192,16 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
 #define ST_K_RESIDUAL   0   /* residual (forward / transposed); for q <= 4 the finest-level
                                residual of the stopping test with its norm in one pass */
 #define ST_K_DST        1   /* batched sine transform along one axis */
-#define ST_K_LINESOLVE  2   /* fused smoothing step: coupling term, q x q block inverse
-                               per sine mode, damping; in FP32 cycles also the first
-                               post-smoothing step with the coarse-grid correction */
+#define ST_K_SMOOTH     2   /* damped smoothing step (coupling term, q x q block inverse
+                               per sine mode, damping) and the coarsest substitution; in
+                               FP32 cycles also the first post-smoothing step with the
+                               coarse-grid correction */
 #define ST_K_RESTRICT   3
 #define ST_K_PROLONG    4
 #define ST_K_NORM       5   /* both reduction stages of a separate norm */
 #define ST_K_VECTOR     6   /* axpy, casts, copies, memsets */
 #define ST_K_RHS        7   /* separate smoother right-hand side (no longer launched:
-                               fused into ST_K_LINESOLVE; the value is kept) */
+                               fused into ST_K_SMOOTH; the value is kept) */
 #define ST_K_SPACEMG    8   /* spatial V-cycle of the inexact block inverse */
 #define ST_K_COUNT      9
 

@@ -848,7 +848,7 @@ void msmooth(st_handle* h, Level& lv, bool adj, bool damp, const T* f, const T* 
   // per (mode, step): trace Q - 1 adds, coupling Q FMA (lamM or ws), A_i^{-1} Q^2 FMA
   // (not with kUseWf), damping Q FMA
   const double flops = (fmode == stmg::kUseWf ? 0.0 : 2.0 * Q * Q) + 4.0 * Q + (fmode == stmg::kFromF ? Q : 0.0);
-  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * passes * nodes * Q, nodes * flops, 1, level_of(h, lv));
+  Prof pr(h, ST_K_SMOOTH, sizeof(T) * passes * nodes * Q, nodes * flops, 1, level_of(h, lv));
   if (h->q > kQfix) launch_msmooth_dyn<T>(h, lv, adj, damp, fmode, f, u, u0, out, wf, s0, ns);
   else STMG_DISPATCH(launch_msmooth_t, h, lv, adj, damp, fmode, f, u, u0, out, wf, s0, ns);
 }
@@ -879,7 +879,7 @@ void prolong_smooth(st_handle* h, int L, bool adj, int fmode, const T* ec, const
   // bytes: read f or wf, u and the coarse correction, write out; flops: the correction
   // (2 (1 + tq) per fine unknown, as k_fprolong) and the damped step (as k_fsmooth)
   const double step_flops = (fmode == stmg::kUseWf ? 0.0 : 2.0 * Q * Q) + 4.0 * Q + (fmode == stmg::kFromF ? Q : 0.0);
-  Prof pr(h, ST_K_LINESOLVE, sizeof(T) * (3.0 * fn_ + (double)coarse.ndof),
+  Prof pr(h, ST_K_SMOOTH, sizeof(T) * (3.0 * fn_ + (double)coarse.ndof),
           2.0 * fn_ * (1.0 + tq) + nodes * step_flops, 1, L);
   if constexpr (sizeof(T) == 4) {   // used by the FP32 cycles only
     STMG_DISPATCH(launch_prolong_smooth_t, h, fine, coarse, adj, fmode, ec, f, u, u0, out);
@@ -1352,7 +1352,7 @@ void smooth_modal(st_handle* h, Level& lv, bool adj, T* u, const T* f, const T* 
 
 // Exact coarsest solve (Section 2) by forward (adjoint: backward) substitution,
 // one block inverse per step with the coupling to the step solved before.
-// Mixed basis: one fused launch per step.
+// One undamped k_fsmooth launch per step (sine basis).
 template <typename T>
 void coarsest_modal(st_handle* h, bool adj, T* u, const T* f, const T* u0) {
   Level& lv = h->levels[0];

@@ -33,7 +33,7 @@ EXPORTS = [
 
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
 
-KERNEL_CLASSES = ["residual", "dst", "line_solve", "restrict", "prolong", "norm", "vector", "rhs", "space_mg"]
+KERNEL_CLASSES = ["residual", "dst", "smooth", "restrict", "prolong", "norm", "vector", "rhs", "space_mg"]
 
 
 class StMesh(ctypes.Structure):

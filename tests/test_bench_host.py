@@ -52,8 +52,8 @@ def test_roofline_takes_the_dominant_class_on_the_finest_level():
     w = workloads.WORKLOADS["heat2d_255"]
     pk = {"hbm_gbs": 6790.3, "src": "measured"}
     # finest level: 10 launches, 6 ms, 3.2 GB and 0.55 GFLOP each
-    fs = _FakeSolver(11, {("line_solve", 10): {"launches": 10, "ms": 6.0, "bytes": 3.2e10, "flops": 5.5e9}})
-    prof = _prof(line_solve=(40, 8.0, 3.6e10, 6.0e9), dst=(6, 7.0, 6.4e9, 1.2e10), residual=(10, 5.0, 1e10, 1e9))
+    fs = _FakeSolver(11, {("smooth", 10): {"launches": 10, "ms": 6.0, "bytes": 3.2e10, "flops": 5.5e9}})
+    prof = _prof(smooth=(40, 8.0, 3.6e10, 6.0e9), dst=(6, 7.0, 6.4e9, 1.2e10), residual=(10, 5.0, 1e10, 1e9))
     rf = bench.roofline(fs, prof, False, pk, w)
     assert rf["level"] == "finest" and rf["launches"] == 10
     assert rf["avg_launch_ms"] == pytest.approx(0.6)
@@ -62,13 +62,13 @@ def test_roofline_takes_the_dominant_class_on_the_finest_level():
     assert rf["frac"] == pytest.approx(gbs / 6790.3, rel=1e-3)
     assert rf["alg_bytes_per_launch"] == pytest.approx(3.2e9)
     # measured traffic of the finest-level smoother, scaled from the profiled case to a launch here
-    t = bench.traffic_table()["line_solve/fp64/d2_n255_q2"]
+    t = bench.traffic_table()["smooth/fp64/d2_n255_q2"]
     ndof = w["N"] * (w["p_t"] + 1) * w["n"] ** w["d"]
     assert rf["traffic"] == pytest.approx(t["bytes_per_dof"] * ndof)
     assert rf["kernel"] == t["kernel"]
     # excluding the dominant class moves to the next one; with flops dominating the bound is the ALU
     fs2 = _FakeSolver(11, {("residual", 10): {"launches": 5, "ms": 4.0, "bytes": 1e8, "flops": 4.0e9}})
-    rf2 = bench.roofline(fs2, prof, False, pk, w, exclude=("line_solve", "dst"))
+    rf2 = bench.roofline(fs2, prof, False, pk, w, exclude=("smooth", "dst"))
     assert rf2["bound"] == "alu" and rf2["unit"] == "TFLOP/s"
     assert rf2["frac"] == pytest.approx(4.0e9 / 4e-3 / 1e12 / bench.FP64_PEAK_TFLOPS, rel=1e-3)
 
@@ -76,7 +76,7 @@ def test_roofline_takes_the_dominant_class_on_the_finest_level():
 def test_traffic_table_entries_cite_existing_summaries():
     table = bench.traffic_table()
     assert table, "profiles/traffic_per_dof.json is missing"
-    kernel_of = {"line_solve": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg"}
+    kernel_of = {"smooth": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg"}
     for key, t in table.items():
         cls, prec, case = key.split("/")
         assert prec in ("fp64", "fp32") and case.startswith("d")
@@ -87,10 +87,10 @@ def test_traffic_table_entries_cite_existing_summaries():
 
 
 def test_vcycle_times_leave_out_the_boundary_transforms():
-    fs = _FakeSolver(3, {("line_solve", 2): {"launches": 8, "ms": 12.0, "bytes": 0.0, "flops": 0.0},
+    fs = _FakeSolver(3, {("smooth", 2): {"launches": 8, "ms": 12.0, "bytes": 0.0, "flops": 0.0},
                          ("residual", 2): {"launches": 4, "ms": 6.0, "bytes": 0.0, "flops": 0.0},
                          ("dst", 2): {"launches": 2, "ms": 9.0, "bytes": 0.0, "flops": 0.0}})
-    prof = _prof(line_solve=(10, 14.0, 0, 0), residual=(6, 7.0, 0, 0), dst=(2, 9.0, 0, 0))
+    prof = _prof(smooth=(10, 14.0, 0, 0), residual=(6, 7.0, 0, 0), dst=(2, 9.0, 0, 0))
     v = bench.vcycle_times(fs, prof, steps=3, iters=2, per_step_ms=20.0)
     assert v["ms_per_cycle_without_transforms"] == pytest.approx((20.0 - 9.0 / 3) / 2)
     assert v["finest_level_kernel_ms_per_cycle"] == pytest.approx((12.0 + 6.0) / 3 / 2)
