@@ -174,7 +174,7 @@ def traffic_table():
 
 
 KERNEL_OF_CLASS = {"smooth": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg / k_dst_cols_reg",
-                   "restrict": "k_frestrict", "prolong": "k_fprolong", "space_mg": "k_fspace_op"}
+                   "restrict": "k_frestrict", "prolong": "k_fprolong", "space_mg": "k_fspace_pre / k_fspace_post"}
 
 
 def roofline(solver, prof, fp32, pk, w, exclude=()):

@@ -737,15 +737,12 @@ void launch_ic_grad_t(st_handle* h, const Level& lv, const T* lam, T* g) {
 }
 
 template <typename T, int D, int Q>
-void launch_space_op_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, int mode, bool adj, const T* x,
-                       const T* b, T* xo, double w, const double* dinv) {
+void launch_space_solve_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, const T* b, T* xo, double w,
+                          const double* dinv) {
   stmg::SmallMat<T, Q> m{};
   for (int i = 0; i < Q * Q; ++i) m.a[i] = (T)dinv[i];
   dim3 grid(blocks_for(sl.Nx), lv.N);
-  const T ww = (T)w;
-  const T* am = sl.amat[adj ? 1 : 0];
-  if (mode != 2) fail(h, ST_EINVAL, "spatial operator mode");   // sweeps and residuals are fused (k_fspace_pre/post)
-  stmg::k_fspace_op<T, Q, 2><<<grid, kThreads, 0, h->stream>>>(x, b, xo, sl.Nx, lv.N, ww, m, am);
+  stmg::k_fspace_solve<T, Q><<<grid, kThreads, 0, h->stream>>>(b, xo, sl.Nx, lv.N, (T)w, m);
 }
 
 template <typename T, int D, int Q>
@@ -1229,14 +1226,13 @@ void node_block_inverse(const st_handle* h, double hl, double tau, bool adj, dou
   for (int i = 0; i < q * q; ++i) out[i] = X[i];
 }
 
+// Exact solve on the one-node spatial level, xo = w Dinv b per (mode, step).
 template <typename T>
-void space_op(st_handle* h, Level& lv, const SpaceLvl<T>& sl, int mode, bool adj, const T* x, const T* b, T* xo,
-              double w, const double* dinv) {
+void space_solve(st_handle* h, Level& lv, const SpaceLvl<T>& sl, const T* b, T* xo, double w, const double* dinv) {
   const double nodes = (double)lv.N * sl.Nx, Q = h->q;
-  // per (mode, step): A_i x Q^2 FMA (modes 0, 1), Dinv r Q^2 FMA and the update (modes 0, 2)
-  Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * nodes * (mode == 2 ? 2.0 : 3.0),
-          2.0 * nodes * (mode == 2 ? Q * Q : mode == 1 ? Q * Q : 2.0 * Q * Q + Q), 1, level_of(h, lv));
-  STMG_DISPATCH(launch_space_op_t, h, lv, sl, mode, adj, x, b, xo, w, dinv);
+  // per (mode, step): Dinv b, Q^2 FMA; read b, write xo
+  Prof pr(h, ST_K_SPACEMG, sizeof(T) * Q * nodes * 2.0, 2.0 * nodes * Q * Q, 1, level_of(h, lv));
+  STMG_DISPATCH(launch_space_solve_t, h, lv, sl, b, xo, w, dinv);
 }
 
 template <typename T>
@@ -1259,7 +1255,7 @@ void space_vcycle(st_handle* h, Level& lv, int ell, bool adj, T* x, const T* b, 
   double dinv[kQmax * kQmax];
   node_block_inverse(h, sl.h, lv.tau, adj, dinv);
   if (sl.n == 1) {   // one node: D^x = A, exact solve
-    space_op<T>(h, lv, sl, 2, adj, nullptr, b, x, 1.0, dinv);
+    space_solve<T>(h, lv, sl, b, x, 1.0, dinv);
     return;
   }
   // pre-smoothing (nu_x sweeps from 0) and the spatial residual in one pass per

@@ -598,42 +598,26 @@ __global__ void __launch_bounds__(256) k_fprolong_smooth(const T* __restrict__ e
 // transform, and the spatial operator of every spatial level is A_i per mode:
 // the sweep, the spatial residual and the exact one-node solve are pointwise,
 // and the spatial transfers pair modes as in k_frestrict (without time blocks).
-// k_fspace_op, per (mode, step), amat = A_i of the spatial level (adjoint: A_i^T,
-// with Dinv of the transposed block):
-//   MODE 0: xo = x + w Dinv (b - A_i x)     MODE 1: xo = b - A_i x
-//   MODE 2: xo = w Dinv b  (on the one-node level w = 1 and Dinv = A^{-1} solve
-//           exactly; the other levels use the fused k_fspace_pre / k_fspace_post)
+// k_fspace_solve, per (mode, step): xo = w Dinv b, the exact solve on the
+// one-node spatial level (w = 1, Dinv = A^{-1}; adjoint: of the transposed
+// block); the sweeps and residuals of the other levels are the fused
+// k_fspace_pre / k_fspace_post.
 // ---------------------------------------------------------------------------
-template <typename T, int Q, int MODE>
-__global__ void __launch_bounds__(256) k_fspace_op(const T* __restrict__ x, const T* __restrict__ b,
-                                                   T* __restrict__ xo, int64_t Nx, int nsteps, T w,
-                                                   SmallMat<T, Q> Dinv, const T* __restrict__ amat) {
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) k_fspace_solve(const T* __restrict__ b, T* __restrict__ xo, int64_t Nx,
+                                                      int nsteps, T w, SmallMat<T, Q> Dinv) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   if (j >= Nx || s >= nsteps) return;
-  T r[Q], xv[Q];
+  T r[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) r[k] = b[((int64_t)s * Q + k) * Nx + j];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    r[k] = b[((int64_t)s * Q + k) * Nx + j];
-    xv[k] = (MODE == 2) ? T(0) : x[((int64_t)s * Q + k) * Nx + j];
-  }
-  if (MODE != 2) {
+    T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < Q; ++k)
-#pragma unroll
-      for (int l = 0; l < Q; ++l) r[k] -= amat[(int64_t)(k * Q + l) * Nx + j] * xv[l];
-  }
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const int64_t idx = ((int64_t)s * Q + k) * Nx + j;
-    if (MODE == 1) {
-      xo[idx] = r[k];
-    } else {
-      T acc = T(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) acc += Dinv.a[k * Q + l] * r[l];
-      xo[idx] = xv[k] + w * acc;
-    }
+    for (int l = 0; l < Q; ++l) acc += Dinv.a[k * Q + l] * r[l];
+    xo[((int64_t)s * Q + k) * Nx + j] = w * acc;
   }
 }
 
