@@ -111,6 +111,19 @@ size_t st_ndof(const st_handle* h);
 
 int st_num_levels(const st_handle* h);
 
+/* The coarsening plan st_setup would build, computed on the host only (no
+ * device, no handle): the hierarchy of Section 2 with the rule of Section 4
+ * (mu_L = tau_L / h_L^2 against mu* of Remark
+ * chap4_remarkCriticalDiscretizationParameter, full coarsening when
+ * mu_L >= mu* and n_L >= 3 under ST_AUTO) down to coarsest_steps steps.
+ * Arrays hold max_levels entries, level 0 = coarsest, with the meaning of
+ * st_level_info; any of them, nlev and mu_star may be NULL.  *nlev receives
+ * the number of levels, *mu_star the critical value for p_t.
+ * Errors: ST_EINVAL for the argument checks of st_setup, or when an array is
+ * given and max_levels is below the number of levels (nlev is still set). */
+int st_plan(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt, int max_levels,
+            int* N_L, int* n_L, double* mu_L, int* full, int* nlev, double* mu_star);
+
 /* Level L (0 = coarsest): time steps, nodes per axis, mu_L = tau_L/h_L^2 and
  * whether level L was obtained from L+1 by full coarsening (1), semi (0), or
  * is the finest (-1).  Any output pointer may be NULL.  Errors: ST_EINVAL. */

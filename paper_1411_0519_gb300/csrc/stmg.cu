@@ -1737,6 +1737,72 @@ void st_default_options(st_options* o) {
   o->gamma = 1;
 }
 
+namespace {
+
+// Argument checks of st_setup (and st_plan): the message of the first
+// violation, or nullptr.  o receives the options with defaults applied.
+const char* check_setup_args(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt,
+                             st_options& o) {
+  if (!mesh || mesh->dim < 1 || mesh->dim > 3 || !is_pow2m1(mesh->n)) return "mesh: dim 1..3, n = 2^k-1";
+  if (mesh->n > 1023) return "mesh: n <= 1023";
+  if (p_t < 0 || p_t > ST_MAX_PT) return "p_t out of range";
+  if (!is_pow2(N)) return "N must be a power of 2";
+  if (!(T > 0.0) || !std::isfinite(T)) return "T must be positive";
+  if (opt) o = *opt; else st_default_options(&o);
+  if (o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) || o.maxit < 0 || !(o.rtol >= 0.0)) return "bad options";
+  if (o.precision != ST_FP64 && o.precision != ST_MIXED) return "bad precision";
+  if (o.coarsening < ST_AUTO || o.coarsening > ST_FULL) return "bad coarsening";
+  if (o.smoother != ST_SMOOTH_EXACT && o.smoother != ST_SMOOTH_VCYCLE) return "bad smoother";
+  if (o.smoother == ST_SMOOTH_VCYCLE && (o.nu_x < 1 || !(o.omega_x > 0.0))) return "bad spatial smoothing options";
+  if (o.smoother == ST_SMOOTH_VCYCLE && p_t + 1 > kQfix) return "the inexact block inverse supports p_t <= 3";
+  if (o.gamma < 1 || o.gamma > 2) return "gamma must be 1 (V-cycle) or 2 (W-cycle)";
+  if (o.coarsest_steps < 1) o.coarsest_steps = 1;
+  if (!is_pow2(o.coarsest_steps) || o.coarsest_steps > N) return "bad coarsest_steps";
+  return nullptr;
+}
+
+struct PlanLevel {
+  int N = 0, n = 0;
+  double tau = 0, h = 0, mu = 0;
+  int coarsen_full = 0;   // how this level is restricted to the next coarser one
+};
+
+// Coarsening plan, finest level first (Section 2; Section 4 with the Remark on
+// the critical parameter): halve the steps on every level; also halve the
+// spatial grid (full coarsening) when mu_L = tau_L / h_L^2 >= mu* (automatic
+// rule; up to a relative 1e-12) and the grid has at least 3 nodes; stop at
+// coarsest_steps steps.
+std::vector<PlanLevel> plan_levels(int n, int p_t, int N, double T, const st_options& o) {
+  const double ms = mu_star(p_t);
+  std::vector<PlanLevel> out;
+  int Nl = N, nl = n;
+  double tau = T / N;
+  while (true) {
+    PlanLevel L;
+    L.N = Nl;
+    L.n = nl;
+    L.tau = tau;
+    L.h = 1.0 / (nl + 1);
+    L.mu = tau / (L.h * L.h);
+    if (Nl <= o.coarsest_steps) {
+      out.push_back(L);
+      break;
+    }
+    bool full;
+    if (o.coarsening == ST_SEMI) full = false;
+    else if (o.coarsening == ST_FULL) full = nl >= 3;
+    else full = (L.mu >= ms * (1.0 - 1e-12)) && nl >= 3;
+    L.coarsen_full = full ? 1 : 0;
+    out.push_back(L);
+    Nl /= 2;
+    tau *= 2.0;
+    if (full) nl = (nl - 1) / 2;
+  }
+  return out;
+}
+
+}  // namespace
+
 int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt, void* cuda_stream,
              st_handle** out) {
   if (!out) return ST_EINVAL;
@@ -1744,24 +1810,7 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
   st_handle* h = new (std::nothrow) st_handle();
   if (!h) return ST_ENOMEM;
   int rc = guarded(h, [&]() -> int {
-    if (!mesh || mesh->dim < 1 || mesh->dim > 3 || !is_pow2m1(mesh->n)) fail(h, ST_EINVAL, "mesh: dim 1..3, n = 2^k-1");
-    if (mesh->n > 1023) fail(h, ST_EINVAL, "mesh: n <= 1023");
-    if (p_t < 0 || p_t > ST_MAX_PT) fail(h, ST_EINVAL, "p_t out of range");
-    if (!is_pow2(N)) fail(h, ST_EINVAL, "N must be a power of 2");
-    if (!(T > 0.0) || !std::isfinite(T)) fail(h, ST_EINVAL, "T must be positive");
-    if (opt) h->opt = *opt; else st_default_options(&h->opt);
-    if (h->opt.nu1 < 0 || h->opt.nu2 < 0 || !(h->opt.omega > 0.0) || h->opt.maxit < 0 || !(h->opt.rtol >= 0.0))
-      fail(h, ST_EINVAL, "bad options");
-    if (h->opt.precision != ST_FP64 && h->opt.precision != ST_MIXED) fail(h, ST_EINVAL, "bad precision");
-    if (h->opt.coarsening < ST_AUTO || h->opt.coarsening > ST_FULL) fail(h, ST_EINVAL, "bad coarsening");
-    if (h->opt.smoother != ST_SMOOTH_EXACT && h->opt.smoother != ST_SMOOTH_VCYCLE) fail(h, ST_EINVAL, "bad smoother");
-    if (h->opt.smoother == ST_SMOOTH_VCYCLE && (h->opt.nu_x < 1 || !(h->opt.omega_x > 0.0)))
-      fail(h, ST_EINVAL, "bad spatial smoothing options");
-    if (h->opt.smoother == ST_SMOOTH_VCYCLE && p_t + 1 > kQfix)
-      fail(h, ST_EINVAL, "the inexact block inverse supports p_t <= 3");
-    if (h->opt.gamma < 1 || h->opt.gamma > 2) fail(h, ST_EINVAL, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
-    if (h->opt.coarsest_steps < 1) h->opt.coarsest_steps = 1;
-    if (!is_pow2(h->opt.coarsest_steps) || h->opt.coarsest_steps > N) fail(h, ST_EINVAL, "bad coarsest_steps");
+    if (const char* bad = check_setup_args(mesh, p_t, N, T, opt, h->opt)) fail(h, ST_EINVAL, bad);
     h->d = mesh->dim;
     h->p_t = p_t;
     h->q = p_t + 1;
@@ -1770,33 +1819,19 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->tm = make_time(p_t);
     // hierarchy, finest first, then reversed to the paper's numbering (0 = coarsest)
-    const double ms = mu_star(p_t);
     std::vector<Level> lv;
-    int Nl = N, nl = mesh->n;
-    double tau = T / N;
-    while (true) {
+    for (const PlanLevel& P : plan_levels(mesh->n, p_t, N, T, h->opt)) {
       Level L;
-      L.N = Nl;
-      L.n = nl;
-      L.tau = tau;
-      L.h = 1.0 / (nl + 1);
-      L.mu = tau / (L.h * L.h);
+      L.N = P.N;
+      L.n = P.n;
+      L.tau = P.tau;
+      L.h = P.h;
+      L.mu = P.mu;
+      L.coarsen_full = P.coarsen_full;
       L.Nx = 1;
-      for (int a = 0; a < h->d; ++a) L.Nx *= nl;
-      L.ndof = (int64_t)Nl * h->q * L.Nx;
-      if (Nl <= h->opt.coarsest_steps) {
-        lv.push_back(L);
-        break;
-      }
-      bool full;
-      if (h->opt.coarsening == ST_SEMI) full = false;
-      else if (h->opt.coarsening == ST_FULL) full = nl >= 3;
-      else full = (L.mu >= ms * (1.0 - 1e-12)) && nl >= 3;
-      L.coarsen_full = full ? 1 : 0;
+      for (int a = 0; a < h->d; ++a) L.Nx *= P.n;
+      L.ndof = (int64_t)P.N * h->q * L.Nx;
       lv.push_back(L);
-      Nl /= 2;
-      tau *= 2.0;
-      if (full) nl = (nl - 1) / 2;
     }
     std::reverse(lv.begin(), lv.end());
     h->levels = lv;
@@ -1901,6 +1936,29 @@ const char* st_last_error(const st_handle* h) {
 size_t st_ndof(const st_handle* h) { return h ? (size_t)h->levels.back().ndof : 0; }
 
 int st_num_levels(const st_handle* h) { return h ? (int)h->levels.size() : 0; }
+
+int st_plan(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt, int max_levels, int* N_L,
+            int* n_L, double* mu_L, int* full, int* nlev, double* mu_star_out) {
+  try {
+    st_options o{};
+    if (check_setup_args(mesh, p_t, N, T, opt, o)) return ST_EINVAL;
+    std::vector<PlanLevel> plan = plan_levels(mesh->n, p_t, N, T, o);
+    std::reverse(plan.begin(), plan.end());   // 0 = coarsest, as st_level_info
+    const int nl = (int)plan.size();
+    if (nlev) *nlev = nl;
+    if (mu_star_out) *mu_star_out = mu_star(p_t);
+    if ((N_L || n_L || mu_L || full) && max_levels < nl) return ST_EINVAL;
+    for (int L = 0; L < nl; ++L) {
+      if (N_L) N_L[L] = plan[L].N;
+      if (n_L) n_L[L] = plan[L].n;
+      if (mu_L) mu_L[L] = plan[L].mu;
+      if (full) full[L] = (L == nl - 1) ? -1 : plan[L + 1].coarsen_full;
+    }
+    return ST_OK;
+  } catch (...) {
+    return ST_ENOMEM;
+  }
+}
 
 int st_level_info(const st_handle* h, int L, int* N_L, int* n_L, double* mu_L, int* full) {
   if (!h || L < 0 || L >= (int)h->levels.size()) return ST_EINVAL;

@@ -29,6 +29,7 @@ EXPORTS = [
     "st_level_residual",
     "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
     "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop", "st_profile_level", "st_norm2_noalloc",
+    "st_plan",
 ]
 
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
@@ -78,6 +79,9 @@ def load_library(path=None):
         "st_ndof": (ctypes.c_size_t, [H]),
         "st_num_levels": (I, [H]),
         "st_level_info": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "st_plan": (I, [ctypes.POINTER(StMesh), I, I, D, ctypes.POINTER(StOptions), I, ctypes.POINTER(I),
+                        ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I),
+                        ctypes.POINTER(D)]),
         "st_residual": (I, [H, P, P, P, P]),
         "st_vcycle": (I, [H, P, P, P]),
         "st_solve": (I, [H, P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
@@ -128,6 +132,46 @@ _PRECISION = {"fp64": ST_FP64, "mixed": ST_MIXED}
 _COARSEN = {"auto": ST_AUTO, "semi": ST_SEMI, "full": ST_FULL}
 
 
+def make_options(*, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50, precision="fp64", coarsening="auto",
+                 coarsest_steps=1, inner_cycles=1, max_workspace_bytes=0, smoother="exact", nu_x=2,
+                 omega_x=2.0 / 3.0, gamma=1):
+    """st_options from keyword arguments (the defaults of st_default_options)."""
+    opt = StOptions()
+    lib().st_default_options(ctypes.byref(opt))
+    opt.nu1, opt.nu2, opt.omega, opt.rtol, opt.maxit = nu1, nu2, omega, rtol, maxit
+    opt.precision = _PRECISION[precision]
+    opt.coarsening = _COARSEN[coarsening]
+    opt.coarsest_steps = coarsest_steps
+    opt.inner_cycles = inner_cycles
+    opt.max_workspace_bytes = max_workspace_bytes
+    opt.smoother = {"exact": ST_SMOOTH_EXACT, "vcycle": ST_SMOOTH_VCYCLE}[smoother]
+    opt.nu_x = nu_x
+    opt.omega_x = omega_x
+    opt.gamma = gamma
+    return opt
+
+
+def plan(dim, n, p_t, N, T, **options):
+    """The hierarchy st_setup would build (st_plan, host only): (levels, mu_star),
+    levels coarsest first as dicts N, n, mu, full (as Solver.level_info)."""
+    L = lib()
+    opt = make_options(**options)
+    mesh = StMesh(dim, n)
+    nlev = ctypes.c_int()
+    ms = ctypes.c_double()
+    rc = L.st_plan(ctypes.byref(mesh), p_t, N, float(T), ctypes.byref(opt), 0, None, None, None, None,
+                   ctypes.byref(nlev), ctypes.byref(ms))
+    if rc != ST_OK:
+        raise StmgError(rc, "st_plan: invalid arguments")
+    k = nlev.value
+    Ns, ns, fs = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_int * k)()
+    mus = (ctypes.c_double * k)()
+    rc = L.st_plan(ctypes.byref(mesh), p_t, N, float(T), ctypes.byref(opt), k, Ns, ns, mus, fs, None, None)
+    if rc != ST_OK:
+        raise StmgError(rc, "st_plan failed")
+    return [{"N": Ns[i], "n": ns[i], "mu": mus[i], "full": fs[i]} for i in range(k)], ms.value
+
+
 class Solver:
     """A space-time hierarchy (st_setup) bound to the current CUDA stream."""
 
@@ -139,18 +183,10 @@ class Solver:
         self._lib = L
         self.dim, self.n, self.p_t, self.N, self.T = dim, n, p_t, N, float(T)
         self.q = p_t + 1
-        opt = StOptions()
-        L.st_default_options(ctypes.byref(opt))
-        opt.nu1, opt.nu2, opt.omega, opt.rtol, opt.maxit = nu1, nu2, omega, rtol, maxit
-        opt.precision = _PRECISION[precision]
-        opt.coarsening = _COARSEN[coarsening]
-        opt.coarsest_steps = coarsest_steps
-        opt.inner_cycles = inner_cycles
-        opt.max_workspace_bytes = max_workspace_bytes
-        opt.smoother = {"exact": ST_SMOOTH_EXACT, "vcycle": ST_SMOOTH_VCYCLE}[smoother]
-        opt.nu_x = nu_x
-        opt.omega_x = omega_x
-        opt.gamma = gamma
+        opt = make_options(nu1=nu1, nu2=nu2, omega=omega, rtol=rtol, maxit=maxit, precision=precision,
+                           coarsening=coarsening, coarsest_steps=coarsest_steps, inner_cycles=inner_cycles,
+                           max_workspace_bytes=max_workspace_bytes, smoother=smoother, nu_x=nu_x,
+                           omega_x=omega_x, gamma=gamma)
         self.options = opt
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
