@@ -211,7 +211,9 @@ def roofline(solver, prof, fp32, pk, w, exclude=()):
                "avg_launch_ms": round(v["ms"] / launches, 4), "share_of_class_total": round(
                    classes[dom]["ms"] / total_ms, 3),
                "alg_bytes_per_launch": v["bytes"] / launches, "alg_flops_per_launch": v["flops"] / launches,
-               "traffic": traffic})
+               "traffic": traffic,
+               # DRAM bytes per launch measured by ncu over this run's average launch time
+               "traffic_gbs": round(traffic / (v["ms"] / launches / 1e3) / 1e9, 1) if traffic else None})
     return rf
 
 

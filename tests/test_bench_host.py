@@ -65,6 +65,7 @@ def test_roofline_takes_the_dominant_class_on_the_finest_level():
     t = bench.traffic_table()["smooth/fp64/d2_n255_q2"]
     ndof = w["N"] * (w["p_t"] + 1) * w["n"] ** w["d"]
     assert rf["traffic"] == pytest.approx(t["bytes_per_dof"] * ndof)
+    assert rf["traffic_gbs"] == pytest.approx(t["bytes_per_dof"] * ndof / 0.6e-3 / 1e9, rel=1e-3)
     assert rf["kernel"] == t["kernel"]
     # excluding the dominant class moves to the next one; with flops dominating the bound is the ALU
     fs2 = _FakeSolver(11, {("residual", 10): {"launches": 5, "ms": 4.0, "bytes": 1e8, "flops": 4.0e9}})
