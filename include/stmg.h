@@ -94,7 +94,7 @@ void st_default_options(st_options* opt);
 /* Build the space-time hierarchy for the problem of Section 1 and allocate
  * its device workspace.  Coarsening follows Section 4 (mu_L = tau_L / h_L^2
  * against mu* of Remark chap4_remarkCriticalDiscretizationParameter) until
- * N_L = coarsest_steps.  cuda_stream: a cudaStream_t (NULL = default stream)
+ * N_L = coarsest_steps.  N is a power of 2 up to 32768.  cuda_stream: a cudaStream_t (NULL = default stream)
  * used by every later call on this handle.  On success *out owns the handle.
  * Errors: ST_EINVAL, ST_ENOMEM, ST_ECUDA. */
 int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* opt,

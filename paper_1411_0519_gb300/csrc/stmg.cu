@@ -1747,6 +1747,7 @@ const char* check_setup_args(const st_mesh* mesh, int p_t, int N, double T, cons
   if (mesh->n > 1023) return "mesh: n <= 1023";
   if (p_t < 0 || p_t > ST_MAX_PT) return "p_t out of range";
   if (!is_pow2(N)) return "N must be a power of 2";
+  if (N > 32768) return "N <= 32768 (the transfer and spatial kernels put the steps on the second grid axis)";
   if (!(T > 0.0) || !std::isfinite(T)) return "T must be positive";
   if (opt) o = *opt; else st_default_options(&o);
   if (o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) || o.maxit < 0 || !(o.rtol >= 0.0)) return "bad options";

@@ -72,6 +72,7 @@ def test_mu_star_of_the_plan_matches_the_printed_values(stmg, golden_dir):
 @pytest.mark.parametrize("args,opts", [
     ((2, 254, 1, 16, 1.0), {}), ((4, 7, 1, 16, 1.0), {}), ((2, 7, 1, 12, 1.0), {}), ((2, 2047, 1, 16, 1.0), {}),
     ((2, 7, 48, 16, 1.0), {}), ((2, 7, 1, 16, -1.0), {}), ((2, 7, 1, 16, 1.0), {"coarsest_steps": 32}),
+    ((1, 7, 1, 65536, 1.0), {}),
     ((2, 7, 1, 16, 1.0), {"gamma": 3}), ((2, 7, 4, 16, 1.0), {"smoother": "vcycle"}),
 ])
 def test_plan_rejects_what_setup_rejects(stmg, args, opts):
