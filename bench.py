@@ -10,10 +10,17 @@ L2, so no flush is needed between steps); f ~ U[-1,1] (seed 0 + rank),
 u0 = sin(pi x) sin(pi y).  The headline value is the plain FP64 solve; the
 mixed-precision form (FP32 V-cycles inside FP64 refinement) of the same solve
 is reported under "mixed".  Device time comes from CUDA events on the
-solver's stream; "e2e" repeats the solve through the same C ABI call with the
-inputs copied from pinned host memory and the solution copied back inside the
-timed region.  Kernel time per class comes from the library's event timing
-(st_profile_start/stop) over the timed region.
+solver's stream; "e2e" repeats the solve through st_solve_host with f and u0
+in pinned host memory and u written back to pinned host memory inside the
+timed region (the transform kernels read and write the host buffers over the
+CPU-GPU link).  Kernel time per class comes from the library's event timing
+(st_profile_start/stop) over the timed region; "roofline" evaluates the
+dominant class on the finest level against the measured peaks, with the DRAM
+traffic of its ncu capture (profiles/).  Further legs: the paper's inexact
+block inverse ("inexact_smoother"), the Example 2 protocol at p_t = 45
+("high_order"), the CPU oracle on a bounded sample ("cpu_baseline"), the SM
+clocks sampled during the timed region ("clocks"), and the time of one cycle
+("vcycle").
 
 Under torchrun every rank solves its own problem (no data-path collective,
 "scaling": "weak"); rank 0 prints one JSON line.
