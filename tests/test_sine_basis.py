@@ -114,3 +114,37 @@ def test_damped_step_on_tabulated_right_hand_side(p_t, adjoint):
         Wm = w * np.linalg.inv(A)
         out = Wm @ f + (lamM * (Wm @ sigma)) * t + (1 - w) * u
         assert np.allclose(out, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n", [63, 127, 255, 511])
+def test_dst_through_half_length_fft_equals_the_dense_transform(n):
+    """The steps of the register sine transform, restated with numpy's FFT:
+    pre-processing y_j = x_j (s_j + 1/2) + x_{Nf-j} (s_j - 1/2) (s_j = sin(j pi/Nf),
+    y_0 = 0), the half-length complex FFT Z of z_m = y_{2m} + i y_{2m+1}, the
+    even/odd split Y_k = 1/2 [A + (w_i - i w_r) B] (A = Z_k + conj Z_{H-k},
+    B = Z_k - conj Z_{H-k}, W^k = w_r + i w_i = e^{-2 pi i k / Nf}) and the
+    outputs X_{2k} = -Im Y_k, X_{2k+1} = sum_{c <= k} Re Y_c - Re Y_0 / 2, against
+    the dense unnormalised DST-I; also with the split's 1/2 moved into the
+    pre-processing weights, as the kernels do."""
+    Nf = n + 1
+    H = Nf // 2
+    x = np.zeros(Nf)
+    x[1:] = np.random.default_rng(n).uniform(-1, 1, n)
+    j = np.arange(Nf)
+    s = np.sin(j * np.pi / Nf)
+    xr = x[(Nf - j) % Nf]                    # x_{Nf - j}, with x_Nf = x_0 = 0
+    for half_in_pre in (False, True):
+        scale = 0.5 if half_in_pre else 1.0
+        y = x * scale * (s + 0.5) + xr * scale * (s - 0.5)
+        y[0] = 0.0
+        Z = np.fft.fft(y[0::2] + 1j * y[1::2])
+        k = np.arange(H)
+        Zc = np.conj(Z[(H - k) % H])
+        A, B = Z + Zc, Z - Zc
+        W = np.exp(-2j * np.pi * k / Nf)
+        Y = (0.5 if not half_in_pre else 1.0) * (A + (W.imag - 1j * W.real) * B)
+        X = np.zeros(Nf)
+        X[0::2] = -Y.imag
+        X[1::2] = np.cumsum(Y.real) - 0.5 * Y.real[0]
+        ref = dst_matrix(n) @ x[1:]
+        assert np.abs(X[1:] - ref).max() < 1e-12 * np.abs(ref).max()
