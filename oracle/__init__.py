@@ -26,6 +26,12 @@ Modules
   lfa        -- local Fourier mode analysis: symbols of L, S, R, P and the
                 two-grid iteration matrices (Section 3, Lemmas 17-29,
                 Theorems 5-6)
+  simplex    -- P1 on the paper's simplicial meshes (unit square in 4
+                triangles, unit cube in 12 tetrahedra, refined uniformly;
+                Section 4, Examples 1 and 2): assembly by quadrature and the
+                nested-space prolongation
+  mesh_multigrid -- the space-time hierarchy, coarsening rule and inexact
+                block inverse on those meshes (the cycle of ``multigrid``)
 
 Parity status: every function above is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` except the numerical values of the LFA two-grid
