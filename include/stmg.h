@@ -131,7 +131,10 @@ int st_level_info(const st_handle* h, int L, int* N_L, int* n_L, double* mu_L, i
 
 /* r = f + IC - L u on the finest level (system chap4_generalLinearSystem),
  * where IC adds psi_k(t_0^+) (M_h u0_ic) to block 1 (the n = 0 term of eq.
- * (equation1)); u0_ic may be NULL (zero initial value).  r may not alias u. */
+ * (equation1)); u0_ic may be NULL (zero initial value).  r may not alias u.
+ * Computed on nodes with the stencils of M_h and K_h at every p_t, by kernels
+ * that share nothing with the sine-basis cycle (an independent check of a
+ * solve's residual). */
 int st_residual(st_handle* h, const double* f, const double* u0_ic, const double* u, double* r);
 
 /* One V-cycle (gamma = 1, Section 2) on L u = f + IC for the finest level, in
@@ -244,10 +247,11 @@ int st_profile_level(const st_handle* h, int cls, int L, int* launches, double* 
  * device synchronisation of cudaMalloc / cudaFree.  It needs no handle.
  *
  * *out (a DEVICE pointer to one double) = ||x||_2 of n FP64 values at the
- * device pointer x, asynchronously on cuda_stream (NULL = default stream),
- * with the same deterministic two-stage sum of squares as st_norm2 (one
- * FP64 partial per chunk of 65536 elements, then one block adds them in a
- * fixed order).  It calls no allocator: the partial sums live in a fixed
+ * device pointer x, asynchronously on cuda_stream (NULL = default stream).
+ * The sum of squares is deterministic in its own fixed order (one FP64
+ * partial per contiguous chunk of 65536 elements, then one block adds the
+ * partials in a fixed order); st_norm2 adds in another fixed order, so the two
+ * agree to rounding.  It calls no allocator: the partial sums live in a fixed
  * 128 KB device array inside this library, which every GPU that loads the
  * library holds until the process exits.
  *  - n must not exceed ST_NOALLOC_MAX_ELEMENTS (2^30); larger n returns
@@ -259,7 +263,11 @@ int st_profile_level(const st_handle* h, int cls, int L, int* launches, double* 
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current) and caches it; make
  *    that first call before any stream capture.
- * Errors: ST_EINVAL, ST_ECUDA (address lookup or launch failed). */
+ *  - A CUDA error already pending on the calling thread makes the call return
+ *    ST_ECUDA without launching; the error is not cleared (it stays for the
+ *    caller's own check), and the launches' own status is read without
+ *    clearing it either.
+ * Errors: ST_EINVAL, ST_ECUDA (pending error, address lookup or launch failed). */
 #define ST_NOALLOC_MAX_ELEMENTS ((size_t)1 << 30)
 int st_norm2_noalloc(const double* x, size_t n, double* out, void* cuda_stream);
 

@@ -18,85 +18,15 @@
 #include "stmg.h"
 #include "stmg_kernels.cuh"
 #include "stmg_sine.cuh"
+#include "stmg_host_time.h"
 
 using stmg::TimeCoef;
 
 namespace {
 
-constexpr int kQmax = ST_MAX_PT + 1;
 constexpr int kQfix = 4;   // q <= kQfix: compile-time q kernels; above: the generic-q kernels
 
-// ---------------------------------------------------------------------------
-// Host-side time data in the Legendre basis (Section 1 definitions evaluated
-// in closed form for P_k on the reference slab):
-//   K_tau[k][l] = 1 - 2 [l < k and k - l odd]    (from int P_l P_k' = 2 there)
-//   M_tau[k][k] = tau / (2k + 1),  psi_k(start) = (-1)^k,  psi_k(end) = 1.
-// R1^T, R2^T (eq. chap4_restrictionTime) are the Legendre coefficients of the
-// coarse P_l restricted to each fine half, by Gauss-Legendre quadrature.
-// ---------------------------------------------------------------------------
-double legendre_P(int k, double s) {
-  double p0 = 1.0, p1 = s;
-  if (k == 0) return p0;
-  for (int m = 1; m < k; ++m) {
-    double p2 = ((2.0 * m + 1.0) * s * p1 - m * p0) / (m + 1.0);
-    p0 = p1;
-    p1 = p2;
-  }
-  return p1;
-}
-
-void gauss_legendre(int npts, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(npts, 0.0);
-  w.assign(npts, 0.0);
-  for (int i = 0; i < npts; ++i) {
-    double z = std::cos(M_PI * (i + 0.75) / (npts + 0.5));
-    for (int it = 0; it < 100; ++it) {
-      double p = legendre_P(npts, z), pm = legendre_P(npts - 1, z);
-      double dp = npts * (z * p - pm) / (z * z - 1.0);
-      double dz = p / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    double p = legendre_P(npts, z), pm = legendre_P(npts - 1, z);
-    double dp = npts * (z * p - pm) / (z * z - 1.0);
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-  }
-}
-
-struct HostTime {
-  int q;
-  double K[kQmax * kQmax], Mh[kQmax], st[kQmax], en[kQmax], R1[kQmax * kQmax], R2[kQmax * kQmax];
-};
-
-HostTime make_time(int p_t) {
-  HostTime t{};
-  const int q = p_t + 1;
-  t.q = q;
-  for (int k = 0; k < q; ++k) {
-    for (int l = 0; l < q; ++l) t.K[k * q + l] = (l < k && ((k - l) & 1)) ? -1.0 : 1.0;
-    t.Mh[k] = 1.0 / (2.0 * k + 1.0);
-    t.st[k] = (k & 1) ? -1.0 : 1.0;
-    t.en[k] = 1.0;
-  }
-  std::vector<double> gx, gw;
-  gauss_legendre(q + 2, gx, gw);
-  // RsT[k][l] = (2k+1)/2 int_{-1}^{1} P_l(c(s)) P_k(s) ds, c(s) = (s -+ 1)/2;
-  // R_s[k][l] = RsT[l][k] (coarse k <- fine l).
-  for (int k = 0; k < q; ++k) {
-    for (int l = 0; l < q; ++l) {
-      double a1 = 0.0, a2 = 0.0;
-      for (size_t g = 0; g < gx.size(); ++g) {
-        a1 += gw[g] * legendre_P(l, 0.5 * (gx[g] - 1.0)) * legendre_P(k, gx[g]);
-        a2 += gw[g] * legendre_P(l, 0.5 * (gx[g] + 1.0)) * legendre_P(k, gx[g]);
-      }
-      const double c = 0.5 * (2.0 * k + 1.0);
-      t.R1[l * q + k] = c * a1;   // transpose: row = coarse l, column = fine k
-      t.R2[l * q + k] = c * a2;
-    }
-  }
-  return t;
-}
+using namespace stmg_host;
 
 template <typename T, int Q>
 TimeCoef<T, Q> to_coef(const HostTime& t) {
@@ -112,29 +42,6 @@ TimeCoef<T, Q> to_coef(const HostTime& t) {
     c.en[i] = (T)t.en[i];
   }
   return c;
-}
-
-// (p, p+1) subdiagonal Pade approximation of exp(z) (textbook closed form);
-// mu* solves R(-3 mu) = sqrt(2) - 1 (Remark on the critical parameter).
-double pade(int p, double z) {
-  const int m = p, k = p + 1;
-  auto fact = [](int a) { double r = 1.0; for (int i = 2; i <= a; ++i) r *= i; return r; };
-  double num = 0.0, den = 0.0;
-  for (int j = 0; j <= m; ++j)
-    num += fact(m + k - j) * fact(m) / (fact(m + k) * fact(j) * fact(m - j)) * std::pow(z, j);
-  for (int j = 0; j <= k; ++j)
-    den += fact(m + k - j) * fact(k) / (fact(m + k) * fact(j) * fact(k - j)) * std::pow(-z, j);
-  return num / den;
-}
-
-double mu_star(int p) {
-  const double target = std::sqrt(2.0) - 1.0;
-  double lo = 0.0, hi = 1.0;
-  for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (pade(p, -3.0 * mid) > target) lo = mid; else hi = mid;
-  }
-  return 0.5 * (lo + hi);
 }
 
 template <typename T>
@@ -205,6 +112,8 @@ struct st_handle {
   int64_t npartial = 0;
   double* dnorm = nullptr;     // device result of a norm
   double* hnorm = nullptr;     // pinned host copy
+  unsigned* dmaxexp = nullptr;   // mixed form: largest biased exponent of the entry data (device)
+  int df_shift = 0;              // mixed form: the data enter the double-float transforms scaled by 2^df_shift
   double* coarse64_u = nullptr;  // mixed precision: FP64 copies for the coarsest solve
   double* coarse64_f = nullptr;
   double* coarse64_r = nullptr;
@@ -213,6 +122,8 @@ struct st_handle {
   double* u_dev = nullptr;        // st_solve_host: device solution buffer (allocated on first use)
   // generic-q kernels: Mh (1/(2k+1)), R1, R2 and R1, R2 times 2^d (prolongation), q x q row-major
   double* tt64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // q > kQfix: [K_tau | M_tau / tau | psi(t^+) | psi(t^-)] for the node-basis residual of st_residual
+  double* node_time64 = nullptr;
   float* tt32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::string err;
   // kernel timing
@@ -800,6 +711,22 @@ void launch_space_post_t(st_handle* h, const Level& lv, const SpaceLvl<T>& sl, c
     }                                                                            \
   } while (0)
 
+template <typename T, int D>
+void launch_residual_dyn_t(st_handle* h, const Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r,
+                           int s0, int ns) {
+  static_assert(sizeof(T) == 8, "the node-basis residual of high degree is FP64");
+  dim3 grid(blocks_for(lv.Nx), 1);
+  for (int c = 0; c < ns; c += 65535) {
+    grid.y = std::min(65535, ns - c);
+    if (adj)
+      stmg::k_residual_dyn<T, D, true><<<grid, kThreads, 0, h->stream>>>(
+          f, u, u0, r, lv.n, lv.N, s0 + c, h->q, (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), h->node_time64);
+    else
+      stmg::k_residual_dyn<T, D, false><<<grid, kThreads, 0, h->stream>>>(
+          f, u, u0, r, lv.n, lv.N, s0 + c, h->q, (T)lv.tau, (T)lv.h, (T)(1.0 / lv.h), h->node_time64);
+  }
+}
+
 template <typename T>
 void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T* u0, T* r, int s0 = 0,
               int ns = -1) {
@@ -811,6 +738,12 @@ void residual(st_handle* h, Level& lv, bool adj, const T* f, const T* u, const T
   const double fma = Q * (9.0 * D - 3.0) + Q + 3.0 * D + Q * Q + 2.0 * Q;
   Prof pr(h, ST_K_RESIDUAL, sizeof(T) * (3.0 * nodes * Q + (u0 ? (double)lv.Nx : 0.0)), 2.0 * fma * nodes, 1,
           level_of(h, lv));
+  if (Q > kQfix) {
+    if (sizeof(T) != 8 || h->node_time64 == nullptr || &lv != &h->levels.back())
+      fail(h, ST_EINVAL, "internal: the node-basis residual above q = 4 is FP64 on the finest level");
+    STMG_DISPATCH_D(launch_residual_dyn_t, h, lv, adj, f, u, u0, r, s0, ns);
+    return;
+  }
   STMG_DISPATCH(launch_residual_t, h, lv, adj, f, u, u0, r, s0, ns);
 }
 
@@ -1101,34 +1034,41 @@ void df_set_smem(st_handle* h) {
 
 template <int LP, int LG, typename SIN, typename SOUT>
 void df_launch_io(st_handle* h, const void* in, void* out, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
-                  stmg::DstTables<stmg::dfloat> dt, bool rows) {
+                  stmg::DstTables<stmg::dfloat> dt, bool rows, int load_exp, int store_exp) {
   using DF = stmg::dfloat;
   constexpr int G = 1 << LG;
   const int thr = dst_reg_threads<DF>();
   const unsigned grid = (unsigned)((nlines + thr / G - 1) / (thr / G));
   if (rows)
     stmg::k_dst_rows_reg<DF, LP, LG, SIN, SOUT><<<grid, thr, dst_reg_smem<DF, LP, LG>(), h->stream>>>(
-        in, out, n, nlines, scale, dt);
+        in, out, n, nlines, scale, dt, load_exp, store_exp);
   else
     stmg::k_dst_cols_reg<DF, LP, LG, SIN, SOUT><<<grid, thr, dst_cols_reg_smem<DF, LP, LG>(), h->stream>>>(
-        in, out, n, nlines, inner, scale, dt);
+        in, out, n, nlines, inner, scale, dt, load_exp, store_exp);
 }
 
-// first / last axis pass: FP64 in / out; between passes the 8-byte slots hold float pairs
+// first / last axis pass: FP64 in / out; between passes the 8-byte slots hold float pairs.
+// The first pass scales the FP64 input by 2^load_exp, the last the FP64 output by 2^store_exp.
 template <int LP, int LG>
 void df_launch(st_handle* h, const void* in, void* out, int n, int64_t nlines, int64_t inner, stmg::dfloat scale,
-               stmg::DstTables<stmg::dfloat> dt, bool rows, bool first, bool last) {
+               stmg::DstTables<stmg::dfloat> dt, bool rows, bool first, bool last, int load_exp, int store_exp) {
   using DF = stmg::dfloat;
-  if (first && last) df_launch_io<LP, LG, double, double>(h, in, out, n, nlines, inner, scale, dt, rows);
-  else if (first) df_launch_io<LP, LG, double, DF>(h, in, out, n, nlines, inner, scale, dt, rows);
-  else if (last) df_launch_io<LP, LG, DF, double>(h, in, out, n, nlines, inner, scale, dt, rows);
-  else df_launch_io<LP, LG, DF, DF>(h, in, out, n, nlines, inner, scale, dt, rows);
+  const int le = first ? load_exp : 0, se = last ? store_exp : 0;
+  if (first && last) df_launch_io<LP, LG, double, double>(h, in, out, n, nlines, inner, scale, dt, rows, le, se);
+  else if (first) df_launch_io<LP, LG, double, DF>(h, in, out, n, nlines, inner, scale, dt, rows, le, se);
+  else if (last) df_launch_io<LP, LG, DF, double>(h, in, out, n, nlines, inner, scale, dt, rows, le, se);
+  else df_launch_io<LP, LG, DF, DF>(h, in, out, n, nlines, inner, scale, dt, rows, le, se);
 }
 
-// scale * DST-I along every axis of `slabs` FP64 fields, computed in double-float
-// (src / mid / dst as in dst_axes).
+// Whether the mixed form's boundary transforms of the finest level run in double-float.
+bool df_transforms(const st_handle* h, const Level& lv) {
+  return h->opt.precision == ST_MIXED && df_len(lv.n + 1) && lv.tdf.sinp != nullptr;
+}
+
+// 2^load_exp * scale * DST-I along every axis of `slabs` FP64 fields, computed in
+// double-float (src / mid / dst as in dst_axes), the FP64 result times 2^store_exp.
 void dst_axes_df(st_handle* h, Level& lv, const double* src, double* mid, double* dst, int64_t slabs,
-                 double axis_scale) {
+                 double axis_scale, int load_exp, int store_exp) {
   const int n = lv.n, Nf = n + 1;
   if (!df_len(Nf) || lv.tdf.sinp == nullptr) {
     dst_axes<double>(h, lv, src, mid, dst, slabs, axis_scale);
@@ -1144,10 +1084,14 @@ void dst_axes_df(st_handle* h, Level& lv, const double* src, double* mid, double
     const void* in = first ? (const void*)src : (const void*)mid;
     void* out = last ? (void*)dst : (void*)mid;
     switch (Nf) {
-      case 64: df_launch<3, 2>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
-      case 128: df_launch<3, 3>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
-      case 256: df_launch<4, 3>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
-      default: df_launch<4, 4>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last); break;
+      case 64: df_launch<3, 2>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last, load_exp, store_exp);
+        break;
+      case 128: df_launch<3, 3>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last, load_exp, store_exp);
+        break;
+      case 256: df_launch<4, 3>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last, load_exp, store_exp);
+        break;
+      default: df_launch<4, 4>(h, in, out, n, nlines, inner, scale, lv.tdf, rows, first, last, load_exp, store_exp);
+        break;
     }
     inner *= n;
   }
@@ -1533,11 +1477,43 @@ struct CycleInputs {
 
 // Basis change of the finest-level FP64 vectors at the boundary of a solve: in
 // FP64, or in double-float on the FP32 pipe for the mixed form.
+// The double-float transforms take the data scaled by 2^df_shift on entry and
+// undo the scaling on exit (inverse).
 void boundary_dst(st_handle* h, const double* src, double* mid, double* dst, int64_t slabs, bool inverse) {
   Level& lv = finest(h);
   const double sc = inverse ? 2.0 / (lv.n + 1) : 1.0;
-  if (h->opt.precision == ST_MIXED) dst_axes_df(h, lv, src, mid, dst, slabs, sc);
+  if (h->opt.precision == ST_MIXED)
+    dst_axes_df(h, lv, src, mid, dst, slabs, sc, inverse ? 0 : h->df_shift, inverse ? -h->df_shift : 0);
   else dst_axes<double>(h, lv, src, mid, dst, slabs, sc);
+}
+
+// Mixed form: the double-float pairs have the FP32 exponent range, so data whose
+// largest magnitude lies outside 2^-64 ... 2^64 enter the transforms scaled by the
+// power of two that brings it into [1, 2) (exact; every later step is linear, so
+// the cycles solve the scaled problem and the inverse transform undoes the scale).
+// Sets h->df_shift from the finite entries of f, u0 and u (u0, u may be null);
+// reads one device word back (synchronises the stream).
+void choose_df_shift(st_handle* h, const double* f, const double* u0, const double* u) {
+  Level& lv = finest(h);
+  h->df_shift = 0;
+  if (!df_transforms(h, lv)) return;
+  check(h, cudaMemsetAsync(h->dmaxexp, 0, sizeof(unsigned), h->stream), "memset");
+  auto scan = [&](const double* x, int64_t n) {
+    if (x == nullptr || n == 0) return;
+    Prof pr(h, ST_K_VECTOR, 8.0 * (double)n, 0.0);
+    stmg::k_max_exponent<<<(unsigned)std::min<int64_t>(blocks_for(n), 152 * 8), kThreads, 0, h->stream>>>(
+        x, n, h->dmaxexp);
+  };
+  scan(f, lv.ndof);
+  scan(u0, lv.Nx);
+  scan(u, lv.ndof);
+  unsigned emax = 0;
+  check(h, cudaMemcpyAsync(h->hnorm, h->dmaxexp, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream), "copy");
+  check(h, cudaStreamSynchronize(h->stream), "sync");
+  std::memcpy(&emax, h->hnorm, sizeof(unsigned));
+  if (emax == 0u) return;                            // all entries zero (or FP64 subnormal)
+  const int e = (int)emax - 1023;                    // 2^e <= max |x| < 2^(e+1)
+  if (e < -64 || e > 64) h->df_shift = -e;
 }
 void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
   boundary_dst(h, data, data, data, slabs, inverse);
@@ -1545,6 +1521,7 @@ void boundary_dst(st_handle* h, double* data, int64_t slabs, bool inverse) {
 
 CycleInputs enter_cycle_basis(st_handle* h, const double* f, const double* u0, double* u, bool u_given) {
   Level& lv = finest(h);
+  choose_df_shift(h, f, u0, u_given ? u : nullptr);
   if (lv.n + 1 >= 64 && lv.n + 1 <= 512) {   // the register transforms read f and write the handle's copy
     boundary_dst(h, f, lv.v64.f, lv.v64.f, (int64_t)lv.N * h->q, false);
   } else {
@@ -1659,22 +1636,17 @@ int solve_host_impl(st_handle* h, const double* f, const double* u0, double* u, 
   CycleInputs in{lv.v64.f, nullptr};
   if (u0) {
     check(h, cudaMemcpyAsync(h->u0m, u0, sizeof(double) * lv.Nx, cudaMemcpyHostToDevice, h->stream), "copy u0");
-    if (md) boundary_dst(h, h->u0m, 1, false);
     in.u0 = h->u0m;
   }
-  if (fv) {
-    boundary_dst(h, fv, lv.v64.f, lv.v64.f, slabs, false);
-  } else {
-    check(h, cudaMemcpyAsync(lv.v64.f, f, bytes, cudaMemcpyHostToDevice, h->stream), "copy f");
-    if (md) boundary_dst(h, lv.v64.f, slabs, false);
-  }
+  if (!fv) check(h, cudaMemcpyAsync(lv.v64.f, f, bytes, cudaMemcpyHostToDevice, h->stream), "copy f");
+  if (given && !uv) check(h, cudaMemcpyAsync(h->u_dev, u, bytes, cudaMemcpyHostToDevice, h->stream), "copy u");
+  choose_df_shift(h, fv ? fv : lv.v64.f, in.u0, given ? (uv ? (const double*)uv : h->u_dev) : nullptr);
+  if (u0 && md) boundary_dst(h, h->u0m, 1, false);
+  if (fv) boundary_dst(h, fv, lv.v64.f, lv.v64.f, slabs, false);
+  else if (md) boundary_dst(h, lv.v64.f, slabs, false);
   if (given) {
-    if (uv) {
-      boundary_dst(h, uv, h->u_dev, h->u_dev, slabs, false);
-    } else {
-      check(h, cudaMemcpyAsync(h->u_dev, u, bytes, cudaMemcpyHostToDevice, h->stream), "copy u");
-      if (md) boundary_dst(h, h->u_dev, slabs, false);
-    }
+    if (uv) boundary_dst(h, uv, h->u_dev, h->u_dev, slabs, false);
+    else if (md) boundary_dst(h, h->u_dev, slabs, false);
   }
   const int status = solve_core(h, false, in, h->u_dev, given, iters, relres);
   if (uv) {
@@ -1885,6 +1857,17 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
           upload(h, h->tt32[i], *src[i]);
         }
       }
+      if (q > kQfix) {
+        std::vector<double> nt(q * q + 3 * q);
+        for (int e = 0; e < q * q; ++e) nt[e] = h->tm.K[e];
+        for (int k = 0; k < q; ++k) {
+          nt[q * q + k] = h->tm.Mh[k];
+          nt[q * q + q + k] = h->tm.st[k];
+          nt[q * q + 2 * q + k] = h->tm.en[k];
+        }
+        h->node_time64 = dalloc<double>(h, nt.size());
+        upload(h, h->node_time64, nt);
+      }
     }
     dst_set_smem_limits<double>(h);
     if (mixed) {
@@ -1907,6 +1890,7 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
       h->partial = dalloc<double>(h, h->npartial);
     }
     h->dnorm = dalloc<double>(h, 1);
+    h->dmaxexp = reinterpret_cast<unsigned*>(dalloc<double>(h, 1));
     check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");
     check(h, cudaDeviceSynchronize(), "setup sync");
     return ST_OK;
@@ -1975,17 +1959,7 @@ int st_residual(st_handle* h, const double* f, const double* u0_ic, const double
   return guarded(h, [&]() -> int {
     if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
     Level& lv = finest(h);
-    if (h->q > kQfix) {   // no node-basis kernels for large q: through the sine basis
-      const int64_t slabs = (int64_t)lv.N * h->q;
-      copy<double>(h, lv.v64.r, u, lv.ndof);
-      to_modal<double>(h, lv, lv.v64.r, slabs);
-      const CycleInputs in = enter_cycle_basis(h, f, u0_ic, lv.v64.r, false);
-      mresidual<double>(h, lv, false, in.f, lv.v64.r, in.u0, r);
-      from_modal<double>(h, lv, r, slabs);
-      after_launch(h);
-      return ST_OK;
-    }
-    residual<double>(h, lv, false, f, u, u0_ic, r);
+    residual<double>(h, lv, false, f, u, u0_ic, r);   // on nodes, for every q
     after_launch(h);
     return ST_OK;
   });

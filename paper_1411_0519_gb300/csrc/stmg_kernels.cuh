@@ -201,6 +201,60 @@ __global__ void k_residual(const T* __restrict__ f, const T* __restrict__ u,
 }
 
 // ---------------------------------------------------------------------------
+// The residual of k_residual for any q <= kNodeQmax, on nodes: the time
+// matrices come from a table tab = [K_tau (q x q, row-major) | M_tau / tau (q) |
+// psi_k(t_{n-1}^+) (q) | psi_k(t_n^-) (q)] instead of template parameters.  It
+// is the node-basis residual of st_residual at high time degree, independent of
+// the sine-basis kernels of the cycle; per (node, step) it keeps M_h u and K_h u
+// of every time dof in local memory.
+// ---------------------------------------------------------------------------
+constexpr int kNodeQmax = 48;
+
+template <typename T, int D, bool ADJ>
+__global__ void k_residual_dyn(const T* __restrict__ f, const T* __restrict__ u, const T* __restrict__ u0,
+                               T* __restrict__ r, int n, int N, int s0, int q, T tau, T h, T hinv,
+                               const T* __restrict__ tab) {
+  const int64_t Nx = (D == 1) ? n : (D == 2) ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N || q > kNodeQmax) return;
+  const T* K = tab;
+  const T* Mh = tab + q * q;
+  const T* st = Mh + q;
+  const T* en = st + q;
+  int ix, iy, iz;
+  node_coords(j, n, D, ix, iy, iz);
+  Stencil<T, D> S(h, hinv);
+  T mu[kNodeQmax], ku[kNodeQmax];
+  for (int l = 0; l < q; ++l) {
+    const T* ul = u + ((int64_t)s * q + l) * Nx;
+    apply_mk<T, D>(S, n, ix, iy, iz, [&](int64_t x) { return ul[x]; }, mu[l], ku[l]);
+  }
+  T mt = T(0);
+  const T* nb = nullptr;                       // neighbouring step (forward: s-1, adjoint: s+1)
+  if (!ADJ && s > 0) nb = u + (int64_t)(s - 1) * q * Nx;
+  if (ADJ && s < N - 1) nb = u + (int64_t)(s + 1) * q * Nx;
+  if (nb != nullptr) {
+    const T* w = ADJ ? st : en;
+    mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t x) {
+      T t = T(0);
+      for (int l = 0; l < q; ++l) t += w[l] * nb[(int64_t)l * Nx + x];
+      return t;
+    });
+  } else if (!ADJ && s == 0 && u0 != nullptr) {
+    mt = apply_m<T, D>(S, n, ix, iy, iz, [&](int64_t x) { return u0[x]; });
+  }
+  for (int k = 0; k < q; ++k) {
+    const int64_t idx = ((int64_t)s * q + k) * Nx + j;
+    T acc = f[idx];
+    for (int l = 0; l < q; ++l) acc -= (ADJ ? K[l * q + k] : K[k * q + l]) * mu[l];
+    acc -= tau * Mh[k] * ku[k];
+    acc += (ADJ ? en[k] : st[k]) * mt;
+    r[idx] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // 2D residual with a shared-memory tile (same result as k_residual<T, 2, Q, ADJ>).
 // A CTA owns a TX x TY block of nodes of one time step.  It stages u (Q fields)
 // and the coupling trace of the neighbouring step on the tile plus a one-node
@@ -376,10 +430,15 @@ __device__ __forceinline__ void double_words(double x, unsigned& hi, unsigned& l
   asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
 }
 
-__device__ __forceinline__ dfloat split_double(double x) {
+// eshift (split_double): an exact power-of-two scaling folded into the split,
+// x 2^eshift, applied to the biased exponent of finite nonzero x; the callers
+// choose it so that the data's largest magnitude lies near 1 when it would
+// otherwise leave the FP32 range (see k_max_exponent).
+__device__ __forceinline__ dfloat split_double(double x, int eshift = 0) {
   unsigned h32, l32;
   double_words(x, h32, l32);
-  const int E = (int)((h32 >> 20) & 0x7ffu);   // biased exponent
+  int E = (int)((h32 >> 20) & 0x7ffu);   // biased exponent
+  if (E != 0 && E != 2047) E += eshift;
   const unsigned sign = h32 & 0x80000000u;
   if (E < 897) return dfloat(__uint_as_float(sign), 0.f);   // zero, or below the FP32 normal range
   if (E > 1150) {                                             // beyond FP32: infinity, or NaN
@@ -393,9 +452,11 @@ __device__ __forceinline__ dfloat split_double(double x) {
   const float hi = __uint_as_float((sign | ((unsigned)(E - 896) << 23) | m23) + up);
   // x - hi = (rem - up 2^29) 2^(E - 1075) on the magnitude: an integer m of at most
   // 28 bits, converted by FP32 arithmetic: its two 14-bit halves are exact floats
-  // (2^23 + v read as a float, minus 2^23), and one FMA rounds m = hi 2^14 + lo;
-  // the scale 2^(E - 1075) is applied in one step, or (E < 949, where it is not a
-  // normal float) as 2^(E - 1011) and then 2^-64, rounding once into the subnormals
+  // (2^23 + v read as a float, minus 2^23), and one FMA rounds m = hi 2^14 + lo to
+  // 24 bits; the scale 2^(E - 1075) is then applied in one exact step, or (E < 949,
+  // where it is not a normal float) as 2^(E - 1011) and then 2^-64, which rounds a
+  // second time, into the subnormals: lo is then within one subnormal ulp (2^-149)
+  // of the 24-bit rounding of x - hi, far below the pair's relative accuracy
   const int r = (int)rem - (int)(up << 29);
   const unsigned m = (unsigned)(r < 0 ? -r : r);
   const float mh = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 14)), 8388608.f);
@@ -416,15 +477,39 @@ __device__ __forceinline__ double float_bits_to_double(float f) {
   return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// Storage conversions of the transforms.  For the double-float type the FP64
+// data are scaled on the way in by 2^load_exp (exactly, in the split) and on
+// the way out by 2^store_exp (one FP64 multiplication, only when store_exp is
+// not zero); the other types ignore both.
 template <typename T, typename S>
-__device__ __forceinline__ T load_as(S x) { return x; }
+__device__ __forceinline__ T load_as(S x, int load_exp = 0) { return x; }
 template <>
-__device__ __forceinline__ dfloat load_as<dfloat, double>(double x) { return split_double(x); }
+__device__ __forceinline__ dfloat load_as<dfloat, double>(double x, int load_exp) {
+  return split_double(x, load_exp);
+}
 template <typename S, typename T>
-__device__ __forceinline__ S store_as(T x) { return x; }
+__device__ __forceinline__ S store_as(T x, int store_exp = 0) { return x; }
 template <>
-__device__ __forceinline__ double store_as<double, dfloat>(dfloat x) {
-  return float_bits_to_double(x.hi) + float_bits_to_double(x.lo);   // one FP64 operation
+__device__ __forceinline__ double store_as<double, dfloat>(dfloat x, int store_exp) {
+  const double v = float_bits_to_double(x.hi) + float_bits_to_double(x.lo);   // one FP64 operation
+  // 2^store_exp as an FP64 encoding; |store_exp| <= 1022 by construction (k_max_exponent)
+  return store_exp == 0 ? v : v * __hiloint2double((1023 + store_exp) << 20, 0);
+}
+
+// Largest biased FP64 exponent among the finite entries of x (0 for all zeros),
+// combined into *out by atomicMax (*out must start at 0).  Integer operations
+// on the high word only: no FP64 instruction.
+__global__ void k_max_exponent(const double* __restrict__ x, int64_t n, unsigned* __restrict__ out) {
+  unsigned m = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned hw, lw;
+    double_words(x[i], hw, lw);
+    const unsigned E = (hw >> 20) & 0x7ffu;
+    if (E != 0x7ffu && E > m) m = E;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(out, m);
 }
 
 template <typename T>
@@ -783,7 +868,8 @@ __device__ __forceinline__ void dst_reg_row(T* bre, T* bim, int g, const T* sm) 
 // last write).
 template <typename T, int LP, int LG, typename SIN = T, typename SOUT = SIN>
 __global__ void __launch_bounds__(256) k_dst_rows_reg(const void* src_data, void* dst_data, int n, int64_t nrows,
-                                                      T scale, DstTables<T> tb) {
+                                                      T scale, DstTables<T> tb, int load_exp = 0,
+                                                      int store_exp = 0) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int BS = Lay::BS, RS = Lay::RS;
   extern __shared__ unsigned char smem_raw[];
@@ -800,7 +886,7 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(const void* src_data, void
     T* br = rows + r * RS;
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
-      br[(j & 1) * BS + (j >> 1)] = load_as<T, SIN>(src[c]);
+      br[(j & 1) * BS + (j >> 1)] = load_as<T, SIN>(src[c], load_exp);
     }
     if (lane == 0) br[0] = T(0);
   }
@@ -815,7 +901,7 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(const void* src_data, void
     for (int c = lane; c < n; c += 32) {
       const int j = c + 1;
       const T v = br[(j & 1) * BS + (j >> 1)];
-      dst[c] = store_as<SOUT, T>(unit ? v : scale * v);
+      dst[c] = store_as<SOUT, T>(unit ? v : scale * v, store_exp);
     }
   }
 }
@@ -829,7 +915,8 @@ __global__ void __launch_bounds__(256) k_dst_rows_reg(const void* src_data, void
 // followed by one int64 line base per line.
 template <typename T, int LP, int LG, typename SIN = T, typename SOUT = SIN>
 __global__ void __launch_bounds__(256) k_dst_cols_reg(const void* src_data, void* dst_data, int n, int64_t nlines,
-                                                      int64_t inner, T scale, DstTables<T> tb) {
+                                                      int64_t inner, T scale, DstTables<T> tb, int load_exp = 0,
+                                                      int store_exp = 0) {
   using Lay = DstRegLayout<LP, LG>;
   constexpr int BS = Lay::BS, RS = Lay::RS;
   extern __shared__ unsigned char smem_raw[];
@@ -852,7 +939,7 @@ __global__ void __launch_bounds__(256) k_dst_cols_reg(const void* src_data, void
     if (r < rcount) {
       const int j = c + 1;
       rows[r * RS + (j & 1) * BS + (j >> 1)] =
-          load_as<T, SIN>(reinterpret_cast<const SIN*>(src_data)[base[r] + (int64_t)c * inner]);
+          load_as<T, SIN>(reinterpret_cast<const SIN*>(src_data)[base[r] + (int64_t)c * inner], load_exp);
     }
   }
   if (tid < rpc) rows[tid * RS] = T(0);
@@ -866,7 +953,8 @@ __global__ void __launch_bounds__(256) k_dst_cols_reg(const void* src_data, void
     if (r < rcount) {
       const int j = c + 1;
       const T v = rows[r * RS + (j & 1) * BS + (j >> 1)];
-      reinterpret_cast<SOUT*>(dst_data)[base[r] + (int64_t)c * inner] = store_as<SOUT, T>(unit ? v : scale * v);
+      reinterpret_cast<SOUT*>(dst_data)[base[r] + (int64_t)c * inner] =
+          store_as<SOUT, T>(unit ? v : scale * v, store_exp);
     }
   }
 }

@@ -4,9 +4,12 @@
 // all of a GPU's memory to its own allocator at start-up and forbids later
 // cudaMalloc, or a code path that must not take the implicit device
 // synchronisation that cudaMalloc / cudaFree may perform.  For them
-// st_norm2_noalloc computes the same deterministic two-stage sum of squares
-// as st_norm2, without a handle (creating one allocates) and with its
-// partial sums in a fixed file-scope device array instead of handle workspace.
+// st_norm2_noalloc computes the l2 norm that st_norm2 computes, without a
+// handle (creating one allocates) and with its partial sums in a fixed
+// file-scope device array instead of handle workspace.  Its sum of squares is
+// deterministic in its own fixed order -- one partial per contiguous chunk of
+// kNoallocChunk elements, then one block adds the partials -- which is not the
+// order of st_norm2 (a fixed grid-stride split), so the two agree to rounding.
 //
 // Limits and sharing rules (also stated in include/stmg.h):
 //  * the scratch holds kNoallocPartials FP64 partial sums (128 KB per GPU that
@@ -19,7 +22,12 @@
 //    cleared between calls;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current) and caches it; make that
-//    first call before any stream capture.
+//    first call before any stream capture;
+//  * a CUDA error that is already pending on the calling thread (from earlier,
+//    unrelated work) is neither cleared nor attributed to a launch here: the
+//    call returns ST_ECUDA before launching anything and leaves the error for
+//    the caller's own check; launch failures of its own kernels are read with
+//    cudaPeekAtLastError, which does not clear them either.
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -110,12 +118,14 @@ int scratch_for_current_device(double** out) {
 extern "C" int st_norm2_noalloc(const double* x, size_t n, double* out, void* cuda_stream) {
   if (x == nullptr || out == nullptr) return ST_EINVAL;
   if (n > (size_t)ST_NOALLOC_MAX_ELEMENTS) return ST_EINVAL;   // beyond the scratch capacity
+  if (cudaPeekAtLastError() != cudaSuccess) return ST_ECUDA;   // an earlier error, left pending for its owner
   double* scratch = nullptr;
   const int rc = scratch_for_current_device(&scratch);
   if (rc != ST_OK) return rc;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   const int np = n == 0 ? 1 : (int)((n + kNoallocChunk - 1) / kNoallocChunk);
   k_noalloc_sumsq<<<np, kThreads, 0, stream>>>(x, (int64_t)n, scratch);
+  if (cudaPeekAtLastError() != cudaSuccess) return ST_ECUDA;
   k_noalloc_finish<<<1, 1024, 0, stream>>>(scratch, np, out);
-  return cudaGetLastError() == cudaSuccess ? ST_OK : ST_ECUDA;
+  return cudaPeekAtLastError() == cudaSuccess ? ST_OK : ST_ECUDA;
 }

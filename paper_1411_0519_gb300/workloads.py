@@ -57,6 +57,16 @@ def uniform_load(d, n, p_t, N, seed=0):
     return rng.uniform(-1.0, 1.0, size=shape(d, n, p_t, N))
 
 
+def uniform_load_steps(d, n, p_t, N, s0, s1, seed=0):
+    """Time steps [s0, s1) of uniform_load(d, n, p_t, N, seed), drawn without the
+    others: the generator (one 64-bit draw per FP64 value) is advanced past the
+    entries of the first s0 steps."""
+    per_step = (p_t + 1) * n ** d
+    rng = np.random.default_rng(seed)
+    rng.bit_generator.advance(s0 * per_step)
+    return rng.uniform(-1.0, 1.0, size=(s1 - s0, p_t + 1) + (n,) * d)
+
+
 def uniform_iterate(d, n, p_t, N, seed=0):
     """Random initial iterate with entries in [0, 1] (two-grid protocol)."""
     rng = np.random.default_rng(seed)

@@ -4,10 +4,13 @@ every level, solves and adjoint solves -- and the Example 2 protocol
 (tau = 1, f = 0, u^0 ~ U[0, 1], eps = 1e-8) against the oracle's counts and
 the printed table.
 
-Tolerances: single steps 1e-11, solves 1e-9 relative to the largest entry
-(the q x q blocks at q = 46 have condition numbers near 1e4, and the oracle
-assembles K_tau by quadrature, which matches the closed form the library
-uses to about 1e-13)."""
+Tolerances: single steps 1e-11; solves 1e-10 relative to the largest entry at
+every degree, as in the FP64 parity tests (the q x q blocks at q = 46 have
+condition numbers near 1e4 and the oracle's quadrature K_tau matches the
+library's closed form to about 1e-13, so a few 1e-10 would be the worst case;
+the measured differences stay below 1e-12).  The residual of a solve is
+recomputed on nodes by st_residual (stencils, no sine transform) and by the
+oracle's operator."""
 import os
 
 import numpy as np
@@ -70,19 +73,24 @@ def test_solves_and_gradients(case):
     disc = case.H.finest.disc
     f = rand(disc.shape(), 80)
     u0 = workloads.smooth_ic(case.d, case.n, seed=81)
+    tol = 1e-10
     u, it, rr = s.solve(to_gpu(f), to_gpu(u0))
     uo, ito, _ = multigrid.solve(case.H, spacetime.add_ic(disc, f, u0), rtol=1e-10, maxit=60)
     assert abs(it - ito) <= 1 and rr <= 1e-10
-    assert rel_err(to_np(u), uo) < 1e-9
-    r = s.residual(to_gpu(f), u, to_gpu(u0))
+    err = rel_err(to_np(u), uo)
+    print(f"p_t={case.p_t}: solve against the oracle {err:.2e} (tolerance {tol:g})")
+    assert err < tol
+    r = s.residual(to_gpu(f), u, to_gpu(u0))      # on nodes, independent of the sine basis
     ro = case.H.finest.residual(to_np(u).reshape(disc.shape()), spacetime.add_ic(disc, f, u0))
     assert np.abs(to_np(r).reshape(ro.shape) - ro).max() <= 1e-11 * np.abs(f).max()
+    g = spacetime.add_ic(disc, f, u0)
+    assert np.linalg.norm(ro) <= 1.5e-10 * np.linalg.norm(g)
     lam, gu0, ita, rra = s.adjoint_solve(to_gpu(f))
     lo, itoa, _ = multigrid.solve(case.H, f, rtol=1e-10, maxit=60, adjoint=True)
-    assert abs(ita - itoa) <= 1 and rel_err(to_np(lam), lo) < 1e-9
+    assert abs(ita - itoa) <= 1 and rel_err(to_np(lam), lo) < tol
     start = (-1.0) ** np.arange(disc.q)
     go = disc.Mh @ (start @ lo[0].reshape(disc.q, disc.Nx))
-    assert rel_err(to_np(gu0), go) < 1e-9
+    assert rel_err(to_np(gu0), go) < tol
 
 
 def test_high_order_mixed_precision_against_fp64():

@@ -10,7 +10,9 @@
   operator on sampled steps; the full oracle adjoint on a reduced grid.
 * heat3d_63 (384M unknowns, p_t = 2) and heat2d_511 (1.07B unknowns, mu
   sweep across mu*): mixed precision against plain FP64 on the GPU, forward
-  and adjoint; the error of the mixed result is printed and bounded.
+  and adjoint, and the mixed solution's residual recomputed by the oracle's
+  operators A, B on sampled time steps (each sampled step's residual must lie
+  within the solve's global tolerance); the errors are printed and bounded.
 """
 import numpy as np
 import pytest
@@ -171,11 +173,35 @@ def test_adjoint_gradients_match_oracle_reduced_grid():
     s.close()
 
 
+def _sampled_oracle_residuals(w, f_np, u, samples, rtol, adjoint=False):
+    """Oracle residuals f_k - A u_k - B u_{k-1} (adjoint: f_k - A^T u_k - B^T u_{k+1})
+    of the GPU vector u on sampled steps k (u0 = 0); each must satisfy
+    ||r_k|| <= rtol ||f|| (the whole residual does).  Returns the relative values."""
+    d, n, p, N, T = w["d"], w["n"], w["p_t"], w["N"], w["T"]
+    disc = spacetime.Discretization(d, n, p, 1, T / N)
+    f2 = f_np.reshape(N, -1)
+    fn = np.linalg.norm(f2)
+    shape = (N, p + 1) + (n,) * d
+    out = []
+    for k in samples:
+        nb = k + 1 if adjoint else k - 1
+        idx = [k] + ([nb] if 0 <= nb < N else [])
+        rows = _steps(u, idx, shape)
+        if adjoint:
+            rk = f2[k] - disc.A.T @ rows[0] - (disc.B.T @ rows[1] if len(idx) > 1 else 0.0)
+        else:
+            rk = f2[k] - disc.A @ rows[0] - (disc.B @ rows[1] if len(idx) > 1 else 0.0)
+        out.append(np.linalg.norm(rk) / fn)
+        assert np.linalg.norm(rk) <= rtol * fn, (k, np.linalg.norm(rk) / fn)
+    return out
+
+
 def test_heat3d_63_mixed_against_fp64():
     require_gpu()
     w = workloads.WORKLOADS["heat3d_63"]
     d, n, p, N, T = w["d"], w["n"], w["p_t"], w["N"], w["T"]
-    f = to_gpu(workloads.gaussian_load(d, n, p, N, T, seed=0))
+    f_np = workloads.gaussian_load(d, n, p, N, T, seed=0)
+    f = to_gpu(f_np)
     s64 = _solver(w, rtol=1e-8, maxit=60, precision="fp64")
     u64, it64, rr64 = s64.solve(f)
     s64.close()
@@ -184,7 +210,10 @@ def test_heat3d_63_mixed_against_fp64():
     smx.close()
     assert rr64 <= 1e-8 and rrm <= 1e-8
     err = ((umx - u64).norm() / u64.norm()).item()
-    print(f"heat3d_63: fp64 {it64} cycles, mixed {itm} refinement steps, ||u_mixed - u_fp64|| / ||u_fp64|| = {err:.2e}")
+    rs = _sampled_oracle_residuals(w, f_np, umx, [0, 1, N // 2, N - 1], 1e-8)
+    print(f"heat3d_63: fp64 {it64} cycles, mixed {itm} refinement steps, ||u_mixed - u_fp64|| / ||u_fp64|| = "
+          f"{err:.2e}; oracle residual of the mixed solution on sampled steps / ||f||: "
+          + ", ".join(f"{v:.1e}" for v in rs))
     assert err < 1e-5
 
 
@@ -195,7 +224,8 @@ def test_heat2d_511_mu_sweep_mixed_forward_and_adjoint(mu):
     w = dict(workloads.WORKLOADS["heat2d_511"])
     w["T"] = mu / 128.0                      # mu = tau / h^2 = 128 T on the finest level
     d, n, p, N, T = w["d"], w["n"], w["p_t"], w["N"], w["T"]
-    f = to_gpu(workloads.uniform_load(d, n, p, N, seed=0))
+    f_np = workloads.uniform_load(d, n, p, N, seed=0)
+    f = to_gpu(f_np)
     s64 = _solver(w, rtol=1e-8, maxit=80, precision="fp64")
     kinds = [s64.level_info(L)["full"] for L in range(s64.num_levels - 1)]
     u64, it64, rr64 = s64.solve(f)
@@ -209,8 +239,12 @@ def test_heat2d_511_mu_sweep_mixed_forward_and_adjoint(mu):
     assert max(rr64, rra64, rrm, rram) <= 1e-8
     eu = ((umx - u64).norm() / u64.norm()).item()
     el = ((lammx - lam64).norm() / lam64.norm()).item()
+    samples = [0, 1, N // 2, N - 1]
+    rs = _sampled_oracle_residuals(w, f_np, umx, samples, 1e-8)
+    ra = _sampled_oracle_residuals(w, to_np(u64).reshape(-1), lammx, samples, 1e-8, adjoint=True)
     print(f"heat2d_511 mu={mu}: levels full/semi {kinds}; fp64 {it64}/{ita64}, mixed {itm}/{itam}; "
-          f"forward err {eu:.2e}, adjoint err {el:.2e}")
+          f"forward err {eu:.2e}, adjoint err {el:.2e}; oracle residuals on sampled steps / ||rhs||: forward "
+          + ", ".join(f"{v:.1e}" for v in rs) + "; adjoint " + ", ".join(f"{v:.1e}" for v in ra))
     assert eu < 1e-5 and el < 1e-5
     del u64, lam64, umx, lammx
     torch.cuda.empty_cache()
