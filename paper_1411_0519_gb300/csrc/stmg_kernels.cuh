@@ -499,7 +499,7 @@ __device__ __forceinline__ double store_as<double, dfloat>(dfloat x, int store_e
 // Largest biased FP64 exponent among the finite entries of x (0 for all zeros),
 // combined into *out by atomicMax (*out must start at 0).  Integer operations
 // on the high word only: no FP64 instruction.
-__global__ void k_max_exponent(const double* __restrict__ x, int64_t n, unsigned* __restrict__ out) {
+static __global__ void k_max_exponent(const double* __restrict__ x, int64_t n, unsigned* __restrict__ out) {
   unsigned m = 0u;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     unsigned hw, lw;

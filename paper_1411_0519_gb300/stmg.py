@@ -32,6 +32,12 @@ EXPORTS = [
     "st_plan",
 ]
 
+MESH_EXPORTS = [
+    "stm_setup", "stm_destroy", "stm_last_error", "stm_ndof", "stm_num_levels", "stm_nodes", "stm_level_info",
+    "stm_residual", "stm_vcycle", "stm_solve", "stm_adjoint_solve", "stm_level_residual", "stm_level_block_solve",
+    "stm_level_smooth", "stm_level_restrict", "stm_level_prolong", "stm_coarsest_solve",
+]
+
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
 
 KERNEL_CLASSES = ["residual", "dst", "smooth", "restrict", "prolong", "norm", "vector", "rhs", "space_mg"]
@@ -48,6 +54,11 @@ class StOptions(ctypes.Structure):
                 ("inner_cycles", ctypes.c_int), ("max_workspace_bytes", ctypes.c_size_t),
                 ("smoother", ctypes.c_int), ("nu_x", ctypes.c_int), ("omega_x", ctypes.c_double),
                 ("gamma", ctypes.c_int)]
+
+
+class SimplexMesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nverts", ctypes.c_int), ("verts", ctypes.POINTER(ctypes.c_double)),
+                ("ncells", ctypes.c_int), ("cells", ctypes.POINTER(ctypes.c_int))]
 
 
 class StmgError(RuntimeError):
@@ -101,6 +112,28 @@ def load_library(path=None):
         "st_profile_stop": (I, [H, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(I)]),
     }
+    IP = ctypes.POINTER(I)
+    DP = ctypes.POINTER(D)
+    sig.update({
+        "stm_setup": (I, [ctypes.POINTER(SimplexMesh), I, I, I, D, ctypes.POINTER(StOptions), P,
+                          ctypes.POINTER(H)]),
+        "stm_destroy": (None, [H]),
+        "stm_last_error": (ctypes.c_char_p, [H]),
+        "stm_ndof": (ctypes.c_size_t, [H]),
+        "stm_num_levels": (I, [H]),
+        "stm_nodes": (I, [H, I, IP, DP]),
+        "stm_level_info": (I, [H, I, IP, IP, DP, IP]),
+        "stm_residual": (I, [H, P, P, P, P]),
+        "stm_vcycle": (I, [H, P, P, P]),
+        "stm_solve": (I, [H, P, P, P, I, IP, DP]),
+        "stm_adjoint_solve": (I, [H, P, P, P, IP, DP]),
+        "stm_level_residual": (I, [H, I, I, P, P, P]),
+        "stm_level_block_solve": (I, [H, I, I, P, P]),
+        "stm_level_smooth": (I, [H, I, I, I, P, P]),
+        "stm_level_restrict": (I, [H, I, P, P]),
+        "stm_level_prolong": (I, [H, I, P, P]),
+        "stm_coarsest_solve": (I, [H, I, P, P]),
+    })
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -367,6 +400,162 @@ class Solver:
         out = self.empty(0) if out is None else out
         m = self.level_ndof(0)
         self._check(self._lib.st_coarsest_solve(self._h, int(adjoint), _ptr(f, m, "f"), _ptr(out, m, "u")))
+        return out
+
+
+class MeshSolver:
+    """The space-time hierarchy on a uniformly refined simplicial mesh of the unit
+    square / cube (stm_setup, include/stmg_mesh.h), bound to the current CUDA
+    stream.  verts: (nverts, dim) coordinates, cells: (ncells, dim + 1) vertex
+    indices of the initial mesh.  Vectors: torch.float64 CUDA tensors with
+    N q Nx elements in the layout (N, q, Nx), Nx interior vertices ordered by
+    (z, y, x) (``nodes()``)."""
+
+    def __init__(self, verts, cells, refinements, p_t, N, T, *, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50,
+                 coarsening="auto", max_workspace_bytes=0, nu_x=2, omega_x=2.0 / 3.0, gamma=1, stream=None,
+                 device=None):
+        import numpy as np
+        L = lib()
+        self._lib = L
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        c = np.ascontiguousarray(cells, dtype=np.int32)
+        self.dim, self.p_t, self.N, self.T = v.shape[1], p_t, N, float(T)
+        self.q = p_t + 1
+        self.refinements = refinements
+        opt = make_options(nu1=nu1, nu2=nu2, omega=omega, rtol=rtol, maxit=maxit, precision="fp64",
+                           coarsening=coarsening, coarsest_steps=1, max_workspace_bytes=max_workspace_bytes,
+                           smoother="vcycle", nu_x=nu_x, omega_x=omega_x, gamma=gamma)
+        self.options = opt
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        mesh = SimplexMesh(self.dim, v.shape[0], v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), c.shape[0],
+                           c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = L.stm_setup(ctypes.byref(mesh), refinements, p_t, N, float(T), ctypes.byref(opt),
+                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != ST_OK:
+            raise StmgError(rc, "stm_setup failed")
+        self._h = h
+        self.ndof = int(L.stm_ndof(h))
+        self.Nx = self.ndof // (N * self.q)
+        self.shape = (N, self.q, self.Nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != ST_OK and rc not in allow:
+            raise StmgError(rc, self._lib.stm_last_error(self._h).decode())
+        return rc
+
+    def nodes(self, space_level=None):
+        """(Nx, dim) coordinates of the interior vertices of a refinement level
+        (default: the finest) in the unknowns' order."""
+        import numpy as np
+        lvl = self.refinements if space_level is None else space_level
+        cnt = ctypes.c_int()
+        self._check(self._lib.stm_nodes(self._h, lvl, ctypes.byref(cnt), None))
+        out = np.zeros((cnt.value, self.dim))
+        self._check(self._lib.stm_nodes(self._h, lvl, None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    @property
+    def num_levels(self):
+        return int(self._lib.stm_num_levels(self._h))
+
+    def level_info(self, L):
+        Nl, sl, mu, full = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        self._check(self._lib.stm_level_info(self._h, L, ctypes.byref(Nl), ctypes.byref(sl), ctypes.byref(mu),
+                                             ctypes.byref(full)))
+        return {"N": Nl.value, "space_level": sl.value, "mu": mu.value, "full": full.value}
+
+    def level_shape(self, L):
+        i = self.level_info(L)
+        cnt = ctypes.c_int()
+        self._check(self._lib.stm_nodes(self._h, i["space_level"], ctypes.byref(cnt), None))
+        return (i["N"], self.q, cnt.value)
+
+    def level_ndof(self, L):
+        a, b, c = self.level_shape(L)
+        return a * b * c
+
+    def empty(self, L=None):
+        shp = self.shape if L is None else self.level_shape(L)
+        return torch.empty(shp, dtype=torch.float64, device=self.device)
+
+    def residual(self, f, u, u0=None, out=None):
+        out = self.empty() if out is None else out
+        self._check(self._lib.stm_residual(self._h, _ptr(f, self.ndof, "f"), _ptr(u0, self.Nx, "u0"),
+                                           _ptr(u, self.ndof, "u"), _ptr(out, self.ndof, "r")))
+        return out
+
+    def vcycle(self, u, f, u0=None):
+        self._check(self._lib.stm_vcycle(self._h, _ptr(u, self.ndof, "u"), _ptr(f, self.ndof, "f"),
+                                         _ptr(u0, self.Nx, "u0")))
+        return u
+
+    def solve(self, f, u0=None, u=None, initial_guess=None, raise_on_failure=True):
+        init = (u is not None) if initial_guess is None else bool(initial_guess)
+        u = self.empty() if u is None else u
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        rc = self._lib.stm_solve(self._h, _ptr(f, self.ndof, "f"), _ptr(u0, self.Nx, "u0"), _ptr(u, self.ndof, "u"),
+                                 ST_INIT_GIVEN if init else 0, ctypes.byref(it), ctypes.byref(rr))
+        self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
+        self.last_status = rc
+        return u, it.value, rr.value
+
+    def adjoint_solve(self, g, lam=None, raise_on_failure=True):
+        lam = self.empty() if lam is None else lam
+        gu0 = torch.empty(self.Nx, dtype=torch.float64, device=self.device)
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        rc = self._lib.stm_adjoint_solve(self._h, _ptr(g, self.ndof, "g"), _ptr(lam, self.ndof, "lambda"),
+                                         _ptr(gu0, self.Nx, "grad_u0"), ctypes.byref(it), ctypes.byref(rr))
+        self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
+        self.last_status = rc
+        return lam, gu0, it.value, rr.value
+
+    def level_residual(self, L, f, u, adjoint=False, out=None):
+        m = self.level_ndof(L)
+        out = self.empty(L) if out is None else out
+        self._check(self._lib.stm_level_residual(self._h, L, int(adjoint), _ptr(f, m, "f"), _ptr(u, m, "u"),
+                                                 _ptr(out, m, "r")))
+        return out
+
+    def level_block_solve(self, L, r, adjoint=False, out=None):
+        m = self.level_ndof(L)
+        out = self.empty(L) if out is None else out
+        self._check(self._lib.stm_level_block_solve(self._h, L, int(adjoint), _ptr(r, m, "r"), _ptr(out, m, "d")))
+        return out
+
+    def level_smooth(self, L, f, u, nu=1, adjoint=False):
+        m = self.level_ndof(L)
+        self._check(self._lib.stm_level_smooth(self._h, L, int(adjoint), nu, _ptr(f, m, "f"), _ptr(u, m, "u")))
+        return u
+
+    def level_restrict(self, L, r, out=None):
+        out = self.empty(L - 1) if out is None else out
+        self._check(self._lib.stm_level_restrict(self._h, L, _ptr(r, self.level_ndof(L), "r"),
+                                                 _ptr(out, self.level_ndof(L - 1), "f_coarse")))
+        return out
+
+    def level_prolong(self, L, e, u):
+        self._check(self._lib.stm_level_prolong(self._h, L, _ptr(e, self.level_ndof(L - 1), "e"),
+                                                _ptr(u, self.level_ndof(L), "u")))
+        return u
+
+    def coarsest_solve(self, f, adjoint=False, out=None):
+        out = self.empty(0) if out is None else out
+        m = self.level_ndof(0)
+        self._check(self._lib.stm_coarsest_solve(self._h, int(adjoint), _ptr(f, m, "f"), _ptr(out, m, "u")))
         return out
 
 

@@ -1,5 +1,6 @@
 """The C ABI library loads without a GPU and exports every function that
-include/stmg.h declares; host-side argument checks (no device calls)."""
+include/stmg.h and include/stmg_mesh.h declare; host-side argument checks
+(no device calls)."""
 import ctypes
 import os
 import re
@@ -8,12 +9,13 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "stmg.h")
+MESH_HEADER = os.path.join(ROOT, "include", "stmg_mesh.h")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER, prefix="st_"):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(st_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -32,13 +34,16 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol(lib):
-    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    names = declared_functions() + declared_functions(MESH_HEADER, "stm_")
+    missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+    assert "stm_setup" in names and "stm_solve" in names
 
 
 def test_binding_lists_match_header():
     from paper_1411_0519_gb300 import stmg
     assert sorted(stmg.EXPORTS) == declared_functions()
+    assert sorted(stmg.MESH_EXPORTS) == declared_functions(MESH_HEADER, "stm_")
 
 
 def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
@@ -62,3 +67,45 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.st_setup(None, 1, 16, 1.0, None, None, ctypes.byref(h)) == stmg.ST_EINVAL
     assert lib.st_num_levels(None) == 0 and lib.st_ndof(None) == 0
     assert lib.st_residual(None, None, None, None, None) == stmg.ST_EINVAL
+
+
+def test_mesh_setup_rejects_bad_arguments_before_touching_the_device(lib):
+    """stm_setup checks the mesh, the discretisation and the options on the host."""
+    import numpy as np
+    from paper_1411_0519_gb300 import stmg
+    verts = np.array([[0, 0], [1, 0], [1, 1], [0, 1], [0.5, 0.5]], dtype=np.float64)
+    cells = np.array([[0, 1, 4], [1, 2, 4], [2, 3, 4], [3, 0, 4]], dtype=np.int32)
+
+    def mesh(v, c, dim=2):
+        return stmg.SimplexMesh(dim, v.shape[0], v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), c.shape[0],
+                                c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    opt = stmg.StOptions()
+    lib.st_default_options(ctypes.byref(opt))
+    opt.smoother = stmg.ST_SMOOTH_VCYCLE
+    h = ctypes.c_void_p()
+    good = mesh(verts, cells)
+    bad_cells = cells.copy()
+    bad_cells[0, 0] = 7
+    outside = verts.copy()
+    outside[0, 0] = -0.5
+    cases = [
+        (mesh(verts, bad_cells), 1, 1, 16, 1.0, opt),       # vertex index out of range
+        (mesh(outside, cells), 1, 1, 16, 1.0, opt),         # vertex outside the unit square
+        (mesh(verts, cells, dim=4), 1, 1, 16, 1.0, opt),    # dim
+        (good, 1, 4, 16, 1.0, opt),                         # p_t > 3
+        (good, 1, 1, 12, 1.0, opt),                         # N not a power of two
+        (good, 1, 1, 16, 0.0, opt),                         # T <= 0
+        (good, -1, 1, 16, 1.0, opt),                        # refinements
+    ]
+    for m, ref, p, N, T, o in cases:
+        assert lib.stm_setup(ctypes.byref(m), ref, p, N, T, ctypes.byref(o), None, ctypes.byref(h)) == stmg.ST_EINVAL
+        assert not h.value
+    for field, val in [("smoother", stmg.ST_SMOOTH_EXACT), ("precision", stmg.ST_MIXED), ("coarsest_steps", 2)]:
+        o = stmg.StOptions()
+        ctypes.pointer(o)[0] = opt
+        setattr(o, field, val)
+        assert lib.stm_setup(ctypes.byref(good), 1, 1, 16, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == \
+            stmg.ST_EINVAL
+    assert lib.stm_setup(None, 1, 1, 16, 1.0, None, None, ctypes.byref(h)) == stmg.ST_EINVAL
+    assert lib.stm_num_levels(None) == 0 and lib.stm_ndof(None) == 0
+    assert lib.stm_residual(None, None, None, None, None) == stmg.ST_EINVAL
