@@ -60,8 +60,19 @@ def parse():
     ap.add_argument("--no-high-order", action="store_true",
                     help="skip the Example 2 solve at p_t = 45 (generic-q kernels)")
     ap.add_argument("--inner-cycles", type=int, default=4)
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
-                    help="run one precision only (profiling); the line's value is that precision's")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the mixed-against-FP64 legs on heat3d_63 and heat2d_511")
+    ap.add_argument("--no-mesh", action="store_true",
+                    help="skip Example 2 on the paper's refined triangle mesh (P1 mesh solver)")
+    ap.add_argument("--two-grid", action="store_true",
+                    help="report mode: the two-grid convergence factors of Section 3.2 measured on the GPU over "
+                         "mu = 1e-6 ... 1e6 (4 points per decade), p_t in {0, 1}, nu in {1, 2, 5}, semi and full "
+                         "coarsening; prints one JSON line with every point")
+    ap.add_argument("--only", choices=["fp64", "mixed", "mesh", "configs"], default=None,
+                    help="profiling: one precision of the main workload only (the line's value is that "
+                         "precision's), or only the mesh leg / the heat3d_63 and heat2d_511 legs (the line "
+                         "carries that leg)")
+    ap.add_argument("--mesh-level", type=int, default=7, help="refinements of the 4-triangle square (mesh leg)")
     return ap.parse_args()
 
 
@@ -226,8 +237,8 @@ def roofline(solver, prof, fp32, pk, w, exclude=()):
 
 def transform_note(prof, w):
     """The boundary sine transforms of the mixed form: double-float arithmetic on
-    the FP32 pipe (FP64-equivalent algorithmic flops; latency-bound, see
-    profiles/dst_heat2d_255_n256.md), reported beside the FP32 cycle kernels."""
+    the FP32 pipe (FP64-equivalent algorithmic flops; latency-bound by their ncu
+    capture), reported beside the FP32 cycle kernels."""
     classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["ms"] > 0}
     if "dst" not in classes:
         return None
@@ -239,17 +250,25 @@ def transform_note(prof, w):
             "bound": "latency (issue 48-52 %, 15.7 warps per SM; ncu)"}
 
 
-def vcycle_times(solver, prof, steps, iters, per_step_ms):
+def vcycle_times(solver, prof, steps, iters, per_step_ms, pk):
     """Time of one cycle: the solve time without the boundary transforms, per
     cycle, and the kernel time of the finest level per cycle (CUDA events of
-    the library, transforms excluded)."""
+    the library, transforms excluded); the cycle's achieved HBM rate is its
+    algorithmic bytes (every kernel of the cycles and stopping tests, each
+    input read once and each output written once, summed over all levels by
+    the library) over that time, as a fraction of the measured copy rate."""
     L = solver.num_levels - 1
     cls = [c for c in prof if not c.startswith("_") and c != "dst"]
     fin = sum(solver.profile_level(c, L)["ms"] for c in cls)
     dst = prof.get("dst", {}).get("ms", 0.0) / steps
     n = max(1, iters)
-    return {"ms_per_cycle_without_transforms": (per_step_ms - dst) / n,
-            "finest_level_kernel_ms_per_cycle": fin / steps / n}
+    ms = (per_step_ms - dst) / n
+    by = sum(prof[c]["bytes"] for c in cls) / steps / n
+    gbs = by / (ms / 1e3) / 1e9
+    return {"ms_per_cycle_without_transforms": ms,
+            "finest_level_kernel_ms_per_cycle": fin / steps / n,
+            "alg_bytes_per_cycle": by, "achieved_gbs": round(gbs, 1), "peak_gbs": pk["hbm_gbs"],
+            "frac": round(gbs / pk["hbm_gbs"], 4)}
 
 
 def breakdown(prof):
@@ -259,32 +278,68 @@ def breakdown(prof):
             for k, v in prof.items() if not k.startswith("_") and v["launches"] > 0}
 
 
-def cpu_baseline(w, rank, repeats=1):
-    """The oracle, as it stands, on a bounded sample (first CPU_SAMPLE_STEPS time
-    steps); returns one entry per timed solve (setup excluded)."""
+def _oracle_worker(job):
+    """One host core: the oracle (as it stands, one BLAS thread) solves the
+    sampled window `job["window"]` of the workload's time steps, after all
+    workers have finished their setup (barrier); returns wall-clock start/end
+    of each timed solve."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
     try:
         from threadpoolctl import threadpool_limits
-        limiter = threadpool_limits(1)
+        threadpool_limits(1)
     except Exception:
-        limiter = None
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        pass
+    sys.path.insert(0, ROOT)
     from oracle import multigrid, spacetime
     from paper_1411_0519_gb300 import workloads
-    Ns = CPU_SAMPLE_STEPS
+    w, Ns, i = job["w"], job["steps"], job["window"]
     tau = w["T"] / w["N"]
     H = multigrid.Hierarchy(w["d"], w["n"], w["p_t"], Ns, tau * Ns)
     disc = H.finest.disc
-    f = workloads.uniform_load(w["d"], w["n"], w["p_t"], w["N"], seed=rank)[:Ns].reshape(disc.shape())
+    f = workloads.uniform_load_steps(w["d"], w["n"], w["p_t"], w["N"], i * Ns, (i + 1) * Ns, seed=job["seed"])
+    f = f.reshape(disc.shape())
     g = spacetime.add_ic(disc, f, workloads.sine_ic(w["d"], w["n"]))
+    job["barrier"].wait()
+    spans = []
+    for _ in range(job["repeats"]):
+        t0 = time.time()
+        _, it, _ = multigrid.solve(H, g, rtol=w["rtol"], maxit=60)
+        spans.append((t0, time.time(), it))
+    return {"spans": spans, "dof": disc.ndof}
+
+
+def cpu_baseline(w, rank, repeats=1, cores=None):
+    """The oracle, as it stands, on every host core: each core (a spawned
+    process with one BLAS thread) solves its own window of CPU_SAMPLE_STEPS
+    consecutive time steps of the workload (same mesh and tau, its own rows of
+    f) to the same tolerance, all at once after a common barrier.  Returns one
+    entry per round of solves: DoF/s = DoF of all windows / wall time from the
+    first start to the last end (setup excluded)."""
+    import multiprocessing as mp
+    if not cores:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    cores = max(1, min(cores, w["N"] // CPU_SAMPLE_STEPS))
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        bar = mgr.Barrier(cores)
+        jobs = [{"w": w, "steps": CPU_SAMPLE_STEPS, "window": i, "seed": rank, "repeats": repeats, "barrier": bar}
+                for i in range(cores)]
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    dof = sum(r["dof"] for r in res)
     out = []
-    for _ in range(repeats):
-        t0 = time.perf_counter()
-        _, it, hist = multigrid.solve(H, g, rtol=w["rtol"], maxit=60)
-        dt = time.perf_counter() - t0
-        out.append({"value": disc.ndof / dt, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                    "sample": f"oracle solve of the first {Ns} of {w['N']} time steps (same mesh and tau, "
-                              f"{disc.ndof} DoF) to {w['rtol']:g}: {it} V-cycles in {dt:.1f} s; setup excluded",
-                    "seconds": dt, "iters": it, "dof": disc.ndof})
+    for k in range(repeats):
+        t0 = min(r["spans"][k][0] for r in res)
+        t1 = max(r["spans"][k][1] for r in res)
+        its = sorted({r["spans"][k][2] for r in res})
+        dt = t1 - t0
+        out.append({"value": dof / dt, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+                    "sample": f"{cores} processes at once (one per host core, one BLAS thread each), each an oracle "
+                              f"solve of its own {CPU_SAMPLE_STEPS} consecutive time steps of the {w['N']} (same mesh "
+                              f"and tau, {res[0]['dof']} DoF each, {dof} in all) to {w['rtol']:g}: "
+                              f"{'/'.join(map(str, its))} V-cycles, {dt:.1f} s wall; setup excluded",
+                    "seconds": dt, "iters": its[-1], "dof": dof})
     return out
 
 
@@ -294,7 +349,7 @@ def run_reference(args):
     w = workloads.WORKLOADS[args.workload]
     if rank != 0:
         return 0
-    # each step: one oracle solve of the bounded sample; warm-up solves untimed
+    # each step: one round of oracle solves of the bounded samples on every core; warm-up rounds untimed
     samples = cpu_baseline(w, 0, repeats=args.warmup + args.steps)[args.warmup:]
     sec = sum(s["seconds"] for s in samples)
     value = samples[0]["dof"] * len(samples) / sec
@@ -304,7 +359,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "d": w["d"], "n": w["n"], "p_t": w["p_t"], "N": w["N"],
                        "T": w["T"], "rtol": w["rtol"], "sampled_time_steps": CPU_SAMPLE_STEPS},
-            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": samples[0]["cores"], "kind": "oracle",
                              "sample": samples[0]["sample"]},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -336,10 +391,213 @@ def run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_ov
     return 0
 
 
+def timed_solve(torch, solver, run, steps, warmup, barrier, max_over_ranks):
+    """`run()` (one solve returning (iterations, relres)) `warmup` times untimed,
+    then `steps` times between CUDA events on the solver's stream with the
+    library's per-kernel timing on."""
+    for _ in range(warmup):
+        run()
+    barrier()
+    torch.cuda.synchronize()
+    solver.profile_start(400000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(solver.stream)
+    res = [run() for _ in range(steps)]
+    e1.record(solver.stream)
+    e1.synchronize()
+    prof = solver.profile_stop()
+    ms = max_over_ranks(e0.elapsed_time(e1)) / steps
+    return ms, res[-1][0], res[-1][1], prof
+
+
+# The paper's initial triangulation of the unit square for Example 2 (Section 4):
+# 4 triangles around the centre.
+SQUARE_VERTS = [[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0], [0.5, 0.5]]
+SQUARE_CELLS = [[0, 1, 4], [1, 2, 4], [2, 3, 4], [3, 0, 4]]
+
+
+def mesh_leg(args, torch, stmg, barrier, max_over_ranks, world, rank, level=7):
+    """Example 2's protocol (Section 4) on the paper's own mesh family: the
+    4-triangle square refined `level` times (P1, node basis), tau = 1,
+    N = T = 1024, f = 0, iterate ~ U[0, 1] (seed = rank), the inexact block
+    inverse (one spatial V-cycle per step), to 1e-8; p_t = 1 and 3.  Each timed
+    solve starts from a copy of the same iterate (the copy is inside the timed
+    region, one vector)."""
+    out = {"workload": f"example2_mesh: 4 triangles refined {level} times, P1, N = 1024, tau = 1, f = 0, "
+                       "iterate ~ U[0, 1], inexact block inverse (nu_x = 2, omega_x = 2/3)"}
+    gen = torch.Generator(device="cuda")
+    for p in (1, 3):
+        s = stmg.MeshSolver(SQUARE_VERTS, SQUARE_CELLS, level, p, 1024, 1024.0, rtol=1e-8, maxit=40)
+        gen.manual_seed(rank)
+        it0 = torch.rand(s.shape, dtype=torch.float64, device="cuda", generator=gen)
+        u = torch.empty_like(it0)
+        fz = torch.zeros_like(it0)
+        for _ in range(1):
+            u.copy_(it0)
+            s.solve(fz, u=u, initial_guess=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nst = 2
+        e0.record(s.stream)
+        for _ in range(nst):
+            with torch.cuda.stream(s.stream):
+                u.copy_(it0)
+            _, it, rr = s.solve(fz, u=u, initial_guess=True)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / nst
+        out["p_t=%d" % p] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
+                             "iters": it, "relres": rr, "dof": s.ndof, "nodes": s.Nx,
+                             "ms_per_cycle": ms / max(1, it), "levels": s.num_levels}
+        s.close()
+        del it0, u, fz
+        torch.cuda.empty_cache()
+    return out
+
+
+def config_legs(args, torch, stmg, workloads, pk, barrier, max_over_ranks, world, rank):
+    """The mixed-against-FP64 comparison on its two stated workloads: heat3d_63
+    (63^3 Q1, p_t = 2, N = 512, 384M unknowns, Gaussian load) and heat2d_511
+    (511^2 Q1, p_t = 1, N = 2048, 1.07B unknowns) across the semi / full
+    coarsening threshold (T = mu / 128 for mu in 1/16, 1/4, 1, 16), each solve to
+    1e-8: DoF/s, cycles, final relative residual and the dominant kernel's
+    roofline; heat2d_511 adds the adjoint solve (L^T lambda = f) in both forms.
+    Entries are drawn on the device (torch's CUDA generator, seed = rank) for
+    heat2d_511; heat3d_63 uses the seeded Gaussian load of the tests."""
+    out = {}
+    # ---- heat3d_63
+    w = dict(workloads.WORKLOADS["heat3d_63"])
+    d, n, p, N, T = w["d"], w["n"], w["p_t"], w["N"], w["T"]
+    f = torch.from_numpy(workloads.gaussian_load(d, n, p, N, T, seed=rank)).cuda()
+    leg = {"workload": "heat3d_63: 3D 63^3 Q1, p_t = 2, N = 512, T = 1, 16 Gaussians, u0 = 0",
+           "dof": N * (p + 1) * n ** d}
+    for prec in ("fp64", "mixed"):
+        s = stmg.Solver(d, n, p, N, T, rtol=w["rtol"], maxit=60, precision=prec, inner_cycles=args.inner_cycles)
+        u = s.empty()
+
+        def run():
+            _, it, rr = s.solve(f, u=u, initial_guess=False)
+            return it, rr
+        ms, it, rr, prof = timed_solve(torch, s, run, 2, 1, barrier, max_over_ranks)
+        leg[prec] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "iters": it,
+                     "relres": rr, "roofline": roofline(s, prof, prec == "mixed", pk, w,
+                                                        exclude=("dst",) if prec == "mixed" else ()),
+                     "cycle": vcycle_times(s, prof, 2, it, ms, pk)}
+        s.close()
+        del u
+        torch.cuda.empty_cache()
+    leg["mixed_over_fp64"] = round(leg["mixed"]["value"] / leg["fp64"]["value"], 3)
+    out["heat3d_63"] = leg
+    del f
+    torch.cuda.empty_cache()
+    # ---- heat2d_511 across mu*
+    w0 = dict(workloads.WORKLOADS["heat2d_511"])
+    d, n, p, N = w0["d"], w0["n"], w0["p_t"], w0["N"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(rank)
+    f = torch.rand((N, p + 1, n, n), dtype=torch.float64, device="cuda", generator=gen).mul_(2.0).sub_(1.0)
+    legs = {"workload": "heat2d_511: 2D 511^2 Q1, p_t = 1, N = 2048, T = mu / 128, f ~ U[-1, 1]",
+            "dof": N * (p + 1) * n ** d}
+    for mu in (1.0 / 16, 0.25, 1.0, 16.0):
+        w = dict(w0)
+        w["T"] = mu / 128.0
+        entry = {}
+        for prec in ("fp64", "mixed"):
+            s = stmg.Solver(d, n, p, N, w["T"], rtol=w["rtol"], maxit=80, precision=prec,
+                            inner_cycles=args.inner_cycles)
+            if prec == "fp64":
+                entry["levels_full"] = [s.level_info(L)["full"] for L in range(s.num_levels - 1)][::-1]
+            u = s.empty()
+
+            def run():
+                _, it, rr = s.solve(f, u=u, initial_guess=False)
+                return it, rr
+
+            def run_adj():
+                _, _, it, rr = s.adjoint_solve(f, lam=u)
+                return it, rr
+            ms, it, rr, prof = timed_solve(torch, s, run, 1, 1, barrier, max_over_ranks)
+            msa, ita, rra, profa = timed_solve(torch, s, run_adj, 1, 1, barrier, max_over_ranks)
+            entry[prec] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "iters": it,
+                           "relres": rr, "roofline": roofline(s, prof, prec == "mixed", pk, w,
+                                                              exclude=("dst",) if prec == "mixed" else ()),
+                           "cycle": vcycle_times(s, prof, 1, it, ms, pk),
+                           "adjoint": {"value": world * s.ndof / (msa / 1e3), "unit": "DoF/s", "ms_per_step": msa,
+                                       "iters": ita, "relres": rra}}
+            s.close()
+            del u
+            torch.cuda.empty_cache()
+        entry["mixed_over_fp64"] = round(entry["mixed"]["value"] / entry["fp64"]["value"], 3)
+        legs["mu=%g" % mu] = entry
+    out["heat2d_511"] = legs
+    del f
+    torch.cuda.empty_cache()
+    return out
+
+
+TWO_GRID_NX, TWO_GRID_NT = 1023, 256
+
+
+def two_grid_factor(torch, stmg, workloads, p, mu, nu, full, eps=1e-140, max_iter=250):
+    """Section 3.2's measured two-grid factor: max_k ||r_{k+1}|| / ||r_k|| over the
+    cycles until ||r_k|| <= eps ||r_0|| or max_iter cycles, for L u = 0 from a
+    random iterate in [0, 1] (1D, 1023 interior nodes, 256 steps, tau = mu h^2).
+    A two-grid cycle is the library's cycle on a two-level hierarchy whose coarse
+    level (128 steps) is solved exactly by forward substitution."""
+    nx, nt = TWO_GRID_NX, TWO_GRID_NT
+    h = 1.0 / (nx + 1)
+    s = stmg.Solver(1, nx, p, nt, mu * h * h * nt, nu1=nu, nu2=nu, coarsening="full" if full else "semi",
+                    coarsest_steps=nt // 2, rtol=0.0, maxit=1)
+    u = torch.from_numpy(workloads.uniform_iterate(1, nx, p, nt, seed=0)).cuda()
+    f = torch.zeros_like(u)
+    r = s.residual(f, u)
+    r0 = s.norm2(r)
+    prev, worst, it = r0, 0.0, 0
+    while it < max_iter:
+        s.vcycle(u, f)
+        s.residual(f, u, out=r)
+        rn = s.norm2(r)
+        it += 1
+        worst = max(worst, rn / prev)
+        prev = rn
+        if rn <= eps * r0 or rn == 0.0:
+            break
+    s.close()
+    return worst, it
+
+
+def run_two_grid(args):
+    import torch
+    from paper_1411_0519_gb300 import stmg, workloads
+    mus = [10.0 ** (e / 4.0) for e in range(-24, 25)]
+    points = []
+    t0 = time.perf_counter()
+    for full in (False, True):
+        for p in (0, 1):
+            for nu in (1, 2, 5):
+                for mu in mus:
+                    fac, it = two_grid_factor(torch, stmg, workloads, p, mu, nu, full)
+                    points.append({"coarsening": "full" if full else "semi", "p_t": p, "nu": nu, "mu": mu,
+                                   "factor": fac, "cycles": it})
+    dt = time.perf_counter() - t0
+    line = {"metric": "two-grid convergence factor max_k ||r_{k+1}|| / ||r_k|| (Section 3.2)", "unit": "1",
+            "value": max(q["factor"] for q in points if q["coarsening"] == "semi"), "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1D heat, 1023 interior nodes, 256 time steps, f = 0, u0 ~ U[0, 1] (seed 0), "
+                                   "omega = 1/2, nu1 = nu2 = nu, until 1e-140 or 250 cycles",
+                       "mu": "10^(k/4), k = -24 ... 24"},
+            "seconds": dt, "points": points}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.two_grid:
+        return run_two_grid(args)
     import torch
     from paper_1411_0519_gb300 import dist as pd
     from paper_1411_0519_gb300 import stmg, workloads
@@ -361,6 +619,17 @@ def main():
 
     if args.only == "mixed":
         return run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_over_ranks, local)
+    if args.only in ("mesh", "configs"):
+        del f, u0
+        torch.cuda.empty_cache()
+        if args.only == "mesh":
+            leg = mesh_leg(args, torch, stmg, barrier, max_over_ranks, world, rank, level=args.mesh_level)
+        else:
+            leg = config_legs(args, torch, stmg, workloads, pk, barrier, max_over_ranks, world, rank)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "only": args.only, "n_gpus": world, "leg": leg}), flush=True)
+        pd.finalize()
+        return 0
 
     # ---------------------------------------------------------------- FP64 (headline)
     s64 = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="fp64")
@@ -394,7 +663,7 @@ def main():
                "ms_per_step": 1e3 * dt / args.steps, "api": "st_solve_host"}
         del fh, u0h, uh
     rf64 = roofline(s64, prof64, False, pk, w)
-    vc64 = vcycle_times(s64, prof64, args.steps, it64[-1], per_step)
+    vc64 = vcycle_times(s64, prof64, args.steps, it64[-1], per_step, pk)
     s64.close()
     torch.cuda.empty_cache()
 
@@ -407,6 +676,7 @@ def main():
         mixed = {"value": world * smx.ndof / (msm / args.steps / 1e3), "unit": "DoF/s",
                  "ms_per_step": msm / args.steps, "iters": itm[-1], "relres": rrm,
                  "inner_cycles": args.inner_cycles, "dtype": "f32 V-cycle in f64 refinement",
+                 "refinement_step": vcycle_times(smx, profm, args.steps, itm[-1], msm / args.steps, pk),
                  "roofline": roofline(smx, profm, True, pk, w, exclude=("dst",)),
                  "transform": transform_note(profm, w),
                  "kernels": breakdown(profm),
@@ -466,6 +736,14 @@ def main():
         del it0, fz, uh
         torch.cuda.empty_cache()
 
+    # ---------------------------------------------------------------- the other stated workloads
+    configs = None
+    if not args.no_configs:
+        configs = config_legs(args, torch, stmg, workloads, pk, barrier, max_over_ranks, world, rank)
+    mesh = None
+    if not args.no_mesh:
+        mesh = mesh_leg(args, torch, stmg, barrier, max_over_ranks, world, rank, level=args.mesh_level)
+
     if rank != 0:
         pd.finalize()
         return 0
@@ -490,6 +768,8 @@ def main():
         "mixed": mixed,
         "inexact_smoother": inexact,
         "high_order": high,
+        "configs": configs,
+        "mesh": mesh,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": ck,

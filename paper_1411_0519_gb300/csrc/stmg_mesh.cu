@@ -304,6 +304,37 @@ void l_jacobi(stm_handle* h, const MLevel& L, int k, bool adj, bool zero, const 
 }
 
 template <int Q>
+void l_residual_jacobi0(stm_handle* h, const MLevel& L, bool adj, const double* f, const double* u, double* r,
+                        double* x) {
+  const SpaceLevel& s = h->sp[L.l];
+  const auto tc = mtime<Q>(h->tm);
+  const double* D = L.dinv[L.l];
+  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
+    if (adj)
+      stmm::k_mresidual_jacobi0<Q, true><<<g, kThreads, 0, h->stream>>>(f, u, r, x, csr(s), s.Nx, L.N, s0, L.tau,
+                                                                          h->opt.omega_x, D, tc);
+    else
+      stmm::k_mresidual_jacobi0<Q, false><<<g, kThreads, 0, h->stream>>>(f, u, r, x, csr(s), s.Nx, L.N, s0, L.tau,
+                                                                           h->opt.omega_x, D, tc);
+  });
+}
+
+template <int Q>
+void l_jacobi_update(stm_handle* h, const MLevel& L, bool adj, const double* b, const double* x, double* u) {
+  const SpaceLevel& s = h->sp[L.l];
+  const auto tc = mtime<Q>(h->tm);
+  const double* D = L.dinv[L.l];
+  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
+    if (adj)
+      stmm::k_mjacobi_update<Q, true><<<g, kThreads, 0, h->stream>>>(b, x, u, csr(s), s.Nx, L.N, s0, L.tau,
+                                                                       h->opt.omega_x, h->opt.omega, D, tc);
+    else
+      stmm::k_mjacobi_update<Q, false><<<g, kThreads, 0, h->stream>>>(b, x, u, csr(s), s.Nx, L.N, s0, L.tau,
+                                                                        h->opt.omega_x, h->opt.omega, D, tc);
+  });
+}
+
+template <int Q>
 void l_space_residual(stm_handle* h, const MLevel& L, int k, bool adj, const double* b, const double* x, double* r) {
   const SpaceLevel& s = h->sp[k];
   const auto tc = mtime<Q>(h->tm);
@@ -405,15 +436,25 @@ double norm2(stm_handle* h, const double* x, int64_t n) {
 // space-time level L (the inexact block inverse, Remark on the V-cycle
 // approximation in space): x = D~^{-1} b from a zero guess.  Returns the buffer
 // that holds the result (one of L.sx[k], L.sy[k]); b is not modified.
-const double* space_vcycle(stm_handle* h, MLevel& L, int k, bool adj, const double* b) {
+// x0_done: L.sx[k] already holds the first sweep omega_x D^{-1} b (fused into the
+// residual pass).  update: instead of returning the result, the last sweep adds
+// omega_t times it into `update` (the damped step of the smoother) and nullptr is
+// returned.
+const double* space_vcycle(stm_handle* h, MLevel& L, int k, bool adj, const double* b, bool x0_done = false,
+                           double* update = nullptr) {
   if (k == 0) {
+    if (update) {
+      l_dense(h, L, adj, b, L.sx[0]);
+      axpy(h, update, L.sx[0], h->opt.omega, L.ndof);
+      return nullptr;
+    }
     l_dense(h, L, adj, b, L.sx[0]);
     return L.sx[0];
   }
   double* x = L.sx[k];
   double* y = L.sy[k];
   const int nu = std::max(1, h->opt.nu_x);
-  STM_Q(l_jacobi, h, L, k, adj, true, b, (const double*)nullptr, x);
+  if (!x0_done) STM_Q(l_jacobi, h, L, k, adj, true, b, (const double*)nullptr, x);
   for (int i = 1; i < nu; ++i) {
     STM_Q(l_jacobi, h, L, k, adj, false, b, x, y);
     std::swap(x, y);
@@ -423,19 +464,30 @@ const double* space_vcycle(stm_handle* h, MLevel& L, int k, bool adj, const doub
   const double* xc = space_vcycle(h, L, k - 1, adj, L.sb[k - 1]);
   STM_Q(l_prolong_space_add, h, L, k, xc, x);
   for (int i = 0; i < nu; ++i) {
+    if (update != nullptr && i == nu - 1) {
+      STM_Q(l_jacobi_update, h, L, adj, b, x, update);
+      return nullptr;
+    }
     STM_Q(l_jacobi, h, L, k, adj, false, b, x, y);
     std::swap(x, y);
   }
   return x;
 }
 
-// u <- u + omega D~^{-1} (f - L u), nu times (eq. chap4_smoother).
+// u <- u + omega D~^{-1} (f - L u), nu times (eq. chap4_smoother).  On a level
+// whose mesh is refined, the residual pass also takes the first Jacobi sweep of
+// the spatial V-cycle and the last sweep adds into u directly.
 void smooth(stm_handle* h, int Li, bool adj, double* u, const double* f, int nu) {
   MLevel& L = h->lv[Li];
   for (int i = 0; i < nu; ++i) {
-    STM_Q(l_residual, h, L, adj, f, u, L.r);
-    const double* d = space_vcycle(h, L, L.l, adj, L.r);
-    axpy(h, u, d, h->opt.omega, L.ndof);
+    if (L.l >= 1) {
+      STM_Q(l_residual_jacobi0, h, L, adj, f, u, L.r, L.sx[L.l]);
+      space_vcycle(h, L, L.l, adj, L.r, true, u);
+    } else {
+      STM_Q(l_residual, h, L, adj, f, u, L.r);
+      const double* d = space_vcycle(h, L, L.l, adj, L.r);
+      axpy(h, u, d, h->opt.omega, L.ndof);
+    }
   }
 }
 

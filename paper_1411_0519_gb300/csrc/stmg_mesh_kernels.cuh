@@ -108,6 +108,76 @@ __global__ void k_mresidual(const double* __restrict__ f, const double* __restri
   }
 }
 
+// The residual of k_mresidual fused with the first point-block Jacobi sweep of
+// the smoother's spatial V-cycle from a zero guess: r as above and, on the
+// same mesh, x = omega_x D_j^{-1} r_j (D^{-T} for the adjoint).
+template <int Q, bool ADJ>
+__global__ void k_mresidual_jacobi0(const double* __restrict__ f, const double* __restrict__ u,
+                                    double* __restrict__ r, double* __restrict__ x, Csr A, int Nx, int N, int s0,
+                                    double tau, double omega_x, const double* __restrict__ dinv, MTime<Q> tc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N) return;
+  const int64_t slab = (int64_t)Q * Nx;
+  double ax[Q];
+  apply_A<Q, ADJ>(A, j, Nx, u + s * slab, tau, tc, ax);
+  double mt = 0.0;
+  const int nb = ADJ ? s + 1 : s - 1;
+  if (nb >= 0 && nb < N) {
+    const double* un = u + nb * slab;
+    const int e1 = A.rp[j + 1];
+    for (int e = A.rp[j]; e < e1; ++e) {
+      const int c = A.ci[e];
+      double t = 0.0;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) t += (ADJ ? tc.st[l] : tc.en[l]) * un[l * (int64_t)Nx + c];
+      mt += A.mv[e] * t;
+    }
+  }
+  double res[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const int64_t idx = s * slab + (int64_t)k * Nx + j;
+    res[k] = f[idx] - ax[k] + (ADJ ? tc.en[k] : tc.st[k]) * mt;
+    r[idx] = res[k];
+  }
+  const double* D = dinv + (int64_t)j * Q * Q;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc += (ADJ ? D[l * Q + k] : D[k * Q + l]) * res[l];
+    x[s * slab + (int64_t)k * Nx + j] = omega_x * acc;
+  }
+}
+
+// The last point-block Jacobi sweep of the spatial V-cycle fused with the
+// damped update of the smoothing step (eq. chap4_smoother):
+// u += omega_t (x + omega_x D_j^{-1} (b - A x)_j), without storing the sweep.
+template <int Q, bool ADJ>
+__global__ void k_mjacobi_update(const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ u,
+                                 Csr A, int Nx, int N, int s0, double tau, double omega_x, double omega_t,
+                                 const double* __restrict__ dinv, MTime<Q> tc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = s0 + blockIdx.y;
+  if (j >= Nx || s >= N) return;
+  const int64_t base = s * (int64_t)Q * Nx + j;
+  double ax[Q];
+  apply_A<Q, ADJ>(A, j, Nx, x + s * (int64_t)Q * Nx, tau, tc, ax);
+  double res[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) res[k] = b[base + (int64_t)k * Nx] - ax[k];
+  const double* D = dinv + (int64_t)j * Q * Q;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) acc += (ADJ ? D[l * Q + k] : D[k * Q + l]) * res[l];
+    const double xn = x[base + (int64_t)k * Nx] + omega_x * acc;
+    u[base + (int64_t)k * Nx] += omega_t * xn;
+  }
+}
+
 // Initial value (eq. (equation1), the n = 0 term): g_{0,k} = f_{0,k} + st[k] (M_h u0)_j.
 template <int Q>
 __global__ void k_madd_ic(const double* __restrict__ f, const double* __restrict__ u0, double* __restrict__ g,

@@ -20,6 +20,7 @@ Workloads (unit square / cube, homogeneous Dirichlet, p_t = DG degree):
   heat2d_255_n256  heat2d_255 cut to its first 256 time steps (profiling)
   example2_p45     Example 2 protocol at the highest degree of its table: 127^2 Q1,
                    p_t = 45, tau = 1 (N = 64, T = 64), f = 0, iterate ~ U[0, 1]
+  heat3d_63_n64    heat3d_63 cut to its first 64 time steps (profiling)
 """
 import numpy as np
 
@@ -33,6 +34,9 @@ WORKLOADS = {
     # (33M unknowns, 266 MB per vector: above L2, a few GB on the device)
     "heat2d_255_n256": dict(d=2, n=255, p_t=1, N=256, T=0.25, rtol=1e-8),
     "example2_p45": dict(d=2, n=127, p_t=45, N=64, T=64.0, rtol=1e-8),
+    # profiling case in 3D: the 63^3 mesh and tau of heat3d_63 on 64 time steps
+    # (48M unknowns, 384 MB per vector: above L2, a few GB on the device)
+    "heat3d_63_n64": dict(d=3, n=63, p_t=2, N=64, T=0.125, rtol=1e-8),
 }
 
 

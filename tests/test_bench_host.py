@@ -26,7 +26,8 @@ def test_reference_arm_prints_one_line_with_the_contract_keys():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert str(d["cpu_baseline"]["cores"]) + " processes at once" in d["cpu_baseline"]["sample"]
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "heat1d_63"
@@ -91,7 +92,21 @@ def test_vcycle_times_leave_out_the_boundary_transforms():
     fs = _FakeSolver(3, {("smooth", 2): {"launches": 8, "ms": 12.0, "bytes": 0.0, "flops": 0.0},
                          ("residual", 2): {"launches": 4, "ms": 6.0, "bytes": 0.0, "flops": 0.0},
                          ("dst", 2): {"launches": 2, "ms": 9.0, "bytes": 0.0, "flops": 0.0}})
-    prof = _prof(smooth=(10, 14.0, 0, 0), residual=(6, 7.0, 0, 0), dst=(2, 9.0, 0, 0))
-    v = bench.vcycle_times(fs, prof, steps=3, iters=2, per_step_ms=20.0)
-    assert v["ms_per_cycle_without_transforms"] == pytest.approx((20.0 - 9.0 / 3) / 2)
+    prof = _prof(smooth=(10, 14.0, 6e9, 0), residual=(6, 7.0, 3e9, 0), dst=(2, 9.0, 5e9, 0))
+    v = bench.vcycle_times(fs, prof, steps=3, iters=2, per_step_ms=20.0, pk={"hbm_gbs": 1000.0})
+    ms = (20.0 - 9.0 / 3) / 2
+    assert v["ms_per_cycle_without_transforms"] == pytest.approx(ms)
     assert v["finest_level_kernel_ms_per_cycle"] == pytest.approx((12.0 + 6.0) / 3 / 2)
+    # the cycle's algorithmic bytes leave out the transforms too
+    assert v["alg_bytes_per_cycle"] == pytest.approx(9e9 / 3 / 2)
+    assert v["achieved_gbs"] == pytest.approx(9e9 / 3 / 2 / (ms / 1e3) / 1e9, rel=1e-3)
+    assert v["frac"] == pytest.approx(v["achieved_gbs"] / 1000.0, rel=1e-3)
+
+
+def test_windowed_load_equals_the_slice_of_the_full_load():
+    """The CPU baseline's workers draw only their own time steps of f."""
+    import numpy as np
+    from paper_1411_0519_gb300 import workloads
+    full = workloads.uniform_load(2, 15, 1, 32, seed=4)
+    for s0, s1 in [(0, 8), (8, 16), (24, 32), (5, 6)]:
+        assert np.array_equal(workloads.uniform_load_steps(2, 15, 1, 32, s0, s1, seed=4), full[s0:s1])
