@@ -420,14 +420,16 @@ def mesh_leg(args, torch, stmg, barrier, max_over_ranks, world, rank, level=7):
     """Example 2's protocol (Section 4) on the paper's own mesh family: the
     4-triangle square refined `level` times (P1, node basis), tau = 1,
     N = T = 1024, f = 0, iterate ~ U[0, 1] (seed = rank), the inexact block
-    inverse (one spatial V-cycle per step), to 1e-8; p_t = 1 and 3.  Each timed
-    solve starts from a copy of the same iterate (the copy is inside the timed
-    region, one vector)."""
+    inverse (one spatial V-cycle per step), to 1e-8; p_t = 1 and 3, in FP64 and
+    in the mixed form (FP32 cycles inside FP64 refinement).  Each timed solve
+    starts from a copy of the same iterate (the copy is inside the timed region,
+    one vector)."""
     out = {"workload": f"example2_mesh: 4 triangles refined {level} times, P1, N = 1024, tau = 1, f = 0, "
                        "iterate ~ U[0, 1], inexact block inverse (nu_x = 2, omega_x = 2/3)"}
     gen = torch.Generator(device="cuda")
-    for p in (1, 3):
-        s = stmg.MeshSolver(SQUARE_VERTS, SQUARE_CELLS, level, p, 1024, 1024.0, rtol=1e-8, maxit=40)
+    for p, prec in ((1, "fp64"), (3, "fp64"), (1, "mixed"), (3, "mixed")):
+        s = stmg.MeshSolver(SQUARE_VERTS, SQUARE_CELLS, level, p, 1024, 1024.0, rtol=1e-8, maxit=40,
+                            precision=prec, inner_cycles=args.inner_cycles)
         gen.manual_seed(rank)
         it0 = torch.rand(s.shape, dtype=torch.float64, device="cuda", generator=gen)
         u = torch.empty_like(it0)
@@ -447,9 +449,10 @@ def mesh_leg(args, torch, stmg, barrier, max_over_ranks, world, rank, level=7):
         e1.record(s.stream)
         e1.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1)) / nst
-        out["p_t=%d" % p] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
-                             "iters": it, "relres": rr, "dof": s.ndof, "nodes": s.Nx,
-                             "ms_per_cycle": ms / max(1, it), "levels": s.num_levels}
+        out["p_t=%d %s" % (p, prec)] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms,
+                                        "iters": it, "relres": rr, "dof": s.ndof, "nodes": s.Nx,
+                                        "ms_per_iteration": ms / max(1, it), "levels": s.num_levels,
+                                        "inner_cycles": args.inner_cycles if prec == "mixed" else None}
         s.close()
         del it0, u, fz
         torch.cuda.empty_cache()

@@ -38,8 +38,14 @@
  * by the caller; calls are asynchronous on the handle's stream except where a
  * host result is returned.  Levels: L = 0 coarsest, stm_num_levels() - 1 finest.
  *
- * Limits: p_t <= 3; precision ST_FP64; smoother ST_SMOOTH_VCYCLE (the exact
- * block inverse of a spatial mesh operator is not built); coarsest_steps = 1;
+ * Precision: ST_FP64, or ST_MIXED: inner_cycles FP32 cycles (every kernel of
+ * the cycle in FP32 with FP32 accumulation, the matrices and tables rounded to
+ * FP32) on the FP64 residual scaled by its norm, inside FP64 iterative
+ * refinement; the outer residual, the update and the coarsest solve stay FP64.
+ * The step-level calls below always run in FP64.
+ *
+ * Limits: p_t <= 3; smoother ST_SMOOTH_VCYCLE (the exact block inverse of a
+ * spatial mesh operator is not built); coarsest_steps = 1;
  * q times the interior vertices of the initial mesh at most 1024 (its exact
  * solve is a dense inverse formed at setup, one per space-time level).  Other options as in stmg.h (nu1, nu2,
  * omega, rtol, maxit, coarsening, nu_x, omega_x, gamma, max_workspace_bytes).
@@ -96,7 +102,9 @@ int stm_level_info(const stm_handle* h, int L, int* N_L, int* space_level, doubl
  * block 1 (eq. (equation1)); u0_ic may be NULL.  r may not alias u. */
 int stm_residual(stm_handle* h, const double* f, const double* u0_ic, const double* u, double* r);
 
-/* One cycle (Section 2, gamma of the options) on L u = f + IC, in place on u. */
+/* One cycle (Section 2, gamma of the options) on L u = f + IC, in place on u;
+ * with ST_MIXED one refinement step (FP64 residual, inner_cycles FP32 cycles,
+ * FP64 update). */
 int stm_vcycle(stm_handle* h, double* u, const double* f, const double* u0_ic);
 
 /* Cycles until ||r|| <= rtol ||r_0|| (Section 2).  flags: ST_INIT_GIVEN to

@@ -160,20 +160,32 @@ struct SpaceLevel {          // one mesh of the refinement (device arrays + host
   std::vector<double> mv_h, kv_h;
   int *rp = nullptr, *ci = nullptr;
   double *mv = nullptr, *kv = nullptr;
+  float *mv32 = nullptr, *kv32 = nullptr;             // mixed form: the entries rounded to FP32
   int *p0 = nullptr, *p1 = nullptr;                   // parents on the next coarser mesh (level >= 1)
   int *ch_rp = nullptr, *ch_ci = nullptr;             // children on the next finer mesh (level < top)
   double* ch_w = nullptr;
+  float* ch_w32 = nullptr;
+};
+
+template <typename T>
+struct Bufs {                // the vectors and tables of one space-time level in one precision
+  T *u = nullptr, *f = nullptr, *r = nullptr;   // FP64: u, f on coarse levels only; FP32: every level
+  std::vector<T*> dinv;      // per mesh level k = 1..l: Nx_k q x q inverses of the node blocks (index k)
+  T* a0inv = nullptr;        // dense inverse of A_tau on the initial mesh
+  std::vector<T*> sb, sx, sy;   // spatial V-cycle buffers per mesh level k = 0..l
 };
 
 struct MLevel {              // one space-time level
   int N = 0, l = 0, full = -1;
   double tau = 0.0, mu = 0.0;
   int64_t ndof = 0;
-  double *u = nullptr, *f = nullptr, *r = nullptr;    // u, f: coarse levels only
-  std::vector<double*> dinv;    // per mesh level k = 1..l: Nx_k q x q inverses of the node blocks (index k)
-  double* a0inv = nullptr;      // dense inverse of A_tau on the initial mesh
-  std::vector<double*> sb, sx, sy;   // spatial V-cycle buffers per mesh level k = 0..l
+  Bufs<double> d;            // FP64
+  Bufs<float> s;             // FP32 (mixed form)
 };
+
+template <typename T> Bufs<T>& bufs(MLevel& L);
+template <> Bufs<double>& bufs<double>(MLevel& L) { return L.d; }
+template <> Bufs<float>& bufs<float>(MLevel& L) { return L.s; }
 
 }  // namespace
 
@@ -234,25 +246,38 @@ T* upload(stm_handle* h, const std::vector<T>& src) {
   return d;
 }
 
-template <int Q>
-stmm::MTime<Q> mtime(const HostTime& t) {
-  stmm::MTime<Q> c{};
+// FP64 host values uploaded rounded to T
+template <typename T>
+T* upload_as(stm_handle* h, const std::vector<double>& src) {
+  std::vector<T> v(src.begin(), src.end());
+  return upload(h, v);
+}
+
+bool mixed(const stm_handle* h) { return h->opt.precision == ST_MIXED; }
+
+template <typename T, int Q>
+stmm::MTime<T, Q> mtime(const HostTime& t) {
+  stmm::MTime<T, Q> c{};
   for (int i = 0; i < Q * Q; ++i) {
-    c.K[i] = t.K[i];
-    c.R1[i] = t.R1[i];
-    c.R2[i] = t.R2[i];
+    c.K[i] = (T)t.K[i];
+    c.R1[i] = (T)t.R1[i];
+    c.R2[i] = (T)t.R2[i];
   }
   for (int i = 0; i < Q; ++i) {
-    c.Mh[i] = t.Mh[i];
-    c.st[i] = t.st[i];
-    c.en[i] = t.en[i];
+    c.Mh[i] = (T)t.Mh[i];
+    c.st[i] = (T)t.st[i];
+    c.en[i] = (T)t.en[i];
   }
   return c;
 }
 
-stmm::Csr csr(const SpaceLevel& s) { return stmm::Csr{s.rp, s.ci, s.mv, s.kv}; }
+template <typename T> stmm::Csr<T> csr(const SpaceLevel& s);
+template <> stmm::Csr<double> csr<double>(const SpaceLevel& s) { return {s.rp, s.ci, s.mv, s.kv}; }
+template <> stmm::Csr<float> csr<float>(const SpaceLevel& s) { return {s.rp, s.ci, s.mv32, s.kv32}; }
+template <typename T> stmm::Children<T> children(const SpaceLevel& s);
+template <> stmm::Children<double> children<double>(const SpaceLevel& s) { return {s.ch_rp, s.ch_ci, s.ch_w}; }
+template <> stmm::Children<float> children<float>(const SpaceLevel& s) { return {s.ch_rp, s.ch_ci, s.ch_w32}; }
 stmm::Parents parents(const SpaceLevel& s) { return stmm::Parents{s.p0, s.p1}; }
-stmm::Children children(const SpaceLevel& s) { return stmm::Children{s.ch_rp, s.ch_ci, s.ch_w}; }
 
 unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
@@ -262,6 +287,17 @@ void over_steps(int nodes, int steps, F&& launch) {
   for (int s0 = 0; s0 < steps; s0 += 65535) {
     dim3 grid(blocks_for(nodes), (unsigned)std::min(65535, steps - s0));
     launch(grid, s0);
+  }
+}
+
+// the same for kernels that take stmm::kMSteps consecutive steps per thread
+template <typename F>
+void over_step_blocks(int nodes, int steps, F&& launch) {
+  constexpr int TS = stmm::kMSteps;
+  const int nblk = (steps + TS - 1) / TS;
+  for (int b0 = 0; b0 < nblk; b0 += 65535) {
+    dim3 grid(blocks_for(nodes), (unsigned)std::min(65535, nblk - b0));
+    launch(grid, b0 * TS);
   }
 }
 
@@ -276,152 +312,176 @@ void over_steps(int nodes, int steps, F&& launch) {
     }                                                                  \
   } while (0)
 
+#define STM_TQ(T, FN, ...)                                             \
+  do {                                                                 \
+    switch (h->q) {                                                    \
+      case 1: FN<T, 1>(__VA_ARGS__); break;                            \
+      case 2: FN<T, 2>(__VA_ARGS__); break;                            \
+      case 3: FN<T, 3>(__VA_ARGS__); break;                            \
+      case 4: FN<T, 4>(__VA_ARGS__); break;                            \
+      default: fail(h, ST_EINVAL, "p_t > 3");                          \
+    }                                                                  \
+  } while (0)
+
 // ------------------------------------------------------------------ launches
-template <int Q>
-void l_residual(stm_handle* h, const MLevel& L, bool adj, const double* f, const double* u, double* r) {
+template <typename T, int Q>
+void l_residual(stm_handle* h, const MLevel& L, bool adj, const T* f, const T* u, T* r) {
   const SpaceLevel& s = h->sp[L.l];
-  const auto tc = mtime<Q>(h->tm);
-  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
-    if (adj) stmm::k_mresidual<Q, true><<<g, kThreads, 0, h->stream>>>(f, u, r, csr(s), s.Nx, L.N, s0, L.tau, tc);
-    else stmm::k_mresidual<Q, false><<<g, kThreads, 0, h->stream>>>(f, u, r, csr(s), s.Nx, L.N, s0, L.tau, tc);
+  const auto tc = mtime<T, Q>(h->tm);
+  over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
+    if (adj)
+      stmm::k_mresidual<T, Q, true><<<g, kThreads, 0, h->stream>>>(f, u, r, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, tc);
+    else
+      stmm::k_mresidual<T, Q, false><<<g, kThreads, 0, h->stream>>>(f, u, r, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, tc);
   });
 }
 
-template <int Q>
-void l_jacobi(stm_handle* h, const MLevel& L, int k, bool adj, bool zero, const double* b, const double* x,
-              double* y) {
+template <typename T, int Q>
+void l_jacobi(stm_handle* h, MLevel& L, int k, bool adj, bool zero, const T* b, const T* x, T* y) {
   const SpaceLevel& s = h->sp[k];
-  const auto tc = mtime<Q>(h->tm);
-  const double w = h->opt.omega_x;
-  const double* D = L.dinv[k];
-  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
-#define STM_JAC(A, Z) \
-  stmm::k_mjacobi<Q, A, Z><<<g, kThreads, 0, h->stream>>>(b, x, y, csr(s), s.Nx, L.N, s0, L.tau, w, D, tc)
+  const auto tc = mtime<T, Q>(h->tm);
+  const T w = (T)h->opt.omega_x;
+  const T* D = bufs<T>(L).dinv[k];
+  over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
+#define STM_JAC(A, Z)                                                                                        \
+  stmm::k_mjacobi<T, Q, A, Z><<<g, kThreads, 0, h->stream>>>(b, x, y, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, w, D, \
+                                                              tc)
     if (adj) { if (zero) STM_JAC(true, true); else STM_JAC(true, false); }
     else { if (zero) STM_JAC(false, true); else STM_JAC(false, false); }
 #undef STM_JAC
   });
 }
 
-template <int Q>
-void l_residual_jacobi0(stm_handle* h, const MLevel& L, bool adj, const double* f, const double* u, double* r,
-                        double* x) {
+template <typename T, int Q>
+void l_residual_jacobi0(stm_handle* h, MLevel& L, bool adj, const T* f, const T* u, T* r, T* x) {
   const SpaceLevel& s = h->sp[L.l];
-  const auto tc = mtime<Q>(h->tm);
-  const double* D = L.dinv[L.l];
-  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
+  const auto tc = mtime<T, Q>(h->tm);
+  const T* D = bufs<T>(L).dinv[L.l];
+  over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
     if (adj)
-      stmm::k_mresidual_jacobi0<Q, true><<<g, kThreads, 0, h->stream>>>(f, u, r, x, csr(s), s.Nx, L.N, s0, L.tau,
-                                                                          h->opt.omega_x, D, tc);
+      stmm::k_mresidual_jacobi0<T, Q, true><<<g, kThreads, 0, h->stream>>>(
+          f, u, r, x, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, D, tc);
     else
-      stmm::k_mresidual_jacobi0<Q, false><<<g, kThreads, 0, h->stream>>>(f, u, r, x, csr(s), s.Nx, L.N, s0, L.tau,
-                                                                           h->opt.omega_x, D, tc);
+      stmm::k_mresidual_jacobi0<T, Q, false><<<g, kThreads, 0, h->stream>>>(
+          f, u, r, x, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, D, tc);
   });
 }
 
-template <int Q>
-void l_jacobi_update(stm_handle* h, const MLevel& L, bool adj, const double* b, const double* x, double* u) {
+template <typename T, int Q>
+void l_jacobi_update(stm_handle* h, MLevel& L, bool adj, const T* b, const T* x, T* u) {
   const SpaceLevel& s = h->sp[L.l];
-  const auto tc = mtime<Q>(h->tm);
-  const double* D = L.dinv[L.l];
-  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
+  const auto tc = mtime<T, Q>(h->tm);
+  const T* D = bufs<T>(L).dinv[L.l];
+  over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
     if (adj)
-      stmm::k_mjacobi_update<Q, true><<<g, kThreads, 0, h->stream>>>(b, x, u, csr(s), s.Nx, L.N, s0, L.tau,
-                                                                       h->opt.omega_x, h->opt.omega, D, tc);
+      stmm::k_mjacobi_update<T, Q, true><<<g, kThreads, 0, h->stream>>>(
+          b, x, u, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, (T)h->opt.omega, D, tc);
     else
-      stmm::k_mjacobi_update<Q, false><<<g, kThreads, 0, h->stream>>>(b, x, u, csr(s), s.Nx, L.N, s0, L.tau,
-                                                                        h->opt.omega_x, h->opt.omega, D, tc);
+      stmm::k_mjacobi_update<T, Q, false><<<g, kThreads, 0, h->stream>>>(
+          b, x, u, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, (T)h->opt.omega, D, tc);
   });
 }
 
-template <int Q>
-void l_space_residual(stm_handle* h, const MLevel& L, int k, bool adj, const double* b, const double* x, double* r) {
+template <typename T, int Q>
+void l_space_residual(stm_handle* h, const MLevel& L, int k, bool adj, const T* b, const T* x, T* r) {
   const SpaceLevel& s = h->sp[k];
-  const auto tc = mtime<Q>(h->tm);
-  over_steps(s.Nx, L.N, [&](dim3 g, int s0) {
-    if (adj) stmm::k_mspace_residual<Q, true><<<g, kThreads, 0, h->stream>>>(b, x, r, csr(s), s.Nx, L.N, s0, L.tau, tc);
-    else stmm::k_mspace_residual<Q, false><<<g, kThreads, 0, h->stream>>>(b, x, r, csr(s), s.Nx, L.N, s0, L.tau, tc);
+  const auto tc = mtime<T, Q>(h->tm);
+  over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
+    if (adj)
+      stmm::k_mspace_residual<T, Q, true><<<g, kThreads, 0, h->stream>>>(b, x, r, csr<T>(s), s.Nx, L.N, s0,
+                                                                           (T)L.tau, tc);
+    else
+      stmm::k_mspace_residual<T, Q, false><<<g, kThreads, 0, h->stream>>>(b, x, r, csr<T>(s), s.Nx, L.N, s0,
+                                                                            (T)L.tau, tc);
   });
 }
 
-template <int Q>
-void l_restrict_space(stm_handle* h, const MLevel& L, int k, const double* r, double* bc) {
+template <typename T, int Q>
+void l_restrict_space(stm_handle* h, const MLevel& L, int k, const T* r, T* bc) {
   const SpaceLevel& c = h->sp[k - 1];
   const SpaceLevel& f = h->sp[k];
   over_steps(c.Nx, L.N, [&](dim3 g, int s0) {
-    stmm::k_mrestrict_space<Q><<<g, kThreads, 0, h->stream>>>(r, bc, children(c), c.Nx, f.Nx, L.N, s0);
+    stmm::k_mrestrict_space<T, Q><<<g, kThreads, 0, h->stream>>>(r, bc, children<T>(c), c.Nx, f.Nx, L.N, s0);
   });
 }
 
-template <int Q>
-void l_prolong_space_add(stm_handle* h, const MLevel& L, int k, const double* xc, double* x) {
+template <typename T, int Q>
+void l_prolong_space_add(stm_handle* h, const MLevel& L, int k, const T* xc, T* x) {
   const SpaceLevel& c = h->sp[k - 1];
   const SpaceLevel& f = h->sp[k];
   over_steps(f.Nx, L.N, [&](dim3 g, int s0) {
-    stmm::k_mprolong_space_add<Q><<<g, kThreads, 0, h->stream>>>(xc, x, parents(f), c.Nx, f.Nx, L.N, s0);
+    stmm::k_mprolong_space_add<T, Q><<<g, kThreads, 0, h->stream>>>(xc, x, parents(f), c.Nx, f.Nx, L.N, s0);
   });
 }
 
-void l_dense(stm_handle* h, const MLevel& L, bool adj, const double* b, double* y) {
+template <typename T>
+void l_dense(stm_handle* h, MLevel& L, bool adj, const T* b, T* y) {
   const int n = h->q * h->sp[0].Nx;
+  const T* ainv = bufs<T>(L).a0inv;
   over_steps(n, L.N, [&](dim3 g, int s0) {
-    stmm::k_mdense_apply<<<g, kThreads, 0, h->stream>>>(b, y, L.a0inv, n, L.N, s0, adj);
+    stmm::k_mdense_apply<T><<<g, kThreads, 0, h->stream>>>(b, y, ainv, n, L.N, s0, adj);
   });
 }
 
-template <int Q>
-void l_restrict(stm_handle* h, int Li, const double* r, double* fc) {
+template <typename T, int Q>
+void l_restrict(stm_handle* h, int Li, const T* r, T* fc) {
   const MLevel& F = h->lv[Li];
   const MLevel& C = h->lv[Li - 1];
   const SpaceLevel& cs = h->sp[C.l];
   const SpaceLevel& fs = h->sp[F.l];
-  const auto tc = mtime<Q>(h->tm);
+  const auto tc = mtime<T, Q>(h->tm);
   over_steps(cs.Nx, C.N, [&](dim3 g, int m0) {
     if (F.l != C.l)
-      stmm::k_mrestrict<Q, true><<<g, kThreads, 0, h->stream>>>(r, fc, children(cs), cs.Nx, fs.Nx, C.N, m0, tc);
+      stmm::k_mrestrict<T, Q, true><<<g, kThreads, 0, h->stream>>>(r, fc, children<T>(cs), cs.Nx, fs.Nx, C.N, m0,
+                                                                     tc);
     else
-      stmm::k_mrestrict<Q, false><<<g, kThreads, 0, h->stream>>>(r, fc, children(cs), cs.Nx, fs.Nx, C.N, m0, tc);
+      stmm::k_mrestrict<T, Q, false><<<g, kThreads, 0, h->stream>>>(r, fc, children<T>(cs), cs.Nx, fs.Nx, C.N, m0,
+                                                                      tc);
   });
 }
 
-template <int Q>
-void l_prolong(stm_handle* h, int Li, const double* ec, double* u) {
+template <typename T, int Q>
+void l_prolong(stm_handle* h, int Li, const T* ec, T* u) {
   const MLevel& F = h->lv[Li];
   const MLevel& C = h->lv[Li - 1];
   const SpaceLevel& cs = h->sp[C.l];
   const SpaceLevel& fs = h->sp[F.l];
-  const auto tc = mtime<Q>(h->tm);
+  const auto tc = mtime<T, Q>(h->tm);
   over_steps(fs.Nx, C.N, [&](dim3 g, int m0) {
     if (F.l != C.l)
-      stmm::k_mprolong<Q, true><<<g, kThreads, 0, h->stream>>>(ec, u, parents(fs), cs.Nx, fs.Nx, C.N, m0, tc);
+      stmm::k_mprolong<T, Q, true><<<g, kThreads, 0, h->stream>>>(ec, u, parents(fs), cs.Nx, fs.Nx, C.N, m0, tc);
     else
-      stmm::k_mprolong<Q, false><<<g, kThreads, 0, h->stream>>>(ec, u, parents(fs), cs.Nx, fs.Nx, C.N, m0, tc);
+      stmm::k_mprolong<T, Q, false><<<g, kThreads, 0, h->stream>>>(ec, u, parents(fs), cs.Nx, fs.Nx, C.N, m0, tc);
   });
 }
 
 template <int Q>
 void l_add_ic(stm_handle* h, const double* f, const double* u0, double* g) {
   const SpaceLevel& s = h->sp.back();
-  const auto tc = mtime<Q>(h->tm);
-  stmm::k_madd_ic<Q><<<blocks_for(s.Nx), kThreads, 0, h->stream>>>(f, u0, g, csr(s), s.Nx, tc);
+  const auto tc = mtime<double, Q>(h->tm);
+  stmm::k_madd_ic<Q><<<blocks_for(s.Nx), kThreads, 0, h->stream>>>(f, u0, g, csr<double>(s), s.Nx, tc);
 }
 
 template <int Q>
 void l_ic_gradient(stm_handle* h, const double* lam, double* g) {
   const SpaceLevel& s = h->sp.back();
-  const auto tc = mtime<Q>(h->tm);
-  stmm::k_mic_gradient<Q><<<blocks_for(s.Nx), kThreads, 0, h->stream>>>(lam, g, csr(s), s.Nx, tc);
+  const auto tc = mtime<double, Q>(h->tm);
+  stmm::k_mic_gradient<Q><<<blocks_for(s.Nx), kThreads, 0, h->stream>>>(lam, g, csr<double>(s), s.Nx, tc);
 }
 
-void copy(stm_handle* h, double* y, const double* x, int64_t n) {
-  check(h, cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream), "copy");
+template <typename T>
+void copy(stm_handle* h, T* y, const T* x, int64_t n) {
+  check(h, cudaMemcpyAsync(y, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream), "copy");
 }
-void zero(stm_handle* h, double* y, int64_t n) {
-  check(h, cudaMemsetAsync(y, 0, sizeof(double) * n, h->stream), "memset");
+template <typename T>
+void zero(stm_handle* h, T* y, int64_t n) {
+  check(h, cudaMemsetAsync(y, 0, sizeof(T) * n, h->stream), "memset");
 }
-void axpy(stm_handle* h, double* y, const double* x, double a, int64_t n) {
-  stmg::k_axpy<double><<<(unsigned)std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, n);
+template <typename T>
+void axpy(stm_handle* h, T* y, const T* x, T a, int64_t n) {
+  stmg::k_axpy<T><<<(unsigned)std::min<int64_t>(blocks_for(n), 152 * 16), kThreads, 0, h->stream>>>(y, x, a, n);
 }
+unsigned vec_grid(int64_t n) { return (unsigned)std::min<int64_t>(blocks_for(n), 152 * 16); }
 
 double norm2(stm_handle* h, const double* x, int64_t n) {
   stmg::k_sumsq_partial<double><<<kNormBlocks, kThreads, 0, h->stream>>>(x, n, h->partial);
@@ -435,40 +495,41 @@ double norm2(stm_handle* h, const double* x, int64_t n) {
 // One spatial V-cycle on mesh levels k, k-1, ..., 0 for every time step of
 // space-time level L (the inexact block inverse, Remark on the V-cycle
 // approximation in space): x = D~^{-1} b from a zero guess.  Returns the buffer
-// that holds the result (one of L.sx[k], L.sy[k]); b is not modified.
-// x0_done: L.sx[k] already holds the first sweep omega_x D^{-1} b (fused into the
+// that holds the result (one of the level's sx[k], sy[k]); b is not modified.
+// x0_done: sx[k] already holds the first sweep omega_x D^{-1} b (fused into the
 // residual pass).  update: instead of returning the result, the last sweep adds
 // omega_t times it into `update` (the damped step of the smoother) and nullptr is
 // returned.
-const double* space_vcycle(stm_handle* h, MLevel& L, int k, bool adj, const double* b, bool x0_done = false,
-                           double* update = nullptr) {
+template <typename T>
+const T* space_vcycle(stm_handle* h, MLevel& L, int k, bool adj, const T* b, bool x0_done = false,
+                      T* update = nullptr) {
+  Bufs<T>& B = bufs<T>(L);
   if (k == 0) {
+    l_dense<T>(h, L, adj, b, B.sx[0]);
     if (update) {
-      l_dense(h, L, adj, b, L.sx[0]);
-      axpy(h, update, L.sx[0], h->opt.omega, L.ndof);
+      axpy<T>(h, update, B.sx[0], (T)h->opt.omega, L.ndof);
       return nullptr;
     }
-    l_dense(h, L, adj, b, L.sx[0]);
-    return L.sx[0];
+    return B.sx[0];
   }
-  double* x = L.sx[k];
-  double* y = L.sy[k];
+  T* x = B.sx[k];
+  T* y = B.sy[k];
   const int nu = std::max(1, h->opt.nu_x);
-  if (!x0_done) STM_Q(l_jacobi, h, L, k, adj, true, b, (const double*)nullptr, x);
+  if (!x0_done) STM_TQ(T, l_jacobi, h, L, k, adj, true, b, (const T*)nullptr, x);
   for (int i = 1; i < nu; ++i) {
-    STM_Q(l_jacobi, h, L, k, adj, false, b, x, y);
+    STM_TQ(T, l_jacobi, h, L, k, adj, false, b, x, y);
     std::swap(x, y);
   }
-  STM_Q(l_space_residual, h, L, k, adj, b, x, y);        // y = b - A x
-  STM_Q(l_restrict_space, h, L, k, y, L.sb[k - 1]);
-  const double* xc = space_vcycle(h, L, k - 1, adj, L.sb[k - 1]);
-  STM_Q(l_prolong_space_add, h, L, k, xc, x);
+  STM_TQ(T, l_space_residual, h, L, k, adj, b, x, y);        // y = b - A x
+  STM_TQ(T, l_restrict_space, h, L, k, y, B.sb[k - 1]);
+  const T* xc = space_vcycle<T>(h, L, k - 1, adj, B.sb[k - 1]);
+  STM_TQ(T, l_prolong_space_add, h, L, k, xc, x);
   for (int i = 0; i < nu; ++i) {
     if (update != nullptr && i == nu - 1) {
-      STM_Q(l_jacobi_update, h, L, adj, b, x, update);
+      STM_TQ(T, l_jacobi_update, h, L, adj, b, x, update);
       return nullptr;
     }
-    STM_Q(l_jacobi, h, L, k, adj, false, b, x, y);
+    STM_TQ(T, l_jacobi, h, L, k, adj, false, b, x, y);
     std::swap(x, y);
   }
   return x;
@@ -477,60 +538,80 @@ const double* space_vcycle(stm_handle* h, MLevel& L, int k, bool adj, const doub
 // u <- u + omega D~^{-1} (f - L u), nu times (eq. chap4_smoother).  On a level
 // whose mesh is refined, the residual pass also takes the first Jacobi sweep of
 // the spatial V-cycle and the last sweep adds into u directly.
-void smooth(stm_handle* h, int Li, bool adj, double* u, const double* f, int nu) {
+template <typename T>
+void smooth(stm_handle* h, int Li, bool adj, T* u, const T* f, int nu) {
   MLevel& L = h->lv[Li];
+  Bufs<T>& B = bufs<T>(L);
   for (int i = 0; i < nu; ++i) {
     if (L.l >= 1) {
-      STM_Q(l_residual_jacobi0, h, L, adj, f, u, L.r, L.sx[L.l]);
-      space_vcycle(h, L, L.l, adj, L.r, true, u);
+      STM_TQ(T, l_residual_jacobi0, h, L, adj, f, u, B.r, B.sx[L.l]);
+      space_vcycle<T>(h, L, L.l, adj, (const T*)B.r, true, u);
     } else {
-      STM_Q(l_residual, h, L, adj, f, u, L.r);
-      const double* d = space_vcycle(h, L, L.l, adj, L.r);
-      axpy(h, u, d, h->opt.omega, L.ndof);
+      STM_TQ(T, l_residual, h, L, adj, f, u, B.r);
+      const T* d = space_vcycle<T>(h, L, L.l, adj, (const T*)B.r);
+      axpy<T>(h, u, d, (T)h->opt.omega, L.ndof);
     }
   }
 }
 
-// Exact solve on the coarsest level (one time step): A u = f by spatial
+// Exact solve on the coarsest level (one time step) in FP64: A u = f by spatial
 // V-cycles repeated until the residual stops decreasing below 1e-13 ||f||
-// (one V-cycle is exact on the initial mesh).
-void coarsest(stm_handle* h, bool adj, double* u, const double* f) {
+// (one V-cycle is exact when the level's mesh is the initial one).
+void coarsest64(stm_handle* h, bool adj, double* u, const double* f) {
   MLevel& L = h->lv[0];
   if (L.l == 0) {
-    l_dense(h, L, adj, f, u);
+    l_dense<double>(h, L, adj, f, u);
     return;
   }
-  zero(h, u, L.ndof);
-  copy(h, L.r, f, L.ndof);
+  zero<double>(h, u, L.ndof);
+  copy<double>(h, L.d.r, f, L.ndof);
   const double f0 = norm2(h, f, L.ndof);
   if (f0 == 0.0) return;
   double prev = f0;
   for (int it = 0; it < 100; ++it) {
-    const double* d = space_vcycle(h, L, L.l, adj, L.r);
-    axpy(h, u, d, 1.0, L.ndof);
-    STM_Q(l_space_residual, h, L, L.l, adj, f, u, L.r);
-    const double rn = norm2(h, L.r, L.ndof);
+    const double* d = space_vcycle<double>(h, L, L.l, adj, L.d.r);
+    axpy<double>(h, u, d, 1.0, L.ndof);
+    STM_TQ(double, l_space_residual, h, L, L.l, adj, f, u, L.d.r);
+    const double rn = norm2(h, L.d.r, L.ndof);
     if (!std::isfinite(rn)) fail(h, ST_ENAN, "coarsest solve: residual not finite");
     if (rn <= 1e-15 * f0 || (rn <= 1e-13 * f0 && rn > 0.5 * prev)) break;
     prev = rn;
   }
 }
 
-void vcycle(stm_handle* h, int Li, bool adj, double* u, const double* f, bool u_zero) {
+// The coarsest solve of the FP32 cycles runs in FP64 (the FP64 buffers of level 0).
+template <typename T>
+void coarsest(stm_handle* h, bool adj, T* u, const T* f);
+template <>
+void coarsest<double>(stm_handle* h, bool adj, double* u, const double* f) {
+  coarsest64(h, adj, u, f);
+}
+template <>
+void coarsest<float>(stm_handle* h, bool adj, float* u, const float* f) {
+  MLevel& L = h->lv[0];
+  stmg::k_cast_up<<<vec_grid(L.ndof), kThreads, 0, h->stream>>>(L.d.f, f, L.ndof);
+  coarsest64(h, adj, L.d.u, L.d.f);
+  stmg::k_cast_down<<<vec_grid(L.ndof), kThreads, 0, h->stream>>>(u, L.d.u, 1.0, L.ndof);
+}
+
+template <typename T>
+void vcycle(stm_handle* h, int Li, bool adj, T* u, const T* f, bool u_zero) {
   if (Li == 0) {
-    coarsest(h, adj, u, f);
+    coarsest<T>(h, adj, u, f);
     return;
   }
   MLevel& L = h->lv[Li];
-  if (u_zero) zero(h, u, L.ndof);
-  smooth(h, Li, adj, u, f, h->opt.nu1);
-  STM_Q(l_residual, h, L, adj, f, u, L.r);
+  if (u_zero) zero<T>(h, u, L.ndof);
+  smooth<T>(h, Li, adj, u, f, h->opt.nu1);
+  Bufs<T>& B = bufs<T>(L);
+  STM_TQ(T, l_residual, h, L, adj, f, (const T*)u, B.r);
   MLevel& C = h->lv[Li - 1];
-  STM_Q(l_restrict, h, Li, L.r, C.f);
+  Bufs<T>& CB = bufs<T>(C);
+  STM_TQ(T, l_restrict, h, Li, (const T*)B.r, CB.f);
   const int reps = (Li - 1 == 0) ? 1 : std::max(1, h->opt.gamma);
-  for (int g = 0; g < reps; ++g) vcycle(h, Li - 1, adj, C.u, C.f, g == 0);
-  STM_Q(l_prolong, h, Li, C.u, u);
-  smooth(h, Li, adj, u, f, h->opt.nu2);
+  for (int g = 0; g < reps; ++g) vcycle<T>(h, Li - 1, adj, CB.u, (const T*)CB.f, g == 0);
+  STM_TQ(T, l_prolong, h, Li, (const T*)CB.u, u);
+  smooth<T>(h, Li, adj, u, f, h->opt.nu2);
 }
 
 MLevel& finest(stm_handle* h) { return h->lv.back(); }
@@ -539,26 +620,38 @@ MLevel& finest(stm_handle* h) { return h->lv.back(); }
 const double* with_ic(stm_handle* h, const double* f, const double* u0) {
   if (u0 == nullptr) return f;
   MLevel& F = finest(h);
-  copy(h, h->feff, f, F.ndof);
+  copy<double>(h, h->feff, f, F.ndof);
   STM_Q(l_add_ic, h, f, u0, h->feff);
   return h->feff;
+}
+
+// One refinement step of the mixed form: given the FP64 residual r (norm s > 0)
+// of the finest level, inner_cycles FP32 cycles on L e = r / s from e = 0, then
+// u += s e in FP64.
+void mixed_step(stm_handle* h, bool adj, double* u, const double* r, double s) {
+  MLevel& F = finest(h);
+  const int top = (int)h->lv.size() - 1;
+  stmg::k_cast_down<<<vec_grid(F.ndof), kThreads, 0, h->stream>>>(F.s.f, r, 1.0 / s, F.ndof);
+  for (int c = 0; c < std::max(1, h->opt.inner_cycles); ++c) vcycle<float>(h, top, adj, F.s.u, F.s.f, c == 0);
+  stmg::k_axpy_up<<<vec_grid(F.ndof), kThreads, 0, h->stream>>>(u, F.s.u, s, F.ndof);
 }
 
 int solve_impl(stm_handle* h, bool adj, const double* f, double* u, bool given, int* iters, double* relres) {
   MLevel& F = finest(h);
   const int top = (int)h->lv.size() - 1;
-  if (!given) zero(h, u, F.ndof);
-  STM_Q(l_residual, h, F, adj, f, u, F.r);
-  const double r0 = norm2(h, F.r, F.ndof);
+  if (!given) zero<double>(h, u, F.ndof);
+  STM_TQ(double, l_residual, h, F, adj, f, (const double*)u, F.d.r);
+  const double r0 = norm2(h, F.d.r, F.ndof);
   double rn = r0;
   int it = 0, status = ST_OK;
   if (!std::isfinite(r0)) status = ST_ENAN;
   while (status == ST_OK && r0 > 0.0 && rn > h->opt.rtol * r0) {
     if (it >= h->opt.maxit) { status = ST_ENOTCONV; h->err = "maxit reached"; break; }
-    vcycle(h, top, adj, u, f, false);
+    if (mixed(h)) mixed_step(h, adj, u, F.d.r, rn);
+    else vcycle<double>(h, top, adj, u, f, false);
     ++it;
-    STM_Q(l_residual, h, F, adj, f, u, F.r);
-    rn = norm2(h, F.r, F.ndof);
+    STM_TQ(double, l_residual, h, F, adj, f, (const double*)u, F.d.r);
+    rn = norm2(h, F.d.r, F.ndof);
     if (!std::isfinite(rn)) { status = ST_ENAN; h->err = "residual norm is not finite"; break; }
     if (rn > 1e6 * r0) { status = ST_ENOTCONV; h->err = "residual grew by 1e6"; break; }
   }
@@ -608,7 +701,8 @@ const char* check_args(const st_simplex_mesh* m, int refinements, int p_t, int N
   if (p_t < 0 || p_t + 1 > kMaxQ) return "p_t must be 0 ... 3";
   if (N < 1 || N > 32768 || (N & (N - 1))) return "N must be a power of 2 up to 32768";
   if (!(T > 0.0)) return "T must be positive";
-  if (o.precision != ST_FP64) return "precision must be ST_FP64";
+  if (o.precision != ST_FP64 && o.precision != ST_MIXED) return "precision must be ST_FP64 or ST_MIXED";
+  if (o.inner_cycles < 0) return "inner_cycles must be >= 0";
   if (o.smoother != ST_SMOOTH_VCYCLE) return "smoother must be ST_SMOOTH_VCYCLE";
   if (o.coarsest_steps != 1) return "coarsest_steps must be 1";
   if (o.nu1 < 0 || o.nu2 < 0 || o.nu_x < 1 || o.maxit < 0 || !(o.rtol >= 0.0) || o.gamma < 1 || o.gamma > 2)
@@ -709,6 +803,10 @@ void build(stm_handle* h, const st_simplex_mesh* m0, int refinements) {
     s.ci = upload(h, s.ci_h);
     s.mv = upload(h, s.mv_h);
     s.kv = upload(h, s.kv_h);
+    if (mixed(h)) {
+      s.mv32 = upload_as<float>(h, s.mv_h);
+      s.kv32 = upload_as<float>(h, s.kv_h);
+    }
     if (lvl > 0) {
       // parents of every interior vertex on the previous mesh
       SpaceLevel& c = h->sp.back();
@@ -744,6 +842,7 @@ void build(stm_handle* h, const st_simplex_mesh* m0, int refinements) {
       c.ch_rp = upload(h, crp);
       c.ch_ci = upload(h, cci);
       c.ch_w = upload(h, cw);
+      if (mixed(h)) c.ch_w32 = upload_as<float>(h, cw);
     }
     prev_pos = pos;
     h->sp.push_back(std::move(s));
@@ -783,24 +882,41 @@ void build(stm_handle* h, const st_simplex_mesh* m0, int refinements) {
     L.full = (i == nl - 1) ? -1 : plan[nl - 2 - i].full;
     L.ndof = (int64_t)p.N * q * h->sp[p.l].Nx;
   }
-  // workspace and per-level tables
+  // workspace and per-level tables (FP64 always; the mixed form adds FP32 copies)
+  const bool mx = mixed(h);
   for (int i = 0; i < nl; ++i) {
     MLevel& L = h->lv[i];
     const bool top = i == nl - 1;
-    if (!top) {
-      L.u = dalloc<double>(h, L.ndof);
-      L.f = dalloc<double>(h, L.ndof);
+    if (!top || i == 0) {   // level 0 keeps FP64 u, f for the FP64 coarsest solve of the FP32 cycles
+      L.d.u = dalloc<double>(h, L.ndof);
+      L.d.f = dalloc<double>(h, L.ndof);
     }
-    L.r = dalloc<double>(h, L.ndof);
-    L.sb.assign(L.l + 1, nullptr);
-    L.sx.assign(L.l + 1, nullptr);
-    L.sy.assign(L.l + 1, nullptr);
-    L.dinv.assign(L.l + 1, nullptr);
+    L.d.r = dalloc<double>(h, L.ndof);
+    if (mx) {
+      L.s.u = dalloc<float>(h, L.ndof);
+      L.s.f = dalloc<float>(h, L.ndof);
+      L.s.r = dalloc<float>(h, L.ndof);
+    }
+    for (Bufs<double>* B : {&L.d}) {
+      B->sb.assign(L.l + 1, nullptr);
+      B->sx.assign(L.l + 1, nullptr);
+      B->sy.assign(L.l + 1, nullptr);
+      B->dinv.assign(L.l + 1, nullptr);
+    }
+    L.s.sb.assign(L.l + 1, nullptr);
+    L.s.sx.assign(L.l + 1, nullptr);
+    L.s.sy.assign(L.l + 1, nullptr);
+    L.s.dinv.assign(L.l + 1, nullptr);
     for (int kk = 0; kk <= L.l; ++kk) {
       const int64_t n = (int64_t)L.N * q * h->sp[kk].Nx;
-      L.sx[kk] = dalloc<double>(h, n);
-      if (kk >= 1) L.sy[kk] = dalloc<double>(h, n);
-      if (kk < L.l) L.sb[kk] = dalloc<double>(h, n);
+      L.d.sx[kk] = dalloc<double>(h, n);
+      if (kk >= 1) L.d.sy[kk] = dalloc<double>(h, n);
+      if (kk < L.l) L.d.sb[kk] = dalloc<double>(h, n);
+      if (mx) {
+        L.s.sx[kk] = dalloc<float>(h, n);
+        if (kk >= 1) L.s.sy[kk] = dalloc<float>(h, n);
+        if (kk < L.l) L.s.sb[kk] = dalloc<float>(h, n);
+      }
       if (kk >= 1) {   // node blocks D_j = (M_h)_jj K_tau + (K_h)_jj M_tau, inverted
         const SpaceLevel& s = h->sp[kk];
         std::vector<double> tab((size_t)s.Nx * q * q);
@@ -812,7 +928,8 @@ void build(stm_handle* h, const st_simplex_mesh* m0, int refinements) {
           if (!invert(D, q)) fail(h, ST_EINVAL, "singular node block");
           std::copy(D.begin(), D.end(), tab.begin() + (size_t)j * q * q);
         }
-        L.dinv[kk] = upload(h, tab);
+        L.d.dinv[kk] = upload(h, tab);
+        if (mx) L.s.dinv[kk] = upload_as<float>(h, tab);
       }
     }
     {   // dense inverse of A_tau = K_tau (x) M_0 + M_tau (x) K_0 on the initial mesh
@@ -828,7 +945,8 @@ void build(stm_handle* h, const st_simplex_mesh* m0, int refinements) {
                   h->tm.K[a * q + b] * s0.mv_h[e] + (a == b ? L.tau * h->tm.Mh[a] * s0.kv_h[e] : 0.0);
         }
       if (!invert(A, n)) fail(h, ST_EINVAL, "singular block on the initial mesh");
-      L.a0inv = upload(h, A);
+      L.d.a0inv = upload(h, A);
+      if (mx) L.s.a0inv = upload_as<float>(h, A);
     }
   }
   h->partial = dalloc<double>(h, kNormBlocks);
@@ -920,7 +1038,7 @@ int stm_residual(stm_handle* h, const double* f, const double* u0_ic, const doub
   return guarded(h, [&]() -> int {
     if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
     const double* g = with_ic(h, f, u0_ic);
-    STM_Q(l_residual, h, finest(h), false, g, u, r);
+    STM_TQ(double, l_residual, h, finest(h), false, g, u, r);
     return ST_OK;
   });
 }
@@ -929,7 +1047,15 @@ int stm_vcycle(stm_handle* h, double* u, const double* f, const double* u0_ic) {
   return guarded(h, [&]() -> int {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
     const double* g = with_ic(h, f, u0_ic);
-    vcycle(h, (int)h->lv.size() - 1, false, u, g, false);
+    if (mixed(h)) {   // one refinement step
+      MLevel& F = finest(h);
+      STM_TQ(double, l_residual, h, F, false, g, (const double*)u, F.d.r);
+      const double rn = norm2(h, F.d.r, F.ndof);
+      if (!std::isfinite(rn)) fail(h, ST_ENAN, "residual norm is not finite");
+      if (rn > 0.0) mixed_step(h, false, u, F.d.r, rn);
+      return ST_OK;
+    }
+    vcycle<double>(h, (int)h->lv.size() - 1, false, u, g, false);
     return ST_OK;
   });
 }
@@ -954,7 +1080,7 @@ int stm_adjoint_solve(stm_handle* h, const double* g, double* lambda, double* gr
 int stm_level_residual(stm_handle* h, int L, int adjoint, const double* f, const double* u, double* r) {
   return guarded(h, [&]() -> int {
     if (!f || !u || !r) fail(h, ST_EINVAL, "null pointer");
-    STM_Q(l_residual, h, h->lv[level_index(h, L)], adjoint != 0, f, u, r);
+    STM_TQ(double, l_residual, h, h->lv[level_index(h, L)], adjoint != 0, f, u, r);
     return ST_OK;
   });
 }
@@ -963,8 +1089,8 @@ int stm_level_block_solve(stm_handle* h, int L, int adjoint, const double* r, do
   return guarded(h, [&]() -> int {
     if (!r || !d) fail(h, ST_EINVAL, "null pointer");
     MLevel& lv = h->lv[level_index(h, L)];
-    const double* x = space_vcycle(h, lv, lv.l, adjoint != 0, r);
-    copy(h, d, x, lv.ndof);
+    const double* x = space_vcycle<double>(h, lv, lv.l, adjoint != 0, r);
+    copy<double>(h, d, x, lv.ndof);
     return ST_OK;
   });
 }
@@ -972,7 +1098,7 @@ int stm_level_block_solve(stm_handle* h, int L, int adjoint, const double* r, do
 int stm_level_smooth(stm_handle* h, int L, int adjoint, int nu, const double* f, double* u) {
   return guarded(h, [&]() -> int {
     if (!f || !u || nu < 0) fail(h, ST_EINVAL, "invalid argument");
-    smooth(h, level_index(h, L), adjoint != 0, u, f, nu);
+    smooth<double>(h, level_index(h, L), adjoint != 0, u, f, nu);
     return ST_OK;
   });
 }
@@ -980,7 +1106,7 @@ int stm_level_smooth(stm_handle* h, int L, int adjoint, int nu, const double* f,
 int stm_level_restrict(stm_handle* h, int L, const double* r_fine, double* f_coarse) {
   return guarded(h, [&]() -> int {
     if (!r_fine || !f_coarse || level_index(h, L) < 1) fail(h, ST_EINVAL, "invalid argument");
-    STM_Q(l_restrict, h, L, r_fine, f_coarse);
+    STM_TQ(double, l_restrict, h, L, r_fine, f_coarse);
     return ST_OK;
   });
 }
@@ -988,7 +1114,7 @@ int stm_level_restrict(stm_handle* h, int L, const double* r_fine, double* f_coa
 int stm_level_prolong(stm_handle* h, int L, const double* e_coarse, double* u_fine) {
   return guarded(h, [&]() -> int {
     if (!e_coarse || !u_fine || level_index(h, L) < 1) fail(h, ST_EINVAL, "invalid argument");
-    STM_Q(l_prolong, h, L, e_coarse, u_fine);
+    STM_TQ(double, l_prolong, h, L, e_coarse, u_fine);
     return ST_OK;
   });
 }
@@ -996,7 +1122,7 @@ int stm_level_prolong(stm_handle* h, int L, const double* e_coarse, double* u_fi
 int stm_coarsest_solve(stm_handle* h, int adjoint, const double* f, double* u) {
   return guarded(h, [&]() -> int {
     if (!f || !u) fail(h, ST_EINVAL, "null pointer");
-    coarsest(h, adjoint != 0, u, f);
+    coarsest<double>(h, adjoint != 0, u, f);
     return ST_OK;
   });
 }

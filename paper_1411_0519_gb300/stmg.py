@@ -412,8 +412,8 @@ class MeshSolver:
     (z, y, x) (``nodes()``)."""
 
     def __init__(self, verts, cells, refinements, p_t, N, T, *, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50,
-                 coarsening="auto", max_workspace_bytes=0, nu_x=2, omega_x=2.0 / 3.0, gamma=1, stream=None,
-                 device=None):
+                 coarsening="auto", max_workspace_bytes=0, nu_x=2, omega_x=2.0 / 3.0, gamma=1, precision="fp64",
+                 inner_cycles=1, stream=None, device=None):
         import numpy as np
         L = lib()
         self._lib = L
@@ -422,9 +422,10 @@ class MeshSolver:
         self.dim, self.p_t, self.N, self.T = v.shape[1], p_t, N, float(T)
         self.q = p_t + 1
         self.refinements = refinements
-        opt = make_options(nu1=nu1, nu2=nu2, omega=omega, rtol=rtol, maxit=maxit, precision="fp64",
-                           coarsening=coarsening, coarsest_steps=1, max_workspace_bytes=max_workspace_bytes,
-                           smoother="vcycle", nu_x=nu_x, omega_x=omega_x, gamma=gamma)
+        opt = make_options(nu1=nu1, nu2=nu2, omega=omega, rtol=rtol, maxit=maxit, precision=precision,
+                           coarsening=coarsening, coarsest_steps=1, inner_cycles=inner_cycles,
+                           max_workspace_bytes=max_workspace_bytes, smoother="vcycle", nu_x=nu_x, omega_x=omega_x,
+                           gamma=gamma)
         self.options = opt
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -100,7 +100,7 @@ def test_mesh_setup_rejects_bad_arguments_before_touching_the_device(lib):
     for m, ref, p, N, T, o in cases:
         assert lib.stm_setup(ctypes.byref(m), ref, p, N, T, ctypes.byref(o), None, ctypes.byref(h)) == stmg.ST_EINVAL
         assert not h.value
-    for field, val in [("smoother", stmg.ST_SMOOTH_EXACT), ("precision", stmg.ST_MIXED), ("coarsest_steps", 2)]:
+    for field, val in [("smoother", stmg.ST_SMOOTH_EXACT), ("precision", 7), ("coarsest_steps", 2)]:
         o = stmg.StOptions()
         ctypes.pointer(o)[0] = opt
         setattr(o, field, val)

@@ -191,3 +191,49 @@ def test_example2_protocol_on_the_paper_mesh():
                                             rtol=1e-8, maxit=40)
                 assert abs(it - ito) <= 1, (level, p, it, ito)
     print("Example 2 on the refined 4-triangle mesh, N = 1024, V-cycles for p_t = 0..3 per space level:", got)
+
+
+@pytest.mark.parametrize("shape", CASES[:2] + CASES[4:], ids=lambda c: "d%d-r%d-p%d-N%d" % c[:4])
+@pytest.mark.parametrize("inner", [1, 4])
+def test_mixed_mesh_solve_against_oracle(shape, inner):
+    """The mixed form on a mesh (FP32 cycles inside FP64 refinement) against the
+    oracle's exact discrete solution, with the bound ||u - u*|| <= ||L^-1|| ||r||
+    of the tensor-grid mixed tests."""
+    require_gpu()
+    from tests.test_gpu_mixed_oracle import _check_against_oracle
+    dim, ref, p, N, T, coarsening = shape
+    c = MeshCase(dim, ref, p, N, T, coarsening, rtol=1e-10, maxit=80, precision="mixed", inner_cycles=inner)
+    try:
+        disc = c.H.finest.disc
+        f = rand(disc.shape(), 91)
+        u0 = np.random.default_rng(92).uniform(-1, 1, disc.Nx)
+        u, it, rr = c.solver.solve(to_gpu(f), to_gpu(u0))
+        assert rr <= 1e-10
+        _check_against_oracle(c.H, mm.add_ic(disc, f, u0), to_np(u), 1e-10,
+                              f"mixed mesh d={dim} refinements={ref} p_t={p} N={N} inner={inner} ({it} refinements)")
+        lam, gu0, ita, rra = c.solver.adjoint_solve(to_gpu(f))
+        lo, _, _ = multigrid.solve(c.H, f, rtol=1e-12, maxit=80, adjoint=True)
+        assert rra <= 1e-10 and rel_err(to_np(lam), lo) < 1e-8
+    finally:
+        c.close()
+
+
+def test_mixed_mesh_one_refinement_step():
+    """stm_vcycle in the mixed form is one refinement step: u + s V32(r / s)
+    against the oracle's FP64 cycle from the same iterate, within the FP32
+    tolerance of the tensor-grid test."""
+    require_gpu()
+    c = MeshCase(2, 3, 1, 16, 1.0, "auto", precision="mixed", inner_cycles=1)
+    try:
+        disc = c.H.finest.disc
+        u, f = rand(disc.shape(), 93), rand(disc.shape(), 94)
+        ug = to_gpu(u)
+        c.solver.vcycle(ug, to_gpu(f))
+        got = to_np(ug).reshape(disc.shape())
+        ref = multigrid.vcycle(c.H, 0, u, f)
+        diff = np.linalg.norm(got - ref) / np.linalg.norm(ref - u)
+        tol = 4.0 * c.solver.num_levels * (2 + 2 + 3) * 2.0 ** -24 * 4   # the spatial V-cycle adds passes
+        print(f"mixed mesh refinement step: ||u32 - u64|| / ||correction|| = {diff:.2e} (tolerance {tol:.2e})")
+        assert diff <= tol
+    finally:
+        c.close()
