@@ -160,7 +160,10 @@ struct SpaceLevel {          // one mesh of the refinement (device arrays + host
   std::vector<double> mv_h, kv_h;
   int *rp = nullptr, *ci = nullptr;
   double *mv = nullptr, *kv = nullptr;
-  float *mv32 = nullptr, *kv32 = nullptr;             // mixed form: the entries rounded to FP32
+  int ell_w = 0;                                      // the rows in slot-major padded form (stmm::Ell)
+  int* ell_ci = nullptr;
+  double *ell_mv = nullptr, *ell_kv = nullptr;
+  float *ell_mv32 = nullptr, *ell_kv32 = nullptr;     // mixed form: the entries rounded to FP32
   int *p0 = nullptr, *p1 = nullptr;                   // parents on the next coarser mesh (level >= 1)
   int *ch_rp = nullptr, *ch_ci = nullptr;             // children on the next finer mesh (level < top)
   double* ch_w = nullptr;
@@ -273,7 +276,9 @@ stmm::MTime<T, Q> mtime(const HostTime& t) {
 
 template <typename T> stmm::Csr<T> csr(const SpaceLevel& s);
 template <> stmm::Csr<double> csr<double>(const SpaceLevel& s) { return {s.rp, s.ci, s.mv, s.kv}; }
-template <> stmm::Csr<float> csr<float>(const SpaceLevel& s) { return {s.rp, s.ci, s.mv32, s.kv32}; }
+template <typename T> stmm::Ell<T> ell(const SpaceLevel& s);
+template <> stmm::Ell<double> ell<double>(const SpaceLevel& s) { return {s.ell_w, s.ell_ci, s.ell_mv, s.ell_kv}; }
+template <> stmm::Ell<float> ell<float>(const SpaceLevel& s) { return {s.ell_w, s.ell_ci, s.ell_mv32, s.ell_kv32}; }
 template <typename T> stmm::Children<T> children(const SpaceLevel& s);
 template <> stmm::Children<double> children<double>(const SpaceLevel& s) { return {s.ch_rp, s.ch_ci, s.ch_w}; }
 template <> stmm::Children<float> children<float>(const SpaceLevel& s) { return {s.ch_rp, s.ch_ci, s.ch_w32}; }
@@ -330,9 +335,9 @@ void l_residual(stm_handle* h, const MLevel& L, bool adj, const T* f, const T* u
   const auto tc = mtime<T, Q>(h->tm);
   over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
     if (adj)
-      stmm::k_mresidual<T, Q, true><<<g, kThreads, 0, h->stream>>>(f, u, r, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, tc);
+      stmm::k_mresidual<T, Q, true><<<g, kThreads, 0, h->stream>>>(f, u, r, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, tc);
     else
-      stmm::k_mresidual<T, Q, false><<<g, kThreads, 0, h->stream>>>(f, u, r, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, tc);
+      stmm::k_mresidual<T, Q, false><<<g, kThreads, 0, h->stream>>>(f, u, r, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, tc);
   });
 }
 
@@ -344,7 +349,7 @@ void l_jacobi(stm_handle* h, MLevel& L, int k, bool adj, bool zero, const T* b, 
   const T* D = bufs<T>(L).dinv[k];
   over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
 #define STM_JAC(A, Z)                                                                                        \
-  stmm::k_mjacobi<T, Q, A, Z><<<g, kThreads, 0, h->stream>>>(b, x, y, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, w, D, \
+  stmm::k_mjacobi<T, Q, A, Z><<<g, kThreads, 0, h->stream>>>(b, x, y, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, w, D, \
                                                               tc)
     if (adj) { if (zero) STM_JAC(true, true); else STM_JAC(true, false); }
     else { if (zero) STM_JAC(false, true); else STM_JAC(false, false); }
@@ -360,10 +365,10 @@ void l_residual_jacobi0(stm_handle* h, MLevel& L, bool adj, const T* f, const T*
   over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
     if (adj)
       stmm::k_mresidual_jacobi0<T, Q, true><<<g, kThreads, 0, h->stream>>>(
-          f, u, r, x, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, D, tc);
+          f, u, r, x, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, D, tc);
     else
       stmm::k_mresidual_jacobi0<T, Q, false><<<g, kThreads, 0, h->stream>>>(
-          f, u, r, x, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, D, tc);
+          f, u, r, x, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, D, tc);
   });
 }
 
@@ -375,10 +380,10 @@ void l_jacobi_update(stm_handle* h, MLevel& L, bool adj, const T* b, const T* x,
   over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
     if (adj)
       stmm::k_mjacobi_update<T, Q, true><<<g, kThreads, 0, h->stream>>>(
-          b, x, u, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, (T)h->opt.omega, D, tc);
+          b, x, u, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, (T)h->opt.omega, D, tc);
     else
       stmm::k_mjacobi_update<T, Q, false><<<g, kThreads, 0, h->stream>>>(
-          b, x, u, csr<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, (T)h->opt.omega, D, tc);
+          b, x, u, ell<T>(s), s.Nx, L.N, s0, (T)L.tau, (T)h->opt.omega_x, (T)h->opt.omega, D, tc);
   });
 }
 
@@ -388,10 +393,10 @@ void l_space_residual(stm_handle* h, const MLevel& L, int k, bool adj, const T* 
   const auto tc = mtime<T, Q>(h->tm);
   over_step_blocks(s.Nx, L.N, [&](dim3 g, int s0) {
     if (adj)
-      stmm::k_mspace_residual<T, Q, true><<<g, kThreads, 0, h->stream>>>(b, x, r, csr<T>(s), s.Nx, L.N, s0,
+      stmm::k_mspace_residual<T, Q, true><<<g, kThreads, 0, h->stream>>>(b, x, r, ell<T>(s), s.Nx, L.N, s0,
                                                                            (T)L.tau, tc);
     else
-      stmm::k_mspace_residual<T, Q, false><<<g, kThreads, 0, h->stream>>>(b, x, r, csr<T>(s), s.Nx, L.N, s0,
+      stmm::k_mspace_residual<T, Q, false><<<g, kThreads, 0, h->stream>>>(b, x, r, ell<T>(s), s.Nx, L.N, s0,
                                                                             (T)L.tau, tc);
   });
 }
@@ -803,9 +808,31 @@ void build(stm_handle* h, const st_simplex_mesh* m0, int refinements) {
     s.ci = upload(h, s.ci_h);
     s.mv = upload(h, s.mv_h);
     s.kv = upload(h, s.kv_h);
-    if (mixed(h)) {
-      s.mv32 = upload_as<float>(h, s.mv_h);
-      s.kv32 = upload_as<float>(h, s.kv_h);
+    {   // slot-major padded rows (stmm::Ell)
+      int w = 0;
+      for (int i = 0; i < s.Nx; ++i) w = std::max(w, s.rp_h[i + 1] - s.rp_h[i]);
+      s.ell_w = w;
+      std::vector<int> eci((size_t)w * s.Nx);
+      std::vector<double> emv((size_t)w * s.Nx, 0.0), ekv((size_t)w * s.Nx, 0.0);
+      for (int i = 0; i < s.Nx; ++i)
+        for (int k = 0; k < w; ++k) {
+          const int e = s.rp_h[i] + k;
+          const size_t o = (size_t)k * s.Nx + i;
+          if (e < s.rp_h[i + 1]) {
+            eci[o] = s.ci_h[e];
+            emv[o] = s.mv_h[e];
+            ekv[o] = s.kv_h[e];
+          } else {
+            eci[o] = i;
+          }
+        }
+      s.ell_ci = upload(h, eci);
+      s.ell_mv = upload(h, emv);
+      s.ell_kv = upload(h, ekv);
+      if (mixed(h)) {
+        s.ell_mv32 = upload_as<float>(h, emv);
+        s.ell_kv32 = upload_as<float>(h, ekv);
+      }
     }
     if (lvl > 0) {
       // parents of every interior vertex on the previous mesh

@@ -30,6 +30,18 @@ struct Csr {
   const T* kv;    // K_h entries
 };
 
+// The same rows padded to the longest row W and stored slot-major: entry w of
+// row j at [w * Nx + j] (padding: the row's own vertex with zero weights), so a
+// warp's loads of one slot are contiguous and all slots of a row can be in
+// flight at once.
+template <typename T>
+struct Ell {
+  int W;
+  const int* ci;
+  const T* mv;
+  const T* kv;
+};
+
 // Prolongation of the nested P1 spaces from mesh level l-1 to l: fine vertex j
 // is a coarse vertex (p1 = -2: value of coarse p0) or the midpoint of a coarse
 // edge (half the value of each endpoint; -1 marks a boundary endpoint).
@@ -55,7 +67,7 @@ constexpr int kMSteps = 4;
 // with TRACE also the M_h-weighted neighbouring trace mt[i] of step s (forward:
 // sum_l en[l] x_{s-1,l}, adjoint: sum_l st[l] x_{s+1,l}; zero outside 0..N-1).
 template <typename T, int Q, bool ADJ, bool TRACE>
-__device__ __forceinline__ void apply_A_steps(const Csr<T>& A, int j, int64_t Nx, int N, int sb,
+__device__ __forceinline__ void apply_A_steps(const Ell<T>& A, int j, int64_t Nx, int N, int sb,
                                               const T* __restrict__ x, T tau, const MTime<T, Q>& tc,
                                               T (&ax)[kMSteps][Q], T (&mt)[kMSteps]) {
   constexpr int TS = kMSteps;
@@ -67,8 +79,9 @@ __device__ __forceinline__ void apply_A_steps(const Csr<T>& A, int j, int64_t Nx
 #pragma unroll
     for (int l = 0; l < Q; ++l) mu[i][l] = ku[i][l] = T(0);
   }
-  const int e1 = A.rp[j + 1];
-  for (int e = A.rp[j]; e < e1; ++e) {
+#pragma unroll 4
+  for (int w = 0; w < A.W; ++w) {
+    const int64_t e = (int64_t)w * Nx + j;
     const int c = A.ci[e];
     const T m = A.mv[e], k = A.kv[e];
     const T* xc = x + c;
@@ -128,7 +141,7 @@ __device__ __forceinline__ void apply_A_steps(const Csr<T>& A, int j, int64_t Nx
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ>
 __global__ void k_mresidual(const T* __restrict__ f, const T* __restrict__ u, T* __restrict__ r,
-                            Csr<T> A, int Nx, int N, int s0, T tau, MTime<T, Q> tc) {
+                            Ell<T> A, int Nx, int N, int s0, T tau, MTime<T, Q> tc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * kMSteps;
   if (j >= Nx || sb >= N) return;
@@ -152,7 +165,7 @@ __global__ void k_mresidual(const T* __restrict__ f, const T* __restrict__ u, T*
 // same mesh, x = omega_x D_j^{-1} r_j (D^{-T} for the adjoint).
 template <typename T, int Q, bool ADJ>
 __global__ void k_mresidual_jacobi0(const T* __restrict__ f, const T* __restrict__ u,
-                                    T* __restrict__ r, T* __restrict__ x, Csr<T> A, int Nx, int N, int s0,
+                                    T* __restrict__ r, T* __restrict__ x, Ell<T> A, int Nx, int N, int s0,
                                     T tau, T omega_x, const T* __restrict__ dinv, MTime<T, Q> tc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * kMSteps;
@@ -192,7 +205,7 @@ __global__ void k_mresidual_jacobi0(const T* __restrict__ f, const T* __restrict
 // ---------------------------------------------------------------------------
 template <typename T, int Q, bool ADJ, bool ZERO>
 __global__ void k_mjacobi(const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ y,
-                          Csr<T> A, int Nx, int N, int s0, T tau, T omega, const T* __restrict__ dinv,
+                          Ell<T> A, int Nx, int N, int s0, T tau, T omega, const T* __restrict__ dinv,
                           MTime<T, Q> tc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * kMSteps;
@@ -224,7 +237,7 @@ __global__ void k_mjacobi(const T* __restrict__ b, const T* __restrict__ x, T* _
 // r = b - A x per time step.
 template <typename T, int Q, bool ADJ>
 __global__ void k_mspace_residual(const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r,
-                                  Csr<T> A, int Nx, int N, int s0, T tau, MTime<T, Q> tc) {
+                                  Ell<T> A, int Nx, int N, int s0, T tau, MTime<T, Q> tc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * kMSteps;
   if (j >= Nx || sb >= N) return;
@@ -246,7 +259,7 @@ __global__ void k_mspace_residual(const T* __restrict__ b, const T* __restrict__
 // u += omega_t (x + omega_x D_j^{-1} (b - A x)_j), without storing the sweep.
 template <typename T, int Q, bool ADJ>
 __global__ void k_mjacobi_update(const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ u,
-                                 Csr<T> A, int Nx, int N, int s0, T tau, T omega_x, T omega_t,
+                                 Ell<T> A, int Nx, int N, int s0, T tau, T omega_x, T omega_t,
                                  const T* __restrict__ dinv, MTime<T, Q> tc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int sb = s0 + blockIdx.y * kMSteps;

@@ -283,3 +283,28 @@ def test_mutation_of_the_prolongation_is_caught():
     P = P.tocsr()
     fine, coarse = fam.spaces[2], fam.spaces[1]
     assert np.abs((P.T @ fine.Mh @ P - coarse.Mh).toarray()).max() > 1e-3
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("space_level", [0, 1])
+def test_example1_on_the_paper_mesh_within_one_cycle(space_level, golden_dir):
+    """Example 1 (Section 4): the 12-tetrahedron cube refined uniformly, T = 1,
+    N = 2^k, p_t = 1, f = 0, u^0 ~ U[0, 1], the inexact block inverse,
+    eps = 1e-8: V-cycle counts within one of the printed table for time levels
+    0 ... 6."""
+    rows = {}
+    for line in open(golden_dir + "/example1_iterations.txt"):
+        if line.startswith("#") or not line.strip():
+            continue
+        vals = [int(v) for v in line.split()]
+        rows[vals[0]] = vals[1:]
+    fam = _family(3, space_level)
+    got = []
+    for k in range(7):
+        H = mm.MeshHierarchy(None, space_level, 1, 2 ** k, 1.0, family=fam)
+        disc = H.finest.disc
+        u0 = np.random.default_rng(0).uniform(0.0, 1.0, disc.shape())
+        _, it, _ = multigrid.solve(H, np.zeros(disc.shape()), u=u0, rtol=1e-8, maxit=40)
+        got.append(it)
+        assert abs(it - rows[space_level][k]) <= 1, (k, it, rows[space_level][k])
+    print("Example 1 on the refined 12-tetrahedron cube, level", space_level, ":", got)
