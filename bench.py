@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="stmg", choices=["stmg", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-fft-leg", action="store_true",
+                    help="skip the FP64 solve with FFT sine transforms (comparison with the tensor-core transforms)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-inexact", action="store_true",
@@ -88,8 +90,9 @@ def peaks():
     if os.path.exists(path):
         with open(path) as fh:
             p = json.load(fh)
-        return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "src": "measured"}
-    return {"hbm_gbs": 6800.0, "src": "fallback"}
+        return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "src": "measured",
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", 1700.0)}
+    return {"hbm_gbs": 6800.0, "src": "fallback", "bf16_tflops_sustained": 1700.0}
 
 
 # FP64 vector-ALU peak of a GB300: 1.25 TFLOP/s (the published per-GPU FP64
@@ -191,7 +194,9 @@ def traffic_table():
         return json.load(fh)
 
 
+TRANSFORM_CLASSES = ("dst", "dst_tc")
 KERNEL_OF_CLASS = {"smooth": "k_fsmooth", "residual": "k_fresidual", "dst": "k_dst_rows_reg / k_dst_cols_reg",
+                   "dst_tc": "k_dst_tc",
                    "restrict": "k_frestrict", "prolong": "k_fprolong", "space_mg": "k_fspace_pre / k_fspace_post"}
 
 
@@ -235,15 +240,28 @@ def roofline(solver, prof, fp32, pk, w, exclude=()):
     return rf
 
 
-def transform_note(prof, w):
-    """The boundary sine transforms of the mixed form: double-float arithmetic on
-    the FP32 pipe (FP64-equivalent algorithmic flops; latency-bound by their ncu
-    capture), reported beside the FP32 cycle kernels."""
+def transform_note(prof, w, pk=None):
+    """The boundary sine transforms of the solve: on the tensor cores (a digit-splitting
+    pass, class dst, and the exact FP16 digit-product pass, class dst_tc, whose tensor
+    rate is reported against the measured sustained BF16 GEMM rate; FP16 and BF16 run
+    at the same rate), or double-float register FFTs on the FP32 pipe (class dst)."""
     classes = {k: v for k, v in prof.items() if not k.startswith("_") and v["ms"] > 0}
+    total = sum(c["ms"] for c in classes.values())
+    if "dst_tc" in classes:
+        tc, sp = classes["dst_tc"], classes.get("dst", {"ms": 0.0, "launches": 0, "bytes": 0.0})
+        peak = (pk or {}).get("bf16_tflops_sustained", 1700.0)
+        tfl = tc["flops"] / (tc["ms"] / 1e3) / 1e12
+        return {"kernel": "k_split_rows / k_split_cols + k_dst_tc", "arithmetic": "exact FP16 digit products, FP32 "
+                "tensor-memory accumulators, integer assembly to FP64",
+                "share_of_kernel_time": round((tc["ms"] + sp["ms"]) / total, 3),
+                "launches": tc["launches"] + sp["launches"],
+                "ms": round(tc["ms"] + sp["ms"], 3), "split_ms": round(sp["ms"], 3), "tensor_ms": round(tc["ms"], 3),
+                "tensor_tflops": round(tfl, 1), "tensor_peak_tflops": peak,
+                "tensor_frac": round(tfl / peak, 4), "peak_src": "MEASURED_PEAKS.json bf16_tflops_sustained",
+                "split_gbs": round(sp["bytes"] / (sp["ms"] / 1e3) / 1e9, 1) if sp["ms"] > 0 else None}
     if "dst" not in classes:
         return None
     v = classes["dst"]
-    total = sum(c["ms"] for c in classes.values())
     return {"kernel": "k_dst_rows_reg / k_dst_cols_reg <dfloat>", "arithmetic": "double-float on the FP32 pipe",
             "share_of_kernel_time": round(v["ms"] / total, 3), "launches": v["launches"],
             "fp64_equivalent_tflops": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4),
@@ -258,9 +276,9 @@ def vcycle_times(solver, prof, steps, iters, per_step_ms, pk):
     input read once and each output written once, summed over all levels by
     the library) over that time, as a fraction of the measured copy rate."""
     L = solver.num_levels - 1
-    cls = [c for c in prof if not c.startswith("_") and c != "dst"]
+    cls = [c for c in prof if not c.startswith("_") and c not in TRANSFORM_CLASSES]
     fin = sum(solver.profile_level(c, L)["ms"] for c in cls)
-    dst = prof.get("dst", {}).get("ms", 0.0) / steps
+    dst = sum(prof.get(c, {}).get("ms", 0.0) for c in TRANSFORM_CLASSES) / steps
     n = max(1, iters)
     ms = (per_step_ms - dst) / n
     by = sum(prof[c]["bytes"] for c in cls) / steps / n
@@ -382,7 +400,7 @@ def run_mixed_only(args, torch, stmg, w, f, u0, pk, world, rank, barrier, max_ov
                 "dtype": "f32 V-cycle in f64 refinement", "data": "synthetic",
                 "config": {"workload": args.workload, "d": d, "n": n, "p_t": p, "N": N, "T": T, "rtol": rtol,
                            "precision": "mixed", "inner_cycles": args.inner_cycles},
-                "iters": itm[-1], "relres": rrm, "roofline": roofline(smx, profm, True, pk, w, exclude=("dst",)), "transform": transform_note(profm, w),
+                "iters": itm[-1], "relres": rrm, "roofline": roofline(smx, profm, True, pk, w, exclude=TRANSFORM_CLASSES), "transform": transform_note(profm, w),
                 "kernels": breakdown(profm),
                 "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_")),
                 "clocks": ck}
@@ -485,7 +503,7 @@ def config_legs(args, torch, stmg, workloads, pk, barrier, max_over_ranks, world
         ms, it, rr, prof = timed_solve(torch, s, run, 2, 1, barrier, max_over_ranks)
         leg[prec] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "iters": it,
                      "relres": rr, "roofline": roofline(s, prof, prec == "mixed", pk, w,
-                                                        exclude=("dst",) if prec == "mixed" else ()),
+                                                        exclude=TRANSFORM_CLASSES if prec == "mixed" else ()),
                      "cycle": vcycle_times(s, prof, 2, it, ms, pk)}
         s.close()
         del u
@@ -524,7 +542,7 @@ def config_legs(args, torch, stmg, workloads, pk, barrier, max_over_ranks, world
             msa, ita, rra, profa = timed_solve(torch, s, run_adj, 1, 1, barrier, max_over_ranks)
             entry[prec] = {"value": world * s.ndof / (ms / 1e3), "unit": "DoF/s", "ms_per_step": ms, "iters": it,
                            "relres": rr, "roofline": roofline(s, prof, prec == "mixed", pk, w,
-                                                              exclude=("dst",) if prec == "mixed" else ()),
+                                                              exclude=TRANSFORM_CLASSES if prec == "mixed" else ()),
                            "cycle": vcycle_times(s, prof, 1, it, ms, pk),
                            "adjoint": {"value": world * s.ndof / (msa / 1e3), "unit": "DoF/s", "ms_per_step": msa,
                                        "iters": ita, "relres": rra}}
@@ -667,8 +685,25 @@ def main():
         del fh, u0h, uh
     rf64 = roofline(s64, prof64, False, pk, w)
     vc64 = vcycle_times(s64, prof64, args.steps, it64[-1], per_step, pk)
+    tr64 = transform_note(prof64, w, pk)
     s64.close()
     torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- the same solve with the FFT transforms
+    fft64 = None
+    if not args.no_fft_leg:
+        sf = stmg.Solver(d, n, p, N, T, rtol=rtol, maxit=60, precision="fp64", transform="fft")
+        nst = min(args.steps, 3)
+        msf, itf, rrf, proff = time_solves(torch, sf, f, u0, None, nst, 1, barrier)
+        msf = max_over_ranks(msf)
+        dsf = sum(proff.get(c, {}).get("ms", 0.0) for c in TRANSFORM_CLASSES) / nst
+        dst64 = sum(prof64.get(c, {}).get("ms", 0.0) for c in TRANSFORM_CLASSES) / args.steps
+        fft64 = {"value": world * sf.ndof / (msf / nst / 1e3), "unit": "DoF/s", "ms_per_step": msf / nst,
+                 "iters": itf[-1], "relres": rrf, "transform_ms_per_solve": round(dsf, 3),
+                 "tensor_transform_ms_per_solve": round(dst64, 3),
+                 "note": "transform=fft: the boundary sine transforms as register FFTs on the FP64 pipe"}
+        sf.close()
+        torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- mixed precision
     mixed = None
@@ -680,8 +715,8 @@ def main():
                  "ms_per_step": msm / args.steps, "iters": itm[-1], "relres": rrm,
                  "inner_cycles": args.inner_cycles, "dtype": "f32 V-cycle in f64 refinement",
                  "refinement_step": vcycle_times(smx, profm, args.steps, itm[-1], msm / args.steps, pk),
-                 "roofline": roofline(smx, profm, True, pk, w, exclude=("dst",)),
-                 "transform": transform_note(profm, w),
+                 "roofline": roofline(smx, profm, True, pk, w, exclude=TRANSFORM_CLASSES),
+                 "transform": transform_note(profm, w, pk),
                  "kernels": breakdown(profm),
                  "gpu_launches": sum(v["launches"] for k, v in profm.items() if not k.startswith("_"))}
         smx.close()
@@ -767,6 +802,8 @@ def main():
         "iters": it64[-1], "relres": rr64, "vcycle": vc64,
         "gpu_launches": launches,
         "roofline": rf64,
+        "transform": tr64,
+        "fp64_fft_transforms": fft64,
         "kernels": breakdown(prof64),
         "mixed": mixed,
         "inexact_smoother": inexact,

@@ -61,6 +61,10 @@ extern "C" {
 #define ST_SMOOTH_VCYCLE 1  /* D~^{-1}: one spatial multigrid V-cycle per step (Remark on the V-cycle
                                approximation in space; damped point-block Jacobi, nu_x, omega_x) */
 
+#define ST_DST_AUTO   0  /* sine transforms on the tensor cores where 64 <= n_L + 1 <= 256, else the FFT kernels */
+#define ST_DST_FFT    1  /* FFT-based sine transforms (FP64 pipe) at every length */
+#define ST_DST_TENSOR 2  /* tensor-core sine transforms; st_setup fails (ST_EINVAL) unless 64 <= n + 1 <= 256 */
+
 #define ST_MAX_PT    47  /* largest supported DG degree p_t (q <= 48); degrees above 3 use the
                              generic-q kernels and need ST_SMOOTH_EXACT */
 
@@ -84,6 +88,13 @@ typedef struct st_options {
   int nu_x;              /* ST_SMOOTH_VCYCLE: spatial pre-/post-smoothing steps, default 2 (Section 4) */
   double omega_x;        /* ST_SMOOTH_VCYCLE: spatial Jacobi damping, default 2/3 (Section 4) */
   int gamma;             /* cycle index (Section 2): 1 = V-cycle (default), 2 = W-cycle */
+  int transform;         /* ST_DST_AUTO (default), ST_DST_FFT or ST_DST_TENSOR: how the FP64 sine
+                            transforms of the exact block inverse (Section 3.1) are computed.  The
+                            tensor-core form splits each line into 7-bit digits scaled by the line's
+                            largest exponent and sums exact FP16 digit products in FP32 tensor memory;
+                            its error is below 2^-50 of sqrt((n+1)/2) ||line||_2, like the FFT's.  It
+                            needs a scratch of 65536 (n+1) 8 bytes (at most 134 MB), allocated on first
+                            use and counted in max_workspace_bytes. */
 } st_options;
 
 typedef struct st_handle st_handle;
@@ -200,6 +211,15 @@ int st_level_prolong(st_handle* h, int L, const double* e_coarse, double* u_fine
  * inverse, several by forward (adjoint: backward) substitution. */
 int st_coarsest_solve(st_handle* h, int adjoint, const double* f, double* u);
 
+/* Change of basis of `slabs` consecutive FP64 spatial fields of level L
+ * (layout (slabs, n_L^d)): y = S x, S the unnormalised DST-I
+ * y_k = sum_j x_j sin(pi j k / (n_L + 1)) along every axis (inverse = 0), or
+ * y = S^{-1} x = (2 / (n_L + 1))^d S x (inverse = 1).  In the sine basis the
+ * spatial operators of every step are diagonal (Section 3.1).  x == y is allowed;
+ * other overlap is not.  Uses the handle's transform option; synchronises and
+ * reports a pending tensor-core time-out.  Errors: ST_EINVAL, ST_ECUDA. */
+int st_transform(st_handle* h, int L, int inverse, const double* x, double* y, size_t slabs);
+
 /* ||x||_2 of n FP64 values (deterministic order); synchronises. */
 int st_norm2(st_handle* h, const double* x, size_t n, double* out);
 
@@ -219,7 +239,9 @@ int st_norm2(st_handle* h, const double* x, size_t n, double* out);
 #define ST_K_RHS        7   /* separate smoother right-hand side (no longer launched:
                                fused into ST_K_SMOOTH; the value is kept) */
 #define ST_K_SPACEMG    8   /* spatial V-cycle of the inexact block inverse */
-#define ST_K_COUNT      9
+#define ST_K_DSTTC      9   /* tensor-core pass of a sine transform along one axis (ST_K_DST then holds
+                               its digit-splitting pass); flops = the FP16 digit products executed */
+#define ST_K_COUNT      10
 
 /* Record a CUDA event pair around every kernel launched by this handle, for up
  * to max_launches launches (events are created here, not per launch).  Adds a

@@ -17,6 +17,7 @@
 
 #include "stmg.h"
 #include "stmg_kernels.cuh"
+#include "stmg_tc.cuh"
 #include "stmg_sine.cuh"
 #include "stmg_host_time.h"
 
@@ -93,6 +94,7 @@ struct Level {
   Tables<double> t64;
   Tables<float> t32;
   stmg::DstTables<stmg::dfloat> tdf{nullptr, nullptr, nullptr};   // finest level, mixed form: double-float transforms
+  uint8_t* tcS = nullptr;   // FP16 digits of S / 2 for the tensor-core transform (made on first use)
   std::vector<SpaceLvl<double>> sp64;   // spatial hierarchy of the inexact block inverse
   std::vector<SpaceLvl<float>> sp32;
 };
@@ -111,7 +113,12 @@ struct st_handle {
   double* partial = nullptr;   // norm partial sums
   int64_t npartial = 0;
   double* dnorm = nullptr;     // device result of a norm
-  double* hnorm = nullptr;     // pinned host copy
+  double* hnorm = nullptr;     // pinned host copy (two words: the norm, then the tensor-core error flag)
+  // tensor-core sine transform: digit bytes and line exponents of one batch, device error flag
+  uint4* tcD = nullptr;
+  int* tcE = nullptr;
+  int* tcErr = nullptr;
+  int num_sms = 152;
   unsigned* dmaxexp = nullptr;   // mixed form: largest biased exponent of the entry data (device)
   int df_shift = 0;              // mixed form: the data enter the double-float transforms scaled by 2^df_shift
   double* coarse64_u = nullptr;  // mixed precision: FP64 copies for the coarsest solve
@@ -924,6 +931,133 @@ double dst_line_flops(int n) {
   return 5.0 * Nf + 5.0 * hf * logh + 12.0 * hf + Nf + n;
 }
 
+// ---- sine transforms on the tensor cores (stmg_tc.cuh) ----
+// Lines per split / tensor-core batch: the digit scratch (8 bytes per value, at most 134 MB)
+// stays near the size of L2 between the two passes.
+constexpr int64_t kTcCapLines = 65536;
+
+bool tc_len(int Nf) { return Nf >= stmg_tc::kMinNf && Nf <= stmg_tc::kMaxNf; }
+bool use_tc(const st_handle* h, const Level& lv) { return h->opt.transform != ST_DST_FFT && tc_len(lv.n + 1); }
+
+// FP16 bits of an integer |d| <= 64.
+uint16_t fp16_of_small_int(int d) {
+  if (d == 0) return 0;
+  const int a = d < 0 ? -d : d;
+  int e = 0;
+  while ((a >> (e + 1)) != 0) ++e;
+  return (uint16_t)((d < 0 ? 0x8000 : 0) | ((e + 15) << 10) | ((a << (10 - e)) & 0x3ff));
+}
+
+// FP16 digits of S / 2, S[k][m] = sin(pi k m / Nf): eight balanced base-128 digits in [-64, 64] each,
+// most significant first, from long-double sines.  Layout of the tensor kernel's shared-memory stage:
+// per (N tile nt, K chunk c) eight planes t of 64 (m) x 16 (k) values in K-major 8 x 8 core matrices.
+std::vector<uint16_t> tc_sine_digits(int Nf) {
+  const int nch = Nf / stmg_tc::BK, ntn = Nf / stmg_tc::BNP;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> sv(2 * (size_t)Nf);
+  for (int j = 0; j < 2 * Nf; ++j) sv[j] = sinl(pi * (long double)j / (long double)Nf);
+  std::vector<uint16_t> tab((size_t)ntn * nch * stmg_tc::B_STAGE / 2);
+  for (int nt = 0; nt < ntn; ++nt)
+    for (int c = 0; c < nch; ++c)
+      for (int mm = 0; mm < stmg_tc::BNP; ++mm)
+        for (int kk = 0; kk < stmg_tc::BK; ++kk) {
+          const int m = nt * stmg_tc::BNP + mm, k = c * stmg_tc::BK + kk;
+          long double v = sv[(size_t)((k * m) % (2 * Nf))] / 2.0L;
+          for (int t = 0; t < stmg_tc::NSL; ++t) {
+            v *= 128.0L;
+            const long double dg = nearbyintl(v);
+            v -= dg;
+            const size_t off = (((size_t)nt * nch + c) * stmg_tc::NSL + t) * (stmg_tc::B_PLANE / 2) +
+                               ((mm / 8) * 2 + kk / 8) * 64 + (mm % 8) * 8 + (kk % 8);
+            tab[off] = fp16_of_small_int((int)dg);
+          }
+        }
+  return tab;
+}
+
+void tc_prepare(st_handle* h, Level& lv) {
+  if (!h->tcD) {
+    h->tcD = reinterpret_cast<uint4*>(dalloc<uint8_t>(h, stmg_tc::digit_bytes_for(kTcCapLines, stmg_tc::kMaxNf)));
+    h->tcE = dalloc<int>(h, kTcCapLines);
+    h->tcErr = dalloc<int>(h, 1);
+    check(h, cudaMemsetAsync(h->tcErr, 0, sizeof(int), h->stream), "memset");
+    check(h, cudaFuncSetAttribute((const void*)stmg_tc::k_dst_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  stmg_tc::Smem::bytes), "cudaFuncSetAttribute");
+    check(h, cudaFuncSetAttribute((const void*)stmg_tc::k_dst_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  stmg_tc::Smem::bytes), "cudaFuncSetAttribute");
+  }
+  if (!lv.tcS) {
+    const std::vector<uint16_t> tab = tc_sine_digits(lv.n + 1);
+    lv.tcS = reinterpret_cast<uint8_t*>(dalloc<uint16_t>(h, tab.size()));
+    check(h, cudaMemcpy(lv.tcS, tab.data(), tab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice), "upload sine digits");
+  }
+}
+
+// A tensor-core wait that timed out (read back with a norm or by st_transform) fails the call.
+void tc_check_flag(st_handle* h) {
+  if (!h->tcErr) return;
+  int flag = 0;
+  std::memcpy(&flag, h->hnorm + 1, sizeof(int));
+  if (flag != 0) {
+    std::memset(h->hnorm + 1, 0, sizeof(int));
+    cudaMemsetAsync(h->tcErr, 0, sizeof(int), h->stream);
+    fail(h, ST_ECUDA, "tensor-core sine transform: an mbarrier wait timed out (code " + std::to_string(flag) + ")");
+  }
+}
+
+// 2^axis_exp S along every axis of `slabs` FP64 fields of level lv (src / mid / dst as in dst_axes),
+// the first pass scaled by 2^load_exp, the last by 2^store_exp: per axis a digit-splitting pass
+// (lines' exponents and digit bytes) and a tensor-core pass, in batches of whole slabs.
+void dst_axes_tc(st_handle* h, Level& lv, const double* src, double* mid, double* dst, int64_t slabs, int axis_exp,
+                 int load_exp, int store_exp) {
+  tc_prepare(h, lv);
+  const int n = lv.n, Nf = n + 1, nch = Nf / stmg_tc::BK, ntn = Nf / stmg_tc::BNP;
+  const int64_t lps = lv.Nx / n;   // lines per field along any axis
+  const int64_t bs = std::max<int64_t>(1, kTcCapLines / lps);
+  const int lvl = level_of(h, lv);
+  for (int64_t s0 = 0; s0 < slabs; s0 += bs) {
+    const int64_t ns = std::min(bs, slabs - s0);
+    const int64_t nlines = ns * lps;
+    const int64_t nlpad = (nlines + stmg_tc::BM - 1) / stmg_tc::BM * stmg_tc::BM;
+    const int64_t off = s0 * lv.Nx;
+    int64_t inner = 1;
+    for (int a = 0; a < h->d; ++a) {
+      const double* in = (a == 0 ? src : mid) + off;
+      double* out = (a == h->d - 1 ? dst : mid) + off;
+      const int oe = axis_exp + (a == 0 ? load_exp : 0) + (a == h->d - 1 ? store_exp : 0);
+      {
+        Prof pr(h, ST_K_DST, 8.0 * (double)nlines * n, 0.0, 1, lvl);
+        if (a == 0)
+          stmg_tc::k_split_rows<<<(unsigned)((nlpad + 7) / 8), 256, 0, h->stream>>>(in, n, nlines, nch, nlpad, h->tcE,
+                                                                                    h->tcD);
+        else
+          stmg_tc::k_split_cols<<<(unsigned)((nlpad + 127) / 128), 128, 0, h->stream>>>(in, n, nlines, inner, nch,
+                                                                                        nlpad, h->tcE, h->tcD);
+      }
+      {
+        const int64_t ntiles = nlpad / stmg_tc::BM * ntn;
+        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, h->num_sms);
+        Prof pr(h, ST_K_DSTTC, 8.0 * (double)nlines * n, 2.0 * 36.0 * Nf * (double)Nf * (double)nlpad, 1, lvl);
+        if (a == 0)
+          stmg_tc::k_dst_tc<true><<<grid, stmg_tc::NTHREADS, stmg_tc::Smem::bytes, h->stream>>>(
+              h->tcD, out, n, nlines, inner, h->tcE, lv.tcS, nch, ntn, oe, h->tcErr);
+        else
+          stmg_tc::k_dst_tc<false><<<grid, stmg_tc::NTHREADS, stmg_tc::Smem::bytes, h->stream>>>(
+              h->tcD, out, n, nlines, inner, h->tcE, lv.tcS, nch, ntn, oe, h->tcErr);
+      }
+      inner *= n;
+    }
+  }
+  check(h, cudaGetLastError(), "tensor-core sine transform");
+}
+
+// log2 of an exact power of two (the transform scales 1 and 2 / Nf).
+int exact_log2(double s) {
+  int e = 0;
+  const double m = std::frexp(s, &e);
+  return m == 0.5 ? e - 1 : 0x7fffffff;
+}
+
 // scale * DST-I along every spatial axis of `slabs` consecutive spatial fields
 // of level lv.  The first pass reads src, the last writes dst, intermediate
 // results live in mid (src == mid == dst: in place).  `scale` is applied once
@@ -931,6 +1065,11 @@ double dst_line_flops(int n) {
 // (64 <= n + 1 <= 512); the other kernels work in place on mid.
 template <typename T>
 void dst_axes(st_handle* h, Level& lv, const T* src, T* mid, T* dst, int64_t slabs, double axis_scale) {
+  if (sizeof(T) == 8 && use_tc(h, lv) && exact_log2(axis_scale) != 0x7fffffff) {
+    dst_axes_tc(h, lv, reinterpret_cast<const double*>(src), reinterpret_cast<double*>(mid),
+                reinterpret_cast<double*>(dst), slabs, exact_log2(axis_scale), 0, 0);
+    return;
+  }
   const int n = lv.n, Nf = n + 1;
   const int naxes = h->d;
   const bool reg = Nf >= 64 && Nf <= 512;
@@ -1062,7 +1201,7 @@ void df_launch(st_handle* h, const void* in, void* out, int n, int64_t nlines, i
 
 // Whether the mixed form's boundary transforms of the finest level run in double-float.
 bool df_transforms(const st_handle* h, const Level& lv) {
-  return h->opt.precision == ST_MIXED && df_len(lv.n + 1) && lv.tdf.sinp != nullptr;
+  return h->opt.precision == ST_MIXED && !use_tc(h, lv) && df_len(lv.n + 1) && lv.tdf.sinp != nullptr;
 }
 
 // 2^load_exp * scale * DST-I along every axis of `slabs` FP64 fields, computed in
@@ -1070,6 +1209,10 @@ bool df_transforms(const st_handle* h, const Level& lv) {
 void dst_axes_df(st_handle* h, Level& lv, const double* src, double* mid, double* dst, int64_t slabs,
                  double axis_scale, int load_exp, int store_exp) {
   const int n = lv.n, Nf = n + 1;
+  if (use_tc(h, lv) && exact_log2(axis_scale) != 0x7fffffff) {   // exact FP64 transform, scaled on entry / exit
+    dst_axes_tc(h, lv, src, mid, dst, slabs, exact_log2(axis_scale), load_exp, store_exp);
+    return;
+  }
   if (!df_len(Nf) || lv.tdf.sinp == nullptr) {
     dst_axes<double>(h, lv, src, mid, dst, slabs, axis_scale);
     return;
@@ -1393,7 +1536,10 @@ double norm2(st_handle* h, const T* x, int64_t n) {
     stmg::k_sum_final<<<1, 1024, 0, h->stream>>>(h->partial, kNormBlocks, h->dnorm);
   }
   check(h, cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm copy");
+  if (h->tcErr)
+    check(h, cudaMemcpyAsync(h->hnorm + 1, h->tcErr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag copy");
   check(h, cudaStreamSynchronize(h->stream), "norm sync");
+  tc_check_flag(h);
   return std::sqrt(*h->hnorm);
 }
 
@@ -1444,7 +1590,10 @@ double residual_norm(st_handle* h, bool adj, const double* f, const double* u, c
     stmg::k_sum_final<<<1, 1024, 0, h->stream>>>(h->partial, (int)np, h->dnorm);
   }
   check(h, cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm copy");
+  if (h->tcErr)
+    check(h, cudaMemcpyAsync(h->hnorm + 1, h->tcErr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag copy");
   check(h, cudaStreamSynchronize(h->stream), "norm sync");
+  tc_check_flag(h);
   return std::sqrt(*h->hnorm);
 }
 
@@ -1707,6 +1856,7 @@ void st_default_options(st_options* o) {
   o->nu_x = 2;
   o->omega_x = 2.0 / 3.0;
   o->gamma = 1;
+  o->transform = ST_DST_AUTO;
 }
 
 namespace {
@@ -1729,6 +1879,8 @@ const char* check_setup_args(const st_mesh* mesh, int p_t, int N, double T, cons
   if (o.smoother == ST_SMOOTH_VCYCLE && (o.nu_x < 1 || !(o.omega_x > 0.0))) return "bad spatial smoothing options";
   if (o.smoother == ST_SMOOTH_VCYCLE && p_t + 1 > kQfix) return "the inexact block inverse supports p_t <= 3";
   if (o.gamma < 1 || o.gamma > 2) return "gamma must be 1 (V-cycle) or 2 (W-cycle)";
+  if (o.transform < ST_DST_AUTO || o.transform > ST_DST_TENSOR) return "bad transform";
+  if (o.transform == ST_DST_TENSOR && !tc_len(mesh->n + 1)) return "the tensor-core transform needs 64 <= n + 1 <= 256";
   if (o.coarsest_steps < 1) o.coarsest_steps = 1;
   if (!is_pow2(o.coarsest_steps) || o.coarsest_steps > N) return "bad coarsest_steps";
   return nullptr;
@@ -1891,7 +2043,14 @@ int st_setup(const st_mesh* mesh, int p_t, int N, double T, const st_options* op
     }
     h->dnorm = dalloc<double>(h, 1);
     h->dmaxexp = reinterpret_cast<unsigned*>(dalloc<double>(h, 1));
-    check(h, cudaMallocHost(&h->hnorm, sizeof(double)), "cudaMallocHost");
+    check(h, cudaMallocHost(&h->hnorm, 2 * sizeof(double)), "cudaMallocHost");
+    std::memset(h->hnorm, 0, 2 * sizeof(double));
+    {
+      int dev = 0, sms = 0;
+      check(h, cudaGetDevice(&dev), "cudaGetDevice");
+      check(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+      h->num_sms = std::max(1, sms);
+    }
     check(h, cudaDeviceSynchronize(), "setup sync");
     return ST_OK;
   });
@@ -2165,6 +2324,28 @@ int st_profile_level(const st_handle* h, int cls, int L, int* launches, double* 
   if (bytes) *bytes = h->lv_stats[b + 2];
   if (flops) *flops = h->lv_stats[b + 3];
   return ST_OK;
+}
+
+int st_transform(st_handle* h, int L, int inverse, const double* x, double* y, size_t slabs) {
+  return guarded(h, [&]() -> int {
+    if (!x || !y) fail(h, ST_EINVAL, "null pointer");
+    Level& lv = h->levels[level_index(h, L)];
+    if (slabs == 0) return ST_OK;
+    const double sc = inverse ? 2.0 / (lv.n + 1) : 1.0;
+    const int Nf = lv.n + 1;
+    if (x == y || use_tc(h, lv) || (Nf >= 64 && Nf <= 512)) {
+      dst_axes<double>(h, lv, x, y, y, (int64_t)slabs, sc);
+    } else {   // the shared-memory FFT kernels work in place
+      copy<double>(h, y, x, (int64_t)slabs * lv.Nx);
+      dst_axes<double>(h, lv, y, (int64_t)slabs, sc);
+    }
+    after_launch(h);
+    if (h->tcErr)
+      check(h, cudaMemcpyAsync(h->hnorm + 1, h->tcErr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag copy");
+    check(h, cudaStreamSynchronize(h->stream), "transform sync");
+    tc_check_flag(h);
+    return ST_OK;
+  });
 }
 
 int st_norm2(st_handle* h, const double* x, size_t n, double* out) {

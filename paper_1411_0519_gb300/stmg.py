@@ -22,6 +22,7 @@ ST_AUTO, ST_SEMI, ST_FULL = 0, 1, 2
 ST_INIT_GIVEN = 1
 ST_MAX_PT = 47
 ST_SMOOTH_EXACT, ST_SMOOTH_VCYCLE = 0, 1
+ST_DST_AUTO, ST_DST_FFT, ST_DST_TENSOR = 0, 1, 2
 
 EXPORTS = [
     "st_default_options", "st_setup", "st_destroy", "st_last_error", "st_ndof", "st_num_levels",
@@ -29,7 +30,7 @@ EXPORTS = [
     "st_level_residual",
     "st_level_block_solve", "st_level_smooth", "st_level_restrict", "st_level_prolong",
     "st_coarsest_solve", "st_norm2", "st_profile_start", "st_profile_stop", "st_profile_level", "st_norm2_noalloc",
-    "st_plan",
+    "st_plan", "st_transform",
 ]
 
 MESH_EXPORTS = [
@@ -40,7 +41,7 @@ MESH_EXPORTS = [
 
 ST_NOALLOC_MAX_ELEMENTS = 1 << 30
 
-KERNEL_CLASSES = ["residual", "dst", "smooth", "restrict", "prolong", "norm", "vector", "rhs", "space_mg"]
+KERNEL_CLASSES = ["residual", "dst", "smooth", "restrict", "prolong", "norm", "vector", "rhs", "space_mg", "dst_tc"]
 
 
 class StMesh(ctypes.Structure):
@@ -53,7 +54,7 @@ class StOptions(ctypes.Structure):
                 ("coarsening", ctypes.c_int), ("coarsest_steps", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("max_workspace_bytes", ctypes.c_size_t),
                 ("smoother", ctypes.c_int), ("nu_x", ctypes.c_int), ("omega_x", ctypes.c_double),
-                ("gamma", ctypes.c_int)]
+                ("gamma", ctypes.c_int), ("transform", ctypes.c_int)]
 
 
 class SimplexMesh(ctypes.Structure):
@@ -105,6 +106,7 @@ def load_library(path=None):
         "st_level_prolong": (I, [H, I, P, P]),
         "st_coarsest_solve": (I, [H, I, P, P]),
         "st_norm2": (I, [H, P, ctypes.c_size_t, ctypes.POINTER(D)]),
+        "st_transform": (I, [H, I, I, P, P, ctypes.c_size_t]),
         "st_profile_start": (I, [H, I]),
         "st_norm2_noalloc": (I, [P, ctypes.c_size_t, P, P]),
         "st_profile_level": (I, [H, I, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D),
@@ -162,13 +164,15 @@ def _ptr(t, numel=None, name="tensor"):
 
 
 _PRECISION = {"fp64": ST_FP64, "mixed": ST_MIXED}
+_TRANSFORM = {"auto": ST_DST_AUTO, "fft": ST_DST_FFT, "tensor": ST_DST_TENSOR}
 _COARSEN = {"auto": ST_AUTO, "semi": ST_SEMI, "full": ST_FULL}
 
 
 def make_options(*, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50, precision="fp64", coarsening="auto",
                  coarsest_steps=1, inner_cycles=1, max_workspace_bytes=0, smoother="exact", nu_x=2,
-                 omega_x=2.0 / 3.0, gamma=1):
-    """st_options from keyword arguments (the defaults of st_default_options)."""
+                 omega_x=2.0 / 3.0, gamma=1, transform="auto"):
+    """st_options from keyword arguments (the defaults of st_default_options).
+    transform: "auto" (tensor cores for 64 <= n + 1 <= 256), "fft" or "tensor"."""
     opt = StOptions()
     lib().st_default_options(ctypes.byref(opt))
     opt.nu1, opt.nu2, opt.omega, opt.rtol, opt.maxit = nu1, nu2, omega, rtol, maxit
@@ -181,6 +185,7 @@ def make_options(*, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50, precision="fp6
     opt.nu_x = nu_x
     opt.omega_x = omega_x
     opt.gamma = gamma
+    opt.transform = _TRANSFORM[transform]
     return opt
 
 
@@ -210,8 +215,8 @@ class Solver:
 
     def __init__(self, dim, n, p_t, N, T, *, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50,
                  precision="fp64", coarsening="auto", coarsest_steps=1, inner_cycles=1,
-                 max_workspace_bytes=0, smoother="exact", nu_x=2, omega_x=2.0 / 3.0, gamma=1, stream=None,
-                 device=None):
+                 max_workspace_bytes=0, smoother="exact", nu_x=2, omega_x=2.0 / 3.0, gamma=1, transform="auto",
+                 stream=None, device=None):
         L = lib()
         self._lib = L
         self.dim, self.n, self.p_t, self.N, self.T = dim, n, p_t, N, float(T)
@@ -219,7 +224,7 @@ class Solver:
         opt = make_options(nu1=nu1, nu2=nu2, omega=omega, rtol=rtol, maxit=maxit, precision=precision,
                            coarsening=coarsening, coarsest_steps=coarsest_steps, inner_cycles=inner_cycles,
                            max_workspace_bytes=max_workspace_bytes, smoother=smoother, nu_x=nu_x,
-                           omega_x=omega_x, gamma=gamma)
+                           omega_x=omega_x, gamma=gamma, transform=transform)
         self.options = opt
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -333,6 +338,20 @@ class Solver:
         self._check(rc, allow=() if raise_on_failure else (ST_ENOTCONV, ST_ENAN))
         self.last_status = rc
         return lam, gu0, it.value, rr.value
+
+    def transform(self, x, L=None, inverse=False, out=None):
+        """st_transform: the sine basis change S (or S^-1) of the spatial fields in x (FP64, any
+        leading shape, n_L^d values per field) on level L (default finest); out may be x."""
+        lv = self.num_levels - 1 if L is None else L
+        nL = self.level_info(lv)["n"]
+        nx = nL ** self.dim
+        if x.numel() % nx:
+            raise ValueError(f"x has {x.numel()} elements, not a multiple of n_L^d = {nx}")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check(self._lib.st_transform(self._h, lv, 1 if inverse else 0, _ptr(x, x.numel(), "x"),
+                                           _ptr(out, x.numel(), "out"), x.numel() // nx))
+        return out
 
     def norm2(self, x):
         out = ctypes.c_double()

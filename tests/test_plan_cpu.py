@@ -74,6 +74,7 @@ def test_mu_star_of_the_plan_matches_the_printed_values(stmg, golden_dir):
     ((2, 7, 48, 16, 1.0), {}), ((2, 7, 1, 16, -1.0), {}), ((2, 7, 1, 16, 1.0), {"coarsest_steps": 32}),
     ((1, 7, 1, 65536, 1.0), {}),
     ((2, 7, 1, 16, 1.0), {"gamma": 3}), ((2, 7, 4, 16, 1.0), {"smoother": "vcycle"}),
+    ((2, 511, 1, 16, 1.0), {"transform": "tensor"}), ((2, 31, 1, 16, 1.0), {"transform": "tensor"}),
 ])
 def test_plan_rejects_what_setup_rejects(stmg, args, opts):
     with pytest.raises(stmg.StmgError) as e:
@@ -91,3 +92,19 @@ def test_plan_checks_the_array_size(stmg):
     rc = lib.st_plan(ctypes.byref(mesh), 1, 1024, 1.0, ctypes.byref(opt), 4, Ns, None, None, None,
                      ctypes.byref(nlev), None)
     assert rc == stmg.ST_EINVAL and nlev.value == 11
+
+
+def test_transform_option_values(stmg):
+    """auto and fft at every length, tensor for 64 <= n + 1 <= 256; other values are rejected."""
+    for n in (31, 63, 255, 511):
+        stmg.plan(2, n, 1, 16, 1.0, transform="auto")
+        stmg.plan(2, n, 1, 16, 1.0, transform="fft")
+    for n in (63, 127, 255):
+        stmg.plan(2, n, 1, 16, 1.0, transform="tensor")
+    import ctypes
+    opt = stmg.make_options()
+    opt.transform = 3
+    nlev, ms = ctypes.c_int(), ctypes.c_double()
+    rc = stmg.lib().st_plan(ctypes.byref(stmg.StMesh(2, 63)), 1, 16, 1.0, ctypes.byref(opt), 0, None, None, None,
+                            None, ctypes.byref(nlev), ctypes.byref(ms))
+    assert rc == stmg.ST_EINVAL
