@@ -61,7 +61,8 @@ extern "C" {
 #define ST_SMOOTH_VCYCLE 1  /* D~^{-1}: one spatial multigrid V-cycle per step (Remark on the V-cycle
                                approximation in space; damped point-block Jacobi, nu_x, omega_x) */
 
-#define ST_DST_AUTO   0  /* sine transforms on the tensor cores where 64 <= n_L + 1 <= 256, else the FFT kernels */
+#define ST_DST_AUTO   0  /* ST_FP64: sine transforms on the tensor cores where 64 <= n_L + 1 <= 256, else the
+                             FFT kernels; ST_MIXED: the double-float FFT kernels (faster on the FP32 pipe) */
 #define ST_DST_FFT    1  /* FFT-based sine transforms (FP64 pipe) at every length */
 #define ST_DST_TENSOR 2  /* tensor-core sine transforms; st_setup fails (ST_EINVAL) unless 64 <= n + 1 <= 256 */
 

@@ -937,7 +937,13 @@ double dst_line_flops(int n) {
 constexpr int64_t kTcCapLines = 65536;
 
 bool tc_len(int Nf) { return Nf >= stmg_tc::kMinNf && Nf <= stmg_tc::kMaxNf; }
-bool use_tc(const st_handle* h, const Level& lv) { return h->opt.transform != ST_DST_FFT && tc_len(lv.n + 1); }
+// ST_DST_AUTO: the tensor cores replace the FP64 FFTs; the mixed form keeps its double-float FFTs
+// (FP32 pipe), which are faster than the tensor-core pass at these lengths.
+bool use_tc(const st_handle* h, const Level& lv) {
+  if (!tc_len(lv.n + 1)) return false;
+  if (h->opt.transform == ST_DST_TENSOR) return true;
+  return h->opt.transform == ST_DST_AUTO && h->opt.precision == ST_FP64;
+}
 
 // FP16 bits of an integer |d| <= 64.
 uint16_t fp16_of_small_int(int d) {
@@ -1202,6 +1208,12 @@ void df_launch(st_handle* h, const void* in, void* out, int n, int64_t nlines, i
 // Whether the mixed form's boundary transforms of the finest level run in double-float.
 bool df_transforms(const st_handle* h, const Level& lv) {
   return h->opt.precision == ST_MIXED && !use_tc(h, lv) && df_len(lv.n + 1) && lv.tdf.sinp != nullptr;
+}
+
+// Whether the mixed form's boundary transforms scale the data by 2^df_shift on entry and undo it
+// on exit: the double-float transforms and the tensor-core transforms both do (exactly).
+bool shift_transforms(const st_handle* h, const Level& lv) {
+  return h->opt.precision == ST_MIXED && (use_tc(h, lv) || df_transforms(h, lv));
 }
 
 // 2^load_exp * scale * DST-I along every axis of `slabs` FP64 fields, computed in
@@ -1636,16 +1648,17 @@ void boundary_dst(st_handle* h, const double* src, double* mid, double* dst, int
   else dst_axes<double>(h, lv, src, mid, dst, slabs, sc);
 }
 
-// Mixed form: the double-float pairs have the FP32 exponent range, so data whose
-// largest magnitude lies outside 2^-64 ... 2^64 enter the transforms scaled by the
-// power of two that brings it into [1, 2) (exact; every later step is linear, so
-// the cycles solve the scaled problem and the inverse transform undoes the scale).
+// Mixed form: the FP32 cycles (and the double-float pairs) have the FP32 exponent range,
+// and the FP64 norms square the data, so data whose largest magnitude lies outside
+// 2^-64 ... 2^64 enter the transforms scaled by the power of two that brings it into
+// [1, 2) (exact; every later step is linear, so the cycles solve the scaled problem and
+// the inverse transform undoes the scale).
 // Sets h->df_shift from the finite entries of f, u0 and u (u0, u may be null);
 // reads one device word back (synchronises the stream).
 void choose_df_shift(st_handle* h, const double* f, const double* u0, const double* u) {
   Level& lv = finest(h);
   h->df_shift = 0;
-  if (!df_transforms(h, lv)) return;
+  if (!shift_transforms(h, lv)) return;
   check(h, cudaMemsetAsync(h->dmaxexp, 0, sizeof(unsigned), h->stream), "memset");
   auto scan = [&](const double* x, int64_t n) {
     if (x == nullptr || n == 0) return;

@@ -15,6 +15,9 @@ if not torch.cuda.is_available():
 from paper_1411_0519_gb300 import stmg  # noqa: E402
 
 CASES = [(1, 63), (1, 255), (2, 63), (2, 127), (2, 255), (3, 63)]
+# normwise error bounds per field: the tensor-core form rounds once per axis pass from exact
+# integer sums; an FFT's error grows like eps log2(n + 1) (measured 4.1e-15 at n = 255)
+TOL = {"tensor": 2e-15, "fft": 1e-14}
 
 
 def ref_transform(x, dim, inverse=False):
@@ -57,9 +60,9 @@ def test_transform_matches_scipy(dim, n, transform):
         yi = s.transform(xd, inverse=True).cpu().numpy()
     finally:
         s.close()
-    # each axis pass errs by a few ulps of the line's scale; the fields mix scales over 2^80
-    assert rel_field_error(y, ref_transform(x, dim), dim) < 4e-15
-    assert rel_field_error(yi, ref_transform(x, dim, inverse=True), dim) < 4e-15
+    # the fields mix line scales over 2^80
+    assert rel_field_error(y, ref_transform(x, dim), dim) < TOL[transform]
+    assert rel_field_error(yi, ref_transform(x, dim, inverse=True), dim) < TOL[transform]
 
 
 @pytest.mark.parametrize("dim,n", [(1, 255), (2, 255), (3, 63)])
@@ -74,8 +77,8 @@ def test_tensor_equals_fft_and_round_trip(dim, n):
     finally:
         st.close()
         sf.close()
-    assert rel_field_error(yt.cpu().numpy(), yf.cpu().numpy(), dim) < 4e-15
-    assert rel_field_error(back.cpu().numpy(), x, dim) < 8e-15
+    assert rel_field_error(yt.cpu().numpy(), yf.cpu().numpy(), dim) < TOL["fft"] + TOL["tensor"]
+    assert rel_field_error(back.cpu().numpy(), x, dim) < 2 * TOL["tensor"]
 
 
 def test_tensor_batches_in_place_and_ragged_blocks():
@@ -90,7 +93,7 @@ def test_tensor_batches_in_place_and_ragged_blocks():
         y = xd.cpu().numpy()
     finally:
         s.close()
-    assert rel_field_error(y, ref_transform(x, dim), dim) < 4e-15
+    assert rel_field_error(y, ref_transform(x, dim), dim) < TOL["tensor"]
 
 
 def special_lines(n):
@@ -118,9 +121,11 @@ def test_tensor_special_lines_1d():
         y = s.transform(torch.from_numpy(x).cuda()).cpu().numpy()
     finally:
         s.close()
-    # exact products in extended precision: y_k = sum_j x_j sin(pi j k / 256)
+    # exact products in extended precision: y_k = sum_j x_j sin(pi j k / 256), the argument
+    # reduced exactly (j k mod 512) and pi in long double
     j = np.arange(1, n + 1)
-    S = np.sin(np.pi * np.outer(j, j).astype(np.longdouble) / (n + 1))
+    pi_l = np.longdouble("3.14159265358979323846264338327950288")
+    S = np.sin(pi_l * (np.outer(j, j) % (2 * (n + 1))).astype(np.longdouble) / (n + 1))
     for r in range(x.shape[0]):
         exact = x[r].astype(np.longdouble) @ S
         scale = np.sqrt((n + 1) / 2.0) * np.sqrt(np.sum(x[r].astype(np.longdouble) ** 2))
@@ -152,7 +157,7 @@ def test_tensor_non_finite_lines():
     for r in (0, 3):
         assert np.all(np.isfinite(yt[r]))
         ref = ref_transform(x[r:r + 1], 1)
-        assert rel_field_error(yt[r:r + 1], ref, 1) < 4e-15
+        assert rel_field_error(yt[r:r + 1], ref, 1) < TOL["tensor"]
 
 
 @pytest.mark.parametrize("dim,n,precision", [(2, 127, "fp64"), (2, 127, "mixed"), (3, 63, "fp64"), (1, 255, "fp64")])
