@@ -114,8 +114,9 @@ struct st_handle {
   int64_t npartial = 0;
   double* dnorm = nullptr;     // device result of a norm
   double* hnorm = nullptr;     // pinned host copy (two words: the norm, then the tensor-core error flag)
-  // tensor-core sine transform: digit bytes and line exponents of one batch, device error flag
-  uint4* tcD = nullptr;
+  // tensor-core sine transform: digit planes and line exponents of one batch, device error flag
+  uint8_t* tcD = nullptr;
+  int64_t tc_cap = 0;   // lines the digit planes hold (at least one field's lines along an axis)
   int* tcE = nullptr;
   int* tcErr = nullptr;
   int num_sms = 152;
@@ -932,9 +933,9 @@ double dst_line_flops(int n) {
 }
 
 // ---- sine transforms on the tensor cores (stmg_tc.cuh) ----
-// Lines per split / tensor-core batch: the digit scratch (8 bytes per value, at most 134 MB)
-// stays near the size of L2 between the two passes.
-constexpr int64_t kTcCapLines = 65536;
+// Lines per split / tensor-core batch: the digit planes (16 bytes per value, at most 134 MB)
+// stay near the size of L2 between the two passes.
+constexpr int64_t kTcCapLines = 32768;
 
 bool tc_len(int Nf) { return Nf >= stmg_tc::kMinNf && Nf <= stmg_tc::kMaxNf; }
 // ST_DST_AUTO: the tensor cores replace the FP64 FFTs; the mixed form keeps its double-float FFTs
@@ -983,8 +984,12 @@ std::vector<uint16_t> tc_sine_digits(int Nf) {
 
 void tc_prepare(st_handle* h, Level& lv) {
   if (!h->tcD) {
-    h->tcD = reinterpret_cast<uint4*>(dalloc<uint8_t>(h, stmg_tc::digit_bytes_for(kTcCapLines, stmg_tc::kMaxNf)));
-    h->tcE = dalloc<int>(h, kTcCapLines);
+    int64_t cap = kTcCapLines;   // a batch is whole fields: hold at least one field's lines
+    for (const Level& l : h->levels)
+      if (tc_len(l.n + 1)) cap = std::max<int64_t>(cap, (l.Nx / l.n + stmg_tc::BM - 1) / stmg_tc::BM * stmg_tc::BM);
+    h->tc_cap = cap;
+    h->tcD = dalloc<uint8_t>(h, stmg_tc::plane_bytes_for(cap, stmg_tc::kMaxNf));
+    h->tcE = dalloc<int>(h, cap);
     h->tcErr = dalloc<int>(h, 1);
     check(h, cudaMemsetAsync(h->tcErr, 0, sizeof(int), h->stream), "memset");
     check(h, cudaFuncSetAttribute((const void*)stmg_tc::k_dst_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1013,13 +1018,13 @@ void tc_check_flag(st_handle* h) {
 
 // 2^axis_exp S along every axis of `slabs` FP64 fields of level lv (src / mid / dst as in dst_axes),
 // the first pass scaled by 2^load_exp, the last by 2^store_exp: per axis a digit-splitting pass
-// (lines' exponents and digit bytes) and a tensor-core pass, in batches of whole slabs.
+// (lines' exponents and FP16 digit planes) and a tensor-core pass, in batches of whole slabs.
 void dst_axes_tc(st_handle* h, Level& lv, const double* src, double* mid, double* dst, int64_t slabs, int axis_exp,
                  int load_exp, int store_exp) {
   tc_prepare(h, lv);
   const int n = lv.n, Nf = n + 1, nch = Nf / stmg_tc::BK, ntn = Nf / stmg_tc::BNP;
   const int64_t lps = lv.Nx / n;   // lines per field along any axis
-  const int64_t bs = std::max<int64_t>(1, kTcCapLines / lps);
+  const int64_t bs = std::max<int64_t>(1, h->tc_cap / lps);   // tc_cap >= lps rounded up to 128
   const int lvl = level_of(h, lv);
   for (int64_t s0 = 0; s0 < slabs; s0 += bs) {
     const int64_t ns = std::min(bs, slabs - s0);
@@ -1033,12 +1038,12 @@ void dst_axes_tc(st_handle* h, Level& lv, const double* src, double* mid, double
       const int oe = axis_exp + (a == 0 ? load_exp : 0) + (a == h->d - 1 ? store_exp : 0);
       {
         Prof pr(h, ST_K_DST, 8.0 * (double)nlines * n, 0.0, 1, lvl);
+        const unsigned blocks = (unsigned)(nlpad / stmg_tc::SPLIT_LINES);
+        uint4* planes = reinterpret_cast<uint4*>(h->tcD);
         if (a == 0)
-          stmg_tc::k_split_rows<<<(unsigned)((nlpad + 7) / 8), 256, 0, h->stream>>>(in, n, nlines, nch, nlpad, h->tcE,
-                                                                                    h->tcD);
+          stmg_tc::k_split_planes<true><<<blocks, 256, 0, h->stream>>>(in, n, nlines, inner, nch, h->tcE, planes);
         else
-          stmg_tc::k_split_cols<<<(unsigned)((nlpad + 127) / 128), 128, 0, h->stream>>>(in, n, nlines, inner, nch,
-                                                                                        nlpad, h->tcE, h->tcD);
+          stmg_tc::k_split_planes<false><<<blocks, 256, 0, h->stream>>>(in, n, nlines, inner, nch, h->tcE, planes);
       }
       {
         const int64_t ntiles = nlpad / stmg_tc::BM * ntn;

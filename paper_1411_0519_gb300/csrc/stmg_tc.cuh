@@ -16,15 +16,15 @@
 // Dropped pairs (s + t >= 8) and the 56-bit truncation of x keep the error near 2^-53 of
 // the line's scale (measured below 5e-16 of sqrt(Nf / 2) ||x||_2).
 //
-// Work split: a split pass (k_split_rows / k_split_cols) writes each value's digits once, as
-// bytes, in the order the tensor kernel consumes them, with the line exponents; the tensor
-// kernel k_dst_tc is persistent (one CTA per SM) and warp-specialised:
-//   warps 0-7  expand the digit bytes of one 128-line x 16-K chunk into eight FP16 digit
-//              planes in shared memory (the MMA A operand);
-//   warp 8     issues 12 tcgen05.mma per chunk: for digit s, the sine planes t = t0 .. t0 + 3
+// Work split: a split pass (k_split_planes) reads 16 lines per CTA through shared memory, finds each
+// line's largest exponent and writes the FP16 digit planes of every value once, in the exact layout of
+// one pipeline stage of the tensor kernel (32 KB per 128 lines x 16 K); the tensor kernel k_dst_tc is
+// persistent (one CTA per SM) and warp-specialised:
+//   warp 0     brings each chunk's data planes and sine planes with two bulk copies (48 KB);
+//   warp 1     issues 12 tcgen05.mma per chunk: for digit s, the sine planes t = t0 .. t0 + 3
 //              are adjacent along N, so one M = 128, N = 64 cnt MMA feeds accumulators
-//              s + t0 .. s + t0 + cnt - 1 (N <= 256); a bulk copy brings the chunk's sine planes;
-//   warps 9-16 drain the eight accumulators (TMEM, 512 columns) into exact int32 pairs
+//              s + t0 .. s + t0 + cnt - 1 (N <= 256);
+//   warps 2-9  drain the eight accumulators (TMEM, 512 columns) into exact int32 pairs
 //              C_g 2^7 + C_(g+1) in shared memory, release TMEM to the next tile's MMAs, then
 //              assemble and store the FP64 results.
 // Every wait on an mbarrier is bounded: on time-out the kernel raises *err, drains its own
@@ -44,9 +44,9 @@ constexpr int B_PLANE = BNP * BK * 2;    // 2 KB: one FP16 sine digit plane of a
 constexpr int A_STAGE = NSL * A_PLANE;   // 32 KB
 constexpr int B_STAGE = NSL * B_PLANE;   // 16 KB (the sine table stores this per (N tile, chunk))
 constexpr int NST = 2;                   // pipeline stages
-constexpr int NPROD = 8;                 // producer warps
-constexpr int MMA_WARP = 8;              // MMA issuer
-constexpr int EPI0 = 9;                  // epilogue warps 9 .. 16: two per TMEM lane quadrant
+constexpr int TMA_WARP = 0;              // bulk copies of the stages
+constexpr int MMA_WARP = 1;              // MMA issuer
+constexpr int EPI0 = 2;                  // epilogue warps 2 .. 9: two per TMEM lane quadrant (warp % 4)
 constexpr int NEPI = 8;
 constexpr int NTHREADS = (EPI0 + NEPI) * 32;
 constexpr int TS_WARP = 32 * 32 * 16;    // staged int32 group pairs of one epilogue warp: 32 columns x 32 lines
@@ -60,13 +60,13 @@ struct Smem {
   static constexpr int b_off = a_off + NST * A_STAGE;
   static constexpr int ts_off = b_off + NST * B_STAGE;
   static constexpr int bar_off = ts_off + NEPI * TS_WARP;
-  static constexpr int nbars = 3 * NST + 3;   // full[NST], bfull[NST], empty[NST], accf, acce, drain
+  static constexpr int nbars = 2 * NST + 3;   // full[NST], empty[NST], accf, acce, drain
   static constexpr int misc_off = bar_off + nbars * 8;
   static constexpr int bytes = misc_off + 16 + 1024;   // + slack for 1024-byte alignment of the base
 };
 
-// Bytes of the digit array of the split pass for nlines lines of Nf - 1 values.
-inline size_t digit_bytes_for(int64_t nlines, int Nf) { return (size_t)((nlines + BM - 1) / BM * BM) * (size_t)Nf * 8; }
+// Bytes of the digit planes of the split pass for nlines lines of Nf - 1 values (16 per value).
+inline size_t plane_bytes_for(int64_t nlines, int Nf) { return (size_t)((nlines + BM - 1) / BM * BM) * (size_t)Nf * 16; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -158,86 +158,104 @@ __device__ __forceinline__ void split28(double x, int Er, uint32_t& f2, uint32_t
   f1 = (uint32_t)F & 0x0fffffffu;
 }
 
-// The eight 7-bit digits of F = f2 2^28 + f1 (most significant first) as bytes 0..7 of
-// (lo, hi); the sign of x in bit 7 of byte 0.
-__device__ __forceinline__ void digit_bytes(uint32_t f2, uint32_t f1, uint32_t sign, uint32_t& lo, uint32_t& hi) {
-  lo = ((f2 >> 21) & 0x7fu) | (((f2 >> 14) & 0x7fu) << 8) | (((f2 >> 7) & 0x7fu) << 16) | ((f2 & 0x7fu) << 24) |
-       (sign << 7);
-  hi = ((f1 >> 21) & 0x7fu) | (((f1 >> 14) & 0x7fu) << 8) | (((f1 >> 7) & 0x7fu) << 16) | ((f1 & 0x7fu) << 24);
+// The FP16 digit s of two values a, b as one word (a low, b high): the 7-bit fields of their fixed-point
+// halves at bit pos, as FP16 1024 + d, then sign and offset in one f16x2 fma: +-(1024 + d) -+ 1024.
+__device__ __forceinline__ uint32_t digit_pair(uint32_t ha, uint32_t hb, int pos, uint32_t sgn2, uint32_t nm2) {
+  const uint32_t w = ((ha >> pos) & 0x7fu) | (((hb >> pos) & 0x7fu) << 16) | 0x64006400u;
+  return hfma2(w, sgn2, nm2);
 }
 
-// Offset, in 16-byte units, of the digit bytes of values k0 .. k0 + 7 (k0 a multiple of 8) of
-// line L: per (line block b = L / 128, K chunk c = k0 / 16) 256 units of 64 bytes, unit
-// u = 32 (row / 16) + row % 16 + 16 ((k0 / 8) mod 2), row = L mod 128, which is the unit that
-// lane u % 32 of producer warp u / 32 reads.
-__device__ __forceinline__ int64_t digit_unit(int64_t L, int k0, int nch) {
-  const int64_t b = L / BM;
-  const int row = (int)(L % BM), c = k0 / BK, kg = (k0 / 8) & 1;
-  const int u = 32 * (row >> 4) + (row & 15) + 16 * kg;
-  return ((b * nch + c) * 256 + u) * 4;
-}
+constexpr int SPLIT_LINES = 16;          // lines per CTA of the split pass
+constexpr int SPLIT_ROW = kMaxNf + 1;    // shared-memory row of one line (odd: no bank conflicts)
 
-// Split pass, contiguous lines (line L: x_j at in[L n + j - 1]): one warp per line of the
-// padded line blocks; lines >= nlines and the slot k = 0 get zero digits.
-// lineE[L] = largest exp_of over line L.  Nf = n + 1 <= 256.
-__global__ void k_split_rows(const double* __restrict__ in, int n, int64_t nlines, int nch, int64_t nlpad,
-                             int* __restrict__ lineE, uint4* __restrict__ D) {
-  const int64_t L = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (L >= nlpad) return;
+// Split pass: digit planes of lines L0 .. L0 + 15 (L0 = 16 blockIdx.x) of the padded line blocks.
+// Line L: x_j at in[L n + j - 1] (ROWS) or in[(L / inner) n inner + (j - 1) inner + L % inner];
+// x_0 and lines >= nlines are zero.  lineE[L] = largest exp_of over line L (L < nlines).
+// P: per (line block b, K chunk c) one stage of 8 planes x 4 KB; plane s holds digit s of
+// (row, k) at byte ((row / 8) 2 + (k / 8) % 2) 128 + (row % 8) 16 + (k % 8) 2 (K-major core
+// matrices).  256 threads; 64 <= Nf = n + 1 <= 256.
+template <bool ROWS>
+__global__ void __launch_bounds__(256) k_split_planes(const double* __restrict__ in, int n, int64_t nlines,
+                                                      int64_t inner, int nch, int* __restrict__ lineE,
+                                                      uint4* __restrict__ P) {
+  __shared__ double xs[SPLIT_LINES * SPLIT_ROW];
+  __shared__ int es[SPLIT_LINES];
   const int Nf = n + 1;
-  const int k0 = 8 * lane;   // this lane's values k0 .. k0 + 7
-  double v[8];
-  int e = kZeroExp;
+  const int64_t L0 = (int64_t)blockIdx.x * SPLIT_LINES;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (ROWS) {   // warp w loads lines 2w, 2w + 1: 32 consecutive values per instruction
+    double v[2][kMaxNf / 32];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int k = k0 + i;
-    v[i] = (L < nlines && k >= 1 && k <= n) ? in[L * n + (k - 1)] : 0.0;
-    e = max(e, exp_of(v[i]));
-  }
+    for (int h = 0; h < 2; ++h) {
+      const int64_t L = L0 + 2 * warp + h;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-  if (lane == 0 && L < nlines) lineE[L] = e;
-  if (k0 >= Nf) return;
-  uint32_t w[16];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    uint32_t f2, f1;
-    split28(v[i], e, f2, f1);
-    digit_bytes(f2, f1, (uint32_t)__double2hiint(v[i]) >> 31, w[2 * i], w[2 * i + 1]);
-  }
-  uint4* d = D + digit_unit(L, k0, nch);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) d[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-}
-
-// Split pass, strided lines (line L: x_j at in[(L / inner) n inner + (j - 1) inner + L % inner]):
-// one thread per line, consecutive lines in consecutive lanes.
-__global__ void k_split_cols(const double* __restrict__ in, int n, int64_t nlines, int64_t inner, int nch,
-                             int64_t nlpad, int* __restrict__ lineE, uint4* __restrict__ D) {
-  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (L >= nlpad) return;
-  const int Nf = n + 1;
-  const bool live = L < nlines;
-  const double* p = live ? in + (L / inner) * n * inner + (L % inner) : in;
-  int e = kZeroExp;
-  if (live) {
-    for (int j = 0; j < n; ++j) e = max(e, exp_of(p[(int64_t)j * inner]));
-    lineE[L] = e;
-  }
-  for (int k0 = 0; k0 < Nf; k0 += 8) {
-    uint32_t w[16];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int k = k0 + i;
-      const double x = (live && k >= 1 && k <= n) ? p[(int64_t)(k - 1) * inner] : 0.0;
-      uint32_t f2, f1;
-      split28(x, e, f2, f1);
-      digit_bytes(f2, f1, (uint32_t)__double2hiint(x) >> 31, w[2 * i], w[2 * i + 1]);
+      for (int i = 0; i < kMaxNf / 32; ++i) {
+        const int j = 32 * i + lane;   // x_(j + 1)
+        v[h][i] = (L < nlines && j < n) ? in[L * n + j] : 0.0;
+      }
     }
-    uint4* d = D + digit_unit(L, k0, nch);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) d[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    for (int h = 0; h < 2; ++h) {
+      double* row = xs + (2 * warp + h) * SPLIT_ROW;
+#pragma unroll
+      for (int i = 0; i < kMaxNf / 32; ++i)
+        if (32 * i + lane < n) row[32 * i + lane + 1] = v[h][i];
+      if (lane == 0) row[0] = 0.0;
+    }
+  } else {      // thread (line r, offset jj): 16 consecutive lines x 2 positions per warp instruction
+    const int r = tid & 15, jj = tid >> 4;
+    const int64_t L = L0 + r;
+    const bool live = L < nlines;
+    const double* p = live ? in + (L / inner) * n * inner + (L % inner) : in;
+    double v[kMaxNf / 16];
+#pragma unroll
+    for (int i = 0; i < kMaxNf / 16; ++i) {
+      const int j = jj + 16 * i;   // x_(j + 1)
+      v[i] = (live && j < n) ? p[(int64_t)j * inner] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxNf / 16; ++i)
+      if (jj + 16 * i < n) xs[r * SPLIT_ROW + jj + 16 * i + 1] = v[i];
+    if (jj == 0) xs[r * SPLIT_ROW] = 0.0;
+  }
+  __syncthreads();
+  for (int r = 2 * warp; r < 2 * warp + 2; ++r) {   // 8 warps, 2 lines each
+    int e = kZeroExp;
+    for (int k = lane; k < Nf; k += 32) e = max(e, exp_of(xs[r * SPLIT_ROW + k]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) {
+      es[r] = e;
+      if (L0 + r < nlines) lineE[L0 + r] = e;
+    }
+  }
+  __syncthreads();
+  // lane -> (row r, K group kg): lanes 0-7 rows 0-7 kg 0, 8-15 rows 0-7 kg 1, 16-31 rows 8-15;
+  // the 32 lanes' 16-byte pieces of one plane are then 512 contiguous bytes
+  const int r = (lane & 7) + 8 * (lane >> 4), kg = (lane >> 3) & 1;
+  const int Er = es[r];
+  const int64_t b = L0 / BM;
+  const int m = (int)((L0 % BM) / SPLIT_LINES);
+  for (int c = warp; c < nch; c += 8) {
+    const double* xr = xs + r * SPLIT_ROW + 16 * c + 8 * kg;
+    uint32_t w[NSL][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const double xa = xr[2 * p], xb = xr[2 * p + 1];
+      uint32_t a2, a1, b2, b1;
+      split28(xa, Er, a2, a1);
+      split28(xb, Er, b2, b1);
+      const uint32_t sbits = (((uint32_t)__double2hiint(xa) >> 31) << 15) | (((uint32_t)__double2hiint(xb) >> 31) << 31);
+      const uint32_t sgn2 = 0x3c003c00u | sbits, nm2 = 0xe400e400u ^ sbits;   // (+-1, +-1), (-+1024, -+1024)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        w[s][p] = digit_pair(a2, b2, 21 - 7 * s, sgn2, nm2);
+        w[4 + s][p] = digit_pair(a1, b1, 21 - 7 * s, sgn2, nm2);
+      }
+    }
+    uint4* stage = P + ((b * nch + c) * (A_STAGE / 16)) + 32 * m + lane;
+#pragma unroll
+    for (int s = 0; s < NSL; ++s) stage[s * (A_PLANE / 16)] = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
   }
 }
 
@@ -300,13 +318,13 @@ __device__ __forceinline__ double assemble_vt(long long V, int t, int e0, bool& 
 }
 
 // y_k = 2^out_exp sum_{j=1..n} x_j sin(pi j k / Nf), k = 1 .. n, Nf = n + 1 = 16 nch = 64 ntn
-// (64 <= Nf <= 256), for every line, from the digit bytes D and line exponents lineE of the split
+// (64 <= Nf <= 256), for every line, from the digit planes P and line exponents lineE of the split
 // pass.  Output line L: y_k at out[L n + k - 1] (ROWS) or out[(L / inner) n inner + (k - 1) inner
 // + L % inner].  sdig: FP16 digits of S / 2, B_STAGE bytes per (N tile, K chunk).  Launch with
 // NTHREADS threads, Smem::bytes of dynamic shared memory and at most one CTA per SM.
 template <bool ROWS>
-__global__ void __maxnreg__(96)
-k_dst_tc(const uint4* __restrict__ D, double* __restrict__ out, int n, int64_t nlines, int64_t inner,
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t nlines, int64_t inner,
          const int* __restrict__ lineE, const uint8_t* __restrict__ sdig, int nch, int ntn, int out_exp,
          int* __restrict__ err) {
   using SL = Smem;
@@ -316,10 +334,9 @@ k_dst_tc(const uint4* __restrict__ D, double* __restrict__ out, int n, int64_t n
   unsigned char* sm = smem_raw + pad;
   const uint32_t sbase = raw + pad;
   const uint32_t bars = sbase + SL::bar_off;
-  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };           // producer warps done
-  auto bfull = [&](int s) { return bars + 8u * (uint32_t)(NST + s); };   // sine planes landed
-  auto empty = [&](int s) { return bars + 8u * (uint32_t)(2 * NST + s); };
-  const uint32_t accf = bars + 8u * (uint32_t)(3 * NST), acce = accf + 8u, drain = accf + 16u;
+  auto full = [&](int s) { return bars + 8u * (uint32_t)s; };            // both bulk copies landed
+  auto empty = [&](int s) { return bars + 8u * (uint32_t)(NST + s); };   // the stage's MMAs completed
+  const uint32_t accf = bars + 8u * (uint32_t)(2 * NST), acce = accf + 8u, drain = accf + 16u;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SL::misc_off);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + SL::misc_off + 4);
 
@@ -333,8 +350,7 @@ k_dst_tc(const uint4* __restrict__ D, double* __restrict__ out, int n, int64_t n
   }
   if (threadIdx.x == 32) {
     for (int s = 0; s < NST; ++s) {
-      bar_init(full(s), NPROD);
-      bar_init(bfull(s), 1);
+      bar_init(full(s), 1);
       bar_init(empty(s), 1);
     }
     bar_init(accf, 1);
@@ -348,72 +364,29 @@ k_dst_tc(const uint4* __restrict__ D, double* __restrict__ out, int n, int64_t n
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = *tslot;
 
-  if (warp < NPROD) {
-    // ---- producers: FP16 digit planes from the digit bytes ----
-    const int r = lane & 15, kg = lane >> 4;   // row 16 warp + r, K group kg of the chunk
-    const int row = 16 * warp + r;
-    uint32_t it = 0;
-    uint4 cur[4];
-    auto load_chunk = [&](int64_t b, int c, uint4* q) {
-      const uint4* src = D + ((b * nch + c) * 256 + 32 * warp + lane) * 4;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) q[j] = __ldg(src + j);
-    };
-    int64_t t = blockIdx.x;
-    if (t < ntiles) load_chunk(t / ntn, 0, cur);
-    bool alive = true;
-    for (; t < ntiles && alive; t += gridDim.x) {
-      const int nt = (int)(t % ntn);
-      for (int c = 0; c < nch; ++c, ++it) {
-        const int st = (int)(it % NST);
-        const uint32_t use = it / NST;
-        if (lane == 0) alive = wait_bar(empty(st), (use & 1u) ^ 1u, abort_flag, err, 1);
-        alive = __shfl_sync(0xffffffffu, alive ? 1 : 0, 0) != 0;
+  if (warp == TMA_WARP) {
+    // ---- bulk copies: the chunk's data planes (split pass) and sine planes ----
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t b = t / ntn;
+        const int nt = (int)(t % ntn);
+        bool alive = true;
+        for (int c = 0; c < nch; ++c, ++it) {
+          const int st = (int)(it % NST);
+          if (!wait_bar(empty(st), ((it / NST) & 1u) ^ 1u, abort_flag, err, 1)) { alive = false; break; }
+          bar_expect_tx(full(st), A_STAGE + B_STAGE);
+          bulk_g2s(sbase + SL::a_off + st * A_STAGE, P + ((size_t)b * nch + c) * A_STAGE, A_STAGE, full(st));
+          bulk_g2s(sbase + SL::b_off + st * B_STAGE, sdig + ((size_t)nt * nch + c) * B_STAGE, B_STAGE, full(st));
+        }
         if (!alive) break;
-        if (warp == 0 && lane == 0) {
-          bar_expect_tx(bfull(st), B_STAGE);
-          bulk_g2s(sbase + SL::b_off + st * B_STAGE, sdig + ((size_t)nt * nch + c) * B_STAGE, B_STAGE, bfull(st));
-        }
-        uint4 q[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) q[j] = cur[j];
-        {   // prefetch the next chunk (this tile's next K chunk, or chunk 0 of the next tile)
-          int64_t tn = t;
-          int cn = c + 1;
-          if (cn == nch) { cn = 0; tn = t + gridDim.x; }
-          if (tn < ntiles) load_chunk(tn / ntn, cn, cur);
-        }
-        // values 2p (a) and 2p + 1 (b) of this lane: digit bytes (q[p].x, q[p].y) and (q[p].z, q[p].w);
-        // FP16 1024 + d from the byte d, then sign and offset in one f16x2 fma: +-(1024 + d) -+ 1024.
-        uint32_t pk[NSL][4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const uint32_t alo = q[p].x, ahi = q[p].y, blo = q[p].z, bhi = q[p].w;
-          const uint32_t sbits = ((alo & 0x80u) << 8) | ((blo & 0x80u) << 24);
-          const uint32_t sgn2 = 0x3c003c00u | sbits, nm2 = 0xe400e400u ^ sbits;
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const uint32_t sel = (uint32_t)s | ((uint32_t)(4 + s) << 8);
-            pk[s][p] = hfma2((__byte_perm(alo, blo, sel) & 0x007f007fu) | 0x64006400u, sgn2, nm2);
-            pk[4 + s][p] = hfma2((__byte_perm(ahi, bhi, sel) & 0x007f007fu) | 0x64006400u, sgn2, nm2);
-          }
-        }
-        unsigned char* a = sm + SL::a_off + st * A_STAGE + ((row >> 3) * 2 + kg) * 128 + (row & 7) * 16;
-#pragma unroll
-        for (int s = 0; s < NSL; ++s)
-          *reinterpret_cast<uint4*>(a + s * A_PLANE) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) bar_arrive(full(st));
       }
-    }
-    // drain: wait for this CTA's sine-plane copies still in flight
-    if (warp == 0 && lane == 0 && it > 0) {
+      // drain: wait for the copies still in flight before the CTA exits
       const uint32_t first = it > (uint32_t)NST ? it - NST : 0u;
       for (uint32_t k = first; k < it; ++k) {
         const int st = (int)(k % NST);
         uint32_t i = 0;
-        while (!try_wait(bfull(st), (k / NST) & 1u) && ++i < kWaitLimit) {}
+        while (!try_wait(full(st), (k / NST) & 1u) && ++i < kWaitLimit) {}
       }
     }
   } else if (warp == MMA_WARP) {
@@ -430,7 +403,7 @@ k_dst_tc(const uint4* __restrict__ D, double* __restrict__ out, int n, int64_t n
         for (int c = 0; c < nch; ++c, ++it) {
           const int st = (int)(it % NST);
           const uint32_t par = (it / NST) & 1u;
-          if (!wait_bar(full(st), par, abort_flag, err, 3) || !wait_bar(bfull(st), par, abort_flag, err, 4)) {
+          if (!wait_bar(full(st), par, abort_flag, err, 3)) {
             alive = false;
             break;
           }
