@@ -94,8 +94,8 @@ typedef struct st_options {
                             tensor-core form splits each line into 7-bit digits scaled by the line's
                             largest exponent and sums exact FP16 digit products in FP32 tensor memory;
                             its error is below 2^-50 of sqrt((n+1)/2) ||line||_2, like the FFT's.  It
-                            needs a scratch of max(32768, n^(d-1)) 4096 bytes (134 MB, 266 MB for
-                            3D n = 255), allocated on first use and counted in max_workspace_bytes. */
+                            needs a scratch of max(131072, n^(d-1)) (n+1) 16 bytes (at most 537 MB),
+                            allocated on first use and counted in max_workspace_bytes. */
 } st_options;
 
 typedef struct st_handle st_handle;

@@ -933,9 +933,9 @@ double dst_line_flops(int n) {
 }
 
 // ---- sine transforms on the tensor cores (stmg_tc.cuh) ----
-// Lines per split / tensor-core batch: the digit planes (16 bytes per value, at most 134 MB)
-// stay near the size of L2 between the two passes.
-constexpr int64_t kTcCapLines = 32768;
+// Lines per split / tensor-core batch (digit planes: 16 bytes per value, 537 MB at Nf = 256): each
+// tensor-pass launch fills and drains its pipeline once, so fewer, larger batches run faster.
+constexpr int64_t kTcCapLines = 131072;
 
 bool tc_len(int Nf) { return Nf >= stmg_tc::kMinNf && Nf <= stmg_tc::kMaxNf; }
 // ST_DST_AUTO: the tensor cores replace the FP64 FFTs; the mixed form keeps its double-float FFTs

@@ -20,13 +20,14 @@
 // line's largest exponent and writes the FP16 digit planes of every value once, in the exact layout of
 // one pipeline stage of the tensor kernel (32 KB per 128 lines x 16 K); the tensor kernel k_dst_tc is
 // persistent (one CTA per SM) and warp-specialised:
-//   warp 0     brings each chunk's data planes and sine planes with two bulk copies (48 KB);
+//   warp 0     brings each chunk's data planes and sine planes with two bulk copies (48 KB) into a
+//              3-stage ring;
 //   warp 1     issues 12 tcgen05.mma per chunk: for digit s, the sine planes t = t0 .. t0 + 3
 //              are adjacent along N, so one M = 128, N = 64 cnt MMA feeds accumulators
 //              s + t0 .. s + t0 + cnt - 1 (N <= 256);
-//   warps 2-9  drain the eight accumulators (TMEM, 512 columns) into exact int32 pairs
-//              C_g 2^7 + C_(g+1) in shared memory, release TMEM to the next tile's MMAs, then
-//              assemble and store the FP64 results.
+//   warps 2-9  drain the eight accumulators (TMEM, 512 columns) into the exact integer of each
+//              output in shared memory, release TMEM to the next tile's MMAs, then round to FP64 and
+//              store.
 // Every wait on an mbarrier is bounded: on time-out the kernel raises *err, drains its own
 // tensor-core and bulk-copy work and returns.
 #pragma once
@@ -43,13 +44,13 @@ constexpr int A_PLANE = BM * BK * 2;     // 4 KB: one FP16 data digit plane of a
 constexpr int B_PLANE = BNP * BK * 2;    // 2 KB: one FP16 sine digit plane of a chunk
 constexpr int A_STAGE = NSL * A_PLANE;   // 32 KB
 constexpr int B_STAGE = NSL * B_PLANE;   // 16 KB (the sine table stores this per (N tile, chunk))
-constexpr int NST = 2;                   // pipeline stages
+constexpr int NST = 3;                   // pipeline stages
 constexpr int TMA_WARP = 0;              // bulk copies of the stages
 constexpr int MMA_WARP = 1;              // MMA issuer
 constexpr int EPI0 = 2;                  // epilogue warps 2 .. 9: two per TMEM lane quadrant (warp % 4)
 constexpr int NEPI = 8;
 constexpr int NTHREADS = (EPI0 + NEPI) * 32;
-constexpr int TS_WARP = 32 * 32 * 16;    // staged int32 group pairs of one epilogue warp: 32 columns x 32 lines
+constexpr int TS_WARP = 32 * 32 * 10;    // staged exact sums of one epilogue warp: 32 columns x 32 lines x (8 + 2) B
 constexpr int kMaxNf = 256;              // Nf <= 256 keeps every accumulator below 2^24
 constexpr int kMinNf = 64;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -58,7 +59,7 @@ constexpr int kZeroExp = -1100;          // exponent assigned to zero (below eve
 struct Smem {
   static constexpr int a_off = 0;
   static constexpr int b_off = a_off + NST * A_STAGE;
-  static constexpr int ts_off = b_off + NST * B_STAGE;
+  static constexpr int ts_off = b_off + NST * B_STAGE;   // per warp: int64 high parts, then uint16 remainders
   static constexpr int bar_off = ts_off + NEPI * TS_WARP;
   static constexpr int nbars = 2 * NST + 3;   // full[NST], empty[NST], accf, acce, drain
   static constexpr int misc_off = bar_off + nbars * 8;
@@ -289,18 +290,16 @@ __device__ __noinline__ double assemble128(__int128 W, int e0) {
   return __longlong_as_double((long long)bits);
 }
 
-// value = (V 2^14 + t) 2^e0 rounded to nearest even, |V| < 2^57, branch-free for results in the
-// normal range; slow = true when the result is subnormal or overflows (use assemble128).
-__device__ __forceinline__ double assemble_vt(long long V, int t, int e0, bool& slow) {
-  const long long Vp = V + (long long)(t >> 14);   // W = Vp 2^14 + r, 0 <= r < 2^14
-  const uint32_t r = (uint32_t)t & 0x3fffu;
+// value = (Vp 2^14 + r) 2^e0 rounded to nearest even, |Vp| < 2^58, 0 <= r < 2^14, branch-free for
+// results in the normal range; slow = true when the result is subnormal or overflows (use assemble128).
+__device__ __forceinline__ double assemble_vr(long long Vp, uint32_t r, int e0, bool& slow) {
   const bool neg = Vp < 0;
   const unsigned long long A = neg ? (unsigned long long)(-Vp) - (r ? 1ull : 0ull) : (unsigned long long)Vp;
   const uint32_t B = neg ? (r ? 16384u - r : 0u) : r;   // |W| = A 2^14 + B = (hw, lw) as 128 bits
   const unsigned long long lw = (A << 14) | B, hw = A >> 50;
   const int p = A ? 77 - __clzll((long long)A) : (B ? 31 - __clz((int)B) : 0);   // leading bit of |W|
   const int be = p + e0 + 1023;
-  const int sh = p - 52;                                                      // in [-52, 18]
+  const int sh = p - 52;                                                      // in [-52, 19]
   const int shp = sh > 0 ? sh : 0, shn = sh < 0 ? -sh : 0;
   unsigned long long q = (lw >> shp) | (shp ? (hw << (64 - shp)) : 0ull);
   q <<= shn;
@@ -434,13 +433,14 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
     }
   } else {
     // ---- epilogue ----
-    // Phase 1 (TMEM held): group sums -> exact int32 pairs t = C_g 2^7 + C_(g+1) in shared memory
-    // (C_0, C_1 < 2^22 by magic-number addition, C_2 .. C_7 < 2^24 by conversion; every pair sum
-    // is below 2^31 by the same bound); then TMEM goes to the next tile's MMAs.
-    // Phase 2: FP64 assembly and stores.
+    // Phase 1 (TMEM held): group sums -> the exact W = sum_g C_g 2^(7 (7 - g)) = Vp 2^14 + r (C_0, C_1 < 2^22
+    // by magic-number addition, C_2 .. C_7 < 2^24 by conversion; pairs C_g 2^7 + C_(g+1) < 2^31 in int32,
+    // then 64-bit) staged in shared memory; then TMEM goes to the next tile's MMAs.
+    // Phase 2: FP64 rounding and stores.
     const int q = warp & 3;                   // TMEM lane quadrant of this warp
     const int half_id = (warp - EPI0) >> 2;   // columns [32 half_id, 32 half_id + 32) of the tile
-    uint4* ts = reinterpret_cast<uint4*>(sm + SL::ts_off + (warp - EPI0) * TS_WARP);   // [column][lane]
+    long long* tsv = reinterpret_cast<long long*>(sm + SL::ts_off + (warp - EPI0) * TS_WARP);   // [column][lane]
+    uint16_t* tsr = reinterpret_cast<uint16_t*>(sm + SL::ts_off + (warp - EPI0) * TS_WARP + 32 * 32 * 8);
     uint32_t ti = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
       const int64_t b = t / ntn;
@@ -453,27 +453,28 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
 #pragma unroll 1
       for (int cb = 0; cb < 4; ++cb) {   // 8 columns at a time
         const uint32_t col = (uint32_t)(32 * half_id + 8 * cb);
+        uint32_t v[NSL][8];   // all eight group sums of 8 columns, one wait
+#pragma unroll
+        for (int g = 0; g < NSL; ++g) tmem_ld8(tl + (uint32_t)(BNP * g) + col, v[g]);
+        tmem_wait_ld();
         uint32_t tp[4][8];
 #pragma unroll
-        for (int g = 0; g < NSL; g += 2) {
-          uint32_t va[8], vb[8];
-          tmem_ld8(tl + (uint32_t)(BNP * g) + col, va);
-          tmem_ld8(tl + (uint32_t)(BNP * (g + 1)) + col, vb);
-          tmem_wait_ld();
+        for (int c = 0; c < 8; ++c) {
+          const uint32_t b0 = __float_as_uint(__uint_as_float(v[0][c]) + 12582912.0f);
+          const uint32_t b1 = __float_as_uint(__uint_as_float(v[1][c]) + 12582912.0f);
+          tp[0][c] = b0 * 128u + b1 - 129u * 0x4b400000u;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            if (g == 0) {
-              const uint32_t b0 = __float_as_uint(__uint_as_float(va[c]) + 12582912.0f);
-              const uint32_t b1 = __float_as_uint(__uint_as_float(vb[c]) + 12582912.0f);
-              tp[0][c] = b0 * 128u + b1 - 129u * 0x4b400000u;
-            } else {
-              tp[g >> 1][c] =
-                  (uint32_t)(__float2int_rn(__uint_as_float(va[c])) * 128 + __float2int_rn(__uint_as_float(vb[c])));
-            }
-          }
+          for (int g = 2; g < NSL; g += 2)
+            tp[g >> 1][c] = (uint32_t)(__float2int_rn(__uint_as_float(v[g][c])) * 128 +
+                                       __float2int_rn(__uint_as_float(v[g + 1][c])));
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) ts[(8 * cb + c) * 32 + lane] = make_uint4(tp[0][c], tp[1][c], tp[2][c], tp[3][c]);
+        for (int c = 0; c < 8; ++c) {
+          const int t67 = (int)tp[3][c];
+          const long long V = (((long long)(int)tp[0][c] << 14) + (int)tp[1][c]) * 16384ll + (int)tp[2][c];
+          tsv[(8 * cb + c) * 32 + lane] = V + (long long)(t67 >> 14);   // floor division: remainder below
+          tsr[(8 * cb + c) * 32 + lane] = (uint16_t)((uint32_t)t67 & 0x3fffu);
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -487,13 +488,13 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
       const int k0 = nt * BNP + 32 * half_id;   // frequency of column 0 of this warp
 #pragma unroll 4
       for (int c = 0; c < 32; ++c) {
-        const uint4 tv = ts[c * 32 + lane];
-        const long long V = (((long long)(int)tv.x << 14) + (int)tv.y) * 16384ll + (int)tv.z;
+        const long long Vp = tsv[c * 32 + lane];
+        const uint32_t r = tsr[c * 32 + lane];
         bool slow;
-        double y = assemble_vt(V, (int)tv.w, e0, slow);
+        double y = assemble_vr(Vp, r, e0, slow);
         if (slow || Er >= 2047)
           y = Er >= 2047 ? __longlong_as_double(0x7ff8000000000000ll)
-                         : assemble128(((__int128)V << 14) + (__int128)(int)tv.w, e0);
+                         : assemble128(((__int128)Vp << 14) + (__int128)r, e0);
         const int k = k0 + c;
         if (L < nlines && k >= 1 && k <= n) out[obase + (int64_t)(k - 1) * ostride] = y;
       }
