@@ -61,9 +61,9 @@ extern "C" {
 #define ST_SMOOTH_VCYCLE 1  /* D~^{-1}: one spatial multigrid V-cycle per step (Remark on the V-cycle
                                approximation in space; damped point-block Jacobi, nu_x, omega_x) */
 
-#define ST_DST_AUTO   0  /* ST_FP64: sine transforms on the tensor cores where 64 <= n_L + 1 <= 256, else the
-                             FFT kernels; ST_MIXED: the double-float FFT kernels (faster on the FP32 pipe) */
-#define ST_DST_FFT    1  /* FFT-based sine transforms (FP64 pipe) at every length */
+#define ST_DST_AUTO   0  /* sine transforms on the tensor cores where 64 <= n_L + 1 <= 256, else the FFT kernels
+                             (FP64, or double-float on the FP32 pipe in the mixed form) */
+#define ST_DST_FFT    1  /* FFT-based sine transforms at every length (FP64; double-float in the mixed form) */
 #define ST_DST_TENSOR 2  /* tensor-core sine transforms; st_setup fails (ST_EINVAL) unless 64 <= n + 1 <= 256 */
 
 #define ST_MAX_PT    47  /* largest supported DG degree p_t (q <= 48); degrees above 3 use the

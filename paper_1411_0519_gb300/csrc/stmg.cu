@@ -938,13 +938,9 @@ double dst_line_flops(int n) {
 constexpr int64_t kTcCapLines = 131072;
 
 bool tc_len(int Nf) { return Nf >= stmg_tc::kMinNf && Nf <= stmg_tc::kMaxNf; }
-// ST_DST_AUTO: the tensor cores replace the FP64 FFTs; the mixed form keeps its double-float FFTs
-// (FP32 pipe), which are faster than the tensor-core pass at these lengths.
-bool use_tc(const st_handle* h, const Level& lv) {
-  if (!tc_len(lv.n + 1)) return false;
-  if (h->opt.transform == ST_DST_TENSOR) return true;
-  return h->opt.transform == ST_DST_AUTO && h->opt.precision == ST_FP64;
-}
+// ST_DST_AUTO and ST_DST_TENSOR: the tensor cores replace the FP64 FFTs and the mixed form's
+// double-float FFTs at these lengths (faster than both).
+bool use_tc(const st_handle* h, const Level& lv) { return h->opt.transform != ST_DST_FFT && tc_len(lv.n + 1); }
 
 // FP16 bits of an integer |d| <= 64.
 uint16_t fp16_of_small_int(int d) {

@@ -434,8 +434,8 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
   } else {
     // ---- epilogue ----
     // Phase 1 (TMEM held): group sums -> the exact W = sum_g C_g 2^(7 (7 - g)) = Vp 2^14 + r (C_0, C_1 < 2^22
-    // by magic-number addition, C_2 .. C_7 < 2^24 by conversion; pairs C_g 2^7 + C_(g+1) < 2^31 in int32,
-    // then 64-bit) staged in shared memory; then TMEM goes to the next tile's MMAs.
+    // by magic-number addition, C_2 .. C_7 < 2^24 by conversion; pairs C_g 2^7 + C_(g+1)
+    // < 2^31 in int32, then 64-bit) staged in shared memory; then TMEM goes to the next tile's MMAs.
     // Phase 2: FP64 rounding and stores.
     const int q = warp & 3;                   // TMEM lane quadrant of this warp
     const int half_id = (warp - EPI0) >> 2;   // columns [32 half_id, 32 half_id + 32) of the tile

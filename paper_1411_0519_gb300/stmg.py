@@ -172,8 +172,7 @@ def make_options(*, nu1=2, nu2=2, omega=0.5, rtol=1e-8, maxit=50, precision="fp6
                  coarsest_steps=1, inner_cycles=1, max_workspace_bytes=0, smoother="exact", nu_x=2,
                  omega_x=2.0 / 3.0, gamma=1, transform="auto"):
     """st_options from keyword arguments (the defaults of st_default_options).
-    transform: "auto" (FP64: tensor cores for 64 <= n + 1 <= 256; mixed: double-float FFTs), "fft" or
-    "tensor"."""
+    transform: "auto" (tensor cores for 64 <= n + 1 <= 256, else FFTs), "fft" or "tensor"."""
     opt = StOptions()
     lib().st_default_options(ctypes.byref(opt))
     opt.nu1, opt.nu2, opt.omega, opt.rtol, opt.maxit = nu1, nu2, omega, rtol, maxit
