@@ -988,10 +988,14 @@ void tc_prepare(st_handle* h, Level& lv) {
     h->tcE = dalloc<int>(h, cap);
     h->tcErr = dalloc<int>(h, 1);
     check(h, cudaMemsetAsync(h->tcErr, 0, sizeof(int), h->stream), "memset");
-    check(h, cudaFuncSetAttribute((const void*)stmg_tc::k_dst_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  stmg_tc::Smem::bytes), "cudaFuncSetAttribute");
-    check(h, cudaFuncSetAttribute((const void*)stmg_tc::k_dst_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  stmg_tc::Smem::bytes), "cudaFuncSetAttribute");
+    auto attr = [&](const void* fn) {
+      check(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, stmg_tc::Smem::bytes),
+            "cudaFuncSetAttribute");
+    };
+    attr((const void*)stmg_tc::k_dst_tc<true, stmg_tc::NEPI>);
+    attr((const void*)stmg_tc::k_dst_tc<false, stmg_tc::NEPI>);
+    attr((const void*)stmg_tc::k_dst_tc<true, stmg_tc::NEPI_SHORT>);
+    attr((const void*)stmg_tc::k_dst_tc<false, stmg_tc::NEPI_SHORT>);
   }
   if (!lv.tcS) {
     const std::vector<uint16_t> tab = tc_sine_digits(lv.n + 1);
@@ -1045,11 +1049,21 @@ void dst_axes_tc(st_handle* h, Level& lv, const double* src, double* mid, double
         const int64_t ntiles = nlpad / stmg_tc::BM * ntn;
         const unsigned grid = (unsigned)std::min<int64_t>(ntiles, h->num_sms);
         Prof pr(h, ST_K_DSTTC, 8.0 * (double)nlines * n, 2.0 * 36.0 * Nf * (double)Nf * (double)nlpad, 1, lvl);
-        if (a == 0)
-          stmg_tc::k_dst_tc<true><<<grid, stmg_tc::NTHREADS, stmg_tc::Smem::bytes, h->stream>>>(
+        // the epilogue sets the pace when a tile has few K-chunks: more warps for it there
+        constexpr int NL = stmg_tc::NEPI, NS = stmg_tc::NEPI_SHORT;
+        const bool shortk = Nf <= 128;
+        const unsigned thr = (unsigned)stmg_tc::threads_for(shortk ? NS : NL);
+        if (a == 0 && !shortk)
+          stmg_tc::k_dst_tc<true, NL><<<grid, thr, stmg_tc::Smem::bytes, h->stream>>>(
+              h->tcD, out, n, nlines, inner, h->tcE, lv.tcS, nch, ntn, oe, h->tcErr);
+        else if (!shortk)
+          stmg_tc::k_dst_tc<false, NL><<<grid, thr, stmg_tc::Smem::bytes, h->stream>>>(
+              h->tcD, out, n, nlines, inner, h->tcE, lv.tcS, nch, ntn, oe, h->tcErr);
+        else if (a == 0)
+          stmg_tc::k_dst_tc<true, NS><<<grid, thr, stmg_tc::Smem::bytes, h->stream>>>(
               h->tcD, out, n, nlines, inner, h->tcE, lv.tcS, nch, ntn, oe, h->tcErr);
         else
-          stmg_tc::k_dst_tc<false><<<grid, stmg_tc::NTHREADS, stmg_tc::Smem::bytes, h->stream>>>(
+          stmg_tc::k_dst_tc<false, NS><<<grid, thr, stmg_tc::Smem::bytes, h->stream>>>(
               h->tcD, out, n, nlines, inner, h->tcE, lv.tcS, nch, ntn, oe, h->tcErr);
       }
       inner *= n;

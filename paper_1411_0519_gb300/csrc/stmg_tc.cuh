@@ -25,9 +25,9 @@
 //   warp 1     issues 12 tcgen05.mma per chunk: for digit s, the sine planes t = t0 .. t0 + 3
 //              are adjacent along N, so one M = 128, N = 64 cnt MMA feeds accumulators
 //              s + t0 .. s + t0 + cnt - 1 (N <= 256);
-//   warps 2-9  drain the eight accumulators (TMEM, 512 columns) into the exact integer of each
-//              output in shared memory, release TMEM to the next tile's MMAs, then round to FP64 and
-//              store.
+//   warps 2-    8 (Nf = 256) or 16 (Nf <= 128) epilogue warps drain the eight accumulators (TMEM, 512
+//              columns) into the exact integer of each output in shared memory, release TMEM to the
+//              next tile's MMAs, then round to FP64 and store.
 // Every wait on an mbarrier is bounded: on time-out the kernel raises *err, drains its own
 // tensor-core and bulk-copy work and returns.
 #pragma once
@@ -47,10 +47,12 @@ constexpr int B_STAGE = NSL * B_PLANE;   // 16 KB (the sine table stores this pe
 constexpr int NST = 3;                   // pipeline stages
 constexpr int TMA_WARP = 0;              // bulk copies of the stages
 constexpr int MMA_WARP = 1;              // MMA issuer
-constexpr int EPI0 = 2;                  // epilogue warps 2 .. 9: two per TMEM lane quadrant (warp % 4)
-constexpr int NEPI = 8;
+constexpr int EPI0 = 2;                  // epilogue warps from 2 on: NE / 4 per TMEM lane quadrant (warp % 4)
+constexpr int NEPI = 8;                  // epilogue warps for Nf = 256 (the MMAs of a tile hide their work)
+constexpr int NEPI_SHORT = 16;           // for Nf <= 128: 4 or 8 K-chunks per tile, the epilogue sets the pace
 constexpr int NTHREADS = (EPI0 + NEPI) * 32;
-constexpr int TS_WARP = 32 * 32 * 10;    // staged exact sums of one epilogue warp: 32 columns x 32 lines x (8 + 2) B
+__host__ __device__ constexpr int threads_for(int ne) { return (EPI0 + ne) * 32; }
+constexpr int TS_BYTES = 4 * BNP * 32 * 10;   // staged exact sums of a tile: 64 columns x 128 lines x (8 + 2) B
 constexpr int kMaxNf = 256;              // Nf <= 256 keeps every accumulator below 2^24
 constexpr int kMinNf = 64;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -60,7 +62,7 @@ struct Smem {
   static constexpr int a_off = 0;
   static constexpr int b_off = a_off + NST * A_STAGE;
   static constexpr int ts_off = b_off + NST * B_STAGE;   // per warp: int64 high parts, then uint16 remainders
-  static constexpr int bar_off = ts_off + NEPI * TS_WARP;
+  static constexpr int bar_off = ts_off + TS_BYTES;
   static constexpr int nbars = 2 * NST + 3;   // full[NST], empty[NST], accf, acce, drain
   static constexpr int misc_off = bar_off + nbars * 8;
   static constexpr int bytes = misc_off + 16 + 1024;   // + slack for 1024-byte alignment of the base
@@ -320,9 +322,10 @@ __device__ __forceinline__ double assemble_vr(long long Vp, uint32_t r, int e0, 
 // (64 <= Nf <= 256), for every line, from the digit planes P and line exponents lineE of the split
 // pass.  Output line L: y_k at out[L n + k - 1] (ROWS) or out[(L / inner) n inner + (k - 1) inner
 // + L % inner].  sdig: FP16 digits of S / 2, B_STAGE bytes per (N tile, K chunk).  Launch with
-// NTHREADS threads, Smem::bytes of dynamic shared memory and at most one CTA per SM.
-template <bool ROWS>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// threads_for(NE) threads (NE = 8 or 16 epilogue warps), Smem::bytes of dynamic shared memory and at
+// most one CTA per SM.
+template <bool ROWS, int NE>
+__global__ void __launch_bounds__(threads_for(NE), 1)
 k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t nlines, int64_t inner,
          const int* __restrict__ lineE, const uint8_t* __restrict__ sdig, int nch, int ntn, int out_exp,
          int* __restrict__ err) {
@@ -353,7 +356,7 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
       bar_init(empty(s), 1);
     }
     bar_init(accf, 1);
-    bar_init(acce, NEPI);
+    bar_init(acce, NE);
     bar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -438,9 +441,11 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
     // < 2^31 in int32, then 64-bit) staged in shared memory; then TMEM goes to the next tile's MMAs.
     // Phase 2: FP64 rounding and stores.
     const int q = warp & 3;                   // TMEM lane quadrant of this warp
-    const int half_id = (warp - EPI0) >> 2;   // columns [32 half_id, 32 half_id + 32) of the tile
-    long long* tsv = reinterpret_cast<long long*>(sm + SL::ts_off + (warp - EPI0) * TS_WARP);   // [column][lane]
-    uint16_t* tsr = reinterpret_cast<uint16_t*>(sm + SL::ts_off + (warp - EPI0) * TS_WARP + 32 * 32 * 8);
+    constexpr int EC = 4 * BNP / NE;          // tile columns per epilogue warp (32 or 16)
+    constexpr int TSW = EC * 32 * 10;         // its staging bytes
+    const int cq = (warp - EPI0) >> 2;        // columns [EC cq, EC cq + EC) of the tile
+    long long* tsv = reinterpret_cast<long long*>(sm + SL::ts_off + (warp - EPI0) * TSW);   // [column][lane]
+    uint16_t* tsr = reinterpret_cast<uint16_t*>(sm + SL::ts_off + (warp - EPI0) * TSW + EC * 32 * 8);
     uint32_t ti = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
       const int64_t b = t / ntn;
@@ -451,8 +456,8 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-      for (int cb = 0; cb < 4; ++cb) {   // 8 columns at a time
-        const uint32_t col = (uint32_t)(32 * half_id + 8 * cb);
+      for (int cb = 0; cb < EC / 8; ++cb) {   // 8 columns at a time
+        const uint32_t col = (uint32_t)(EC * cq + 8 * cb);
         uint32_t v[NSL][8];   // all eight group sums of 8 columns, one wait
 #pragma unroll
         for (int g = 0; g < NSL; ++g) tmem_ld8(tl + (uint32_t)(BNP * g) + col, v[g]);
@@ -485,9 +490,9 @@ k_dst_tc(const uint8_t* __restrict__ P, double* __restrict__ out, int n, int64_t
       int64_t obase = 0;
       if (L < nlines) obase = ROWS ? L * n : (L / inner) * n * inner + (L % inner);
       const int64_t ostride = ROWS ? 1 : inner;
-      const int k0 = nt * BNP + 32 * half_id;   // frequency of column 0 of this warp
+      const int k0 = nt * BNP + EC * cq;   // frequency of column 0 of this warp
 #pragma unroll 4
-      for (int c = 0; c < 32; ++c) {
+      for (int c = 0; c < EC; ++c) {
         const long long Vp = tsv[c * 32 + lane];
         const uint32_t r = tsr[c * 32 + lane];
         bool slow;
