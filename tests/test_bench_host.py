@@ -103,6 +103,30 @@ def test_vcycle_times_leave_out_the_boundary_transforms():
     assert v["frac"] == pytest.approx(v["achieved_gbs"] / 1000.0, rel=1e-3)
 
 
+def test_vcycle_times_leave_out_both_transform_classes():
+    """With the tensor-core transforms the boundary work is two classes (split pass 'dst' and tensor
+    pass 'dst_tc'); neither counts toward the cycle."""
+    fs = _FakeSolver(3, {("smooth", 2): {"launches": 8, "ms": 12.0, "bytes": 0.0, "flops": 0.0},
+                         ("residual", 2): {"launches": 4, "ms": 6.0, "bytes": 0.0, "flops": 0.0}})
+    prof = _prof(smooth=(10, 14.0, 6e9, 0), residual=(6, 7.0, 3e9, 0), dst=(2, 3.0, 5e9, 0),
+                 dst_tc=(2, 6.0, 5e9, 1e15))
+    v = bench.vcycle_times(fs, prof, steps=3, iters=2, per_step_ms=20.0, pk={"hbm_gbs": 1000.0})
+    assert v["ms_per_cycle_without_transforms"] == pytest.approx((20.0 - 9.0 / 3) / 2)
+    assert v["alg_bytes_per_cycle"] == pytest.approx(9e9 / 3 / 2)
+
+
+def test_transform_note_reports_the_tensor_rate_against_the_measured_peak():
+    prof = _prof(smooth=(10, 14.0, 6e9, 0), dst=(4, 2.0, 4e9, 0), dst_tc=(4, 6.0, 4e9, 9.0e12))
+    note = bench.transform_note(prof, {}, {"bf16_tflops_sustained": 1500.0})
+    assert note["tensor_tflops"] == pytest.approx(1500.0, rel=1e-6)      # 9e12 flop in 6 ms
+    assert note["tensor_frac"] == pytest.approx(1.0, rel=1e-6)
+    assert note["split_gbs"] == pytest.approx(4e9 / 2e-3 / 1e9, rel=1e-6)
+    assert note["share_of_kernel_time"] == pytest.approx(8.0 / 22.0, abs=1e-3)
+    # the FFT form (no tensor pass) keeps the double-float description
+    fft = bench.transform_note(_prof(smooth=(10, 14.0, 6e9, 0), dst=(4, 8.0, 4e9, 1e9)), {})
+    assert fft["arithmetic"].startswith("double-float")
+
+
 def test_windowed_load_equals_the_slice_of_the_full_load():
     """The CPU baseline's workers draw only their own time steps of f."""
     import numpy as np
