@@ -25,9 +25,9 @@
 //   warp 1     issues 12 tcgen05.mma per chunk: for digit s, the sine planes t = t0 .. t0 + 3
 //              are adjacent along N, so one M = 128, N = 64 cnt MMA feeds accumulators
 //              s + t0 .. s + t0 + cnt - 1 (N <= 256);
-//   warps 2-    8 (Nf = 256) or 16 (Nf <= 128) epilogue warps drain the eight accumulators (TMEM, 512
-//              columns) into the exact integer of each output in shared memory, release TMEM to the
-//              next tile's MMAs, then round to FP64 and store.
+//   warps 2 .. 8 (Nf = 256) or 16 (Nf <= 128) epilogue warps drain the eight accumulators (TMEM,
+//              512 columns) into the exact integer of each output in shared memory, release TMEM to
+//              the next tile's MMAs, then round to FP64 and store.
 // Every wait on an mbarrier is bounded: on time-out the kernel raises *err, drains its own
 // tensor-core and bulk-copy work and returns.
 #pragma once
